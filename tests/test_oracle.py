@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself:
+  * the closed-form solution of the constant-kernel problem (Sec. 1 cites it as an
+    exactly solvable case): n_s(t) = (t/2)^{s-1} / (1 + t/2)^{s+1};
+  * the mass balance of Eq. (4): shattering moves mass to monomers without loss, so
+    sum_s s S_s(n) equals the truncation flux exactly;
+  * a brute-force pure-Python restatement of Eq. (4) on tiny M (explicit loops);
+  * the direct O(M^2) route against the low-rank FFT route (Sec. 1, Sec. 2) on
+    non-symmetric random factors, so a transposed U/V fails the death term;
+  * the stability polynomials of the Sec. 2 schemes on y' = z y (tests/golden);
+  * the worked examples of the RKF45 step rule (Sec. 2, last paragraph; tests/golden);
+  * observed convergence orders 2 / 4 / 4 on a smooth ODE;
+  * conservation of the linear invariant sum_s s n_s + F by every explicit RK step.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import kernel_factors, monodisperse, random_factors, random_state, sample_state
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def closed_form(M, t):
+    s = np.arange(1, M + 1, dtype=np.float64)
+    h = t / 2.0
+    return h ** (s - 1) / (1.0 + h) ** (s + 1)
+
+
+def closed_form_dt(M, t):
+    """d/dt of the closed form, differentiated by hand:
+    n_s = h^{s-1} (1+h)^{-(s+1)}, h = t/2, dh/dt = 1/2 ->
+    dn_s/dt = 1/2 [ (s-1) h^{s-2} (1+h)^{-(s+1)} - (s+1) h^{s-1} (1+h)^{-(s+2)} ]."""
+    s = np.arange(1, M + 1, dtype=np.float64)
+    h = t / 2.0
+    a = np.where(s > 1, (s - 1) * h ** np.maximum(s - 2, 0) / (1.0 + h) ** (s + 1), 0.0)
+    b = (s + 1) * h ** (s - 1) / (1.0 + h) ** (s + 2)
+    return 0.5 * (a - b)
+
+
+def brute_force_rhs(n, kfun, lam):
+    """Eq. (4) written with explicit loops over 1-based sizes (tiny M only)."""
+    M = len(n)
+    N = {s: n[s - 1] for s in range(1, M + 1)}
+    out = []
+    for s in range(1, M + 1):
+        loss = N[s] * sum(kfun(s, i) * N[i] for i in range(1, M + 1))
+        if s == 1:
+            src = 0.0
+            for i in range(2, M + 1):
+                for j in range(2, M + 1):
+                    src += 0.5 * lam * (i + j) * kfun(i, j) * N[i] * N[j]
+            src += lam * N[1] * sum(j * kfun(1, j) * N[j] for j in range(2, M + 1))
+            out.append(-loss + src)
+        else:
+            birth = 0.5 * sum(kfun(i, s - i) * N[i] * N[s - i] for i in range(1, s))
+            out.append(birth - loss - lam * loss)
+    return np.array(out)
+
+
+# ---------------------------------------------------------------------------
+# Right-hand side
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("t", [0.5, 2.0, 5.0])
+def test_rhs_matches_closed_form_derivative(t):
+    """K = 1, lambda = 0 on the closed-form state: S(n) = dn/dt up to the death sum's
+    truncation n_s sum_{i>M} n_i, which is below 1e-20 at M = 256 for t <= 5."""
+    M = 256
+    n = closed_form(M, t)
+    U, V = kernel_factors("const", M)
+    for terms in (oracle.rhs_terms_direct(n, U @ V, 0.0), oracle.rhs_terms_lowrank(n, U, V, 0.0)):
+        S = terms["total"]
+        ref = closed_form_dt(M, t)
+        assert np.max(np.abs(S - ref)) <= 1e-14 * np.max(np.abs(ref)) + 1e-20
+
+
+@pytest.mark.parametrize("kind,a", [("const", 0.0), ("brownian", 0.3), ("brownian", 0.9), ("brownian_const", 1 / 3)])
+@pytest.mark.parametrize("lam", [0.0, 0.01, 0.5])
+def test_mass_flux_identity(kind, a, lam):
+    """Eq. (4) with a symmetric kernel: sum_s s S_s(n) = -1/2 sum_{i+j>M} (i+j) K_ij n_i n_j.
+    Fails if the n_1 factor of the monomer source, the (i+j) weight, or the shattering
+    loss is dropped or mis-signed."""
+    M = 40
+    n = random_state(M, seed=7, decay=12.0)
+    U, V = kernel_factors(kind, M, a=a)
+    K = oracle.kernel_closed_form(kind, M, a=a)
+    s = np.arange(1, M + 1, dtype=np.float64)
+    flux = oracle.mass_flux_direct(n, K)
+    for S in (oracle.rhs_terms_direct(n, K, lam)["total"], oracle.rhs_terms_lowrank(n, U, V, lam)["total"]):
+        lhs = float(np.dot(s, S))
+        scale = float(np.dot(s, np.abs(S))) + abs(flux)
+        assert abs(lhs - flux) <= 1e-13 * scale
+
+
+def test_mass_identity_fails_without_n1_factor():
+    """The reading of the monomer equation matters: the literal printed term
+    lambda sum_{j>=2} j K_{1j} n_j (no n_1) breaks the mass balance."""
+    M, lam = 30, 0.3
+    n = random_state(M, seed=3, decay=8.0)
+    K = oracle.kernel_closed_form("brownian", M, a=0.4)
+    s = np.arange(1, M + 1, dtype=np.float64)
+    S = oracle.rhs_terms_direct(n, K, lam)["total"].copy()
+    w = lam * np.sum(s[1:] * K[0, 1:] * n[1:])
+    S[0] += w - n[0] * w          # swap lambda n_1 sum(...) for the literal lambda sum(...)
+    flux = oracle.mass_flux_direct(n, K)
+    assert abs(float(np.dot(s, S)) - flux) > 1e-6
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 7])
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_brute_force_tiny(M, lam):
+    """Vectorised direct route and low-rank FFT route vs explicit loops, with a
+    non-symmetric rank-2 kernel."""
+    U, V = random_factors(M, 2, seed=11)
+    K = U @ V
+    n = random_state(M, seed=5, decay=2.0)
+    ref = brute_force_rhs(n, lambda i, j: K[i - 1, j - 1], lam)
+    d = oracle.rhs_terms_direct(n, K, lam)["total"]
+    f = oracle.rhs_terms_lowrank(n, U, V, lam)["total"]
+    scale = np.max(np.abs(ref)) + 1e-300
+    assert np.max(np.abs(d - ref)) <= 1e-14 * scale
+    assert np.max(np.abs(f - ref)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("M,R", [(64, 1), (257, 3), (1024, 2), (4096, 4)])
+def test_direct_vs_lowrank_random_factors(M, R):
+    """Sec. 1 / Sec. 2: the O(M R log M) route equals the O(M^2) definition; factors
+    are non-symmetric, so swapping U and V changes the death and source terms."""
+    U, V = random_factors(M, R, seed=M + R)
+    n = random_state(M, seed=M)
+    d = oracle.rhs_terms_direct(n, U @ V, 0.05)
+    f = oracle.rhs_terms_lowrank(n, U, V, 0.05)
+    for key in ("birth", "death", "shatter_loss", "monomer_source"):
+        ref = d[key]
+        nrm = np.linalg.norm(ref) + 1e-300
+        assert np.linalg.norm(f[key] - ref) <= 1e-12 * nrm, key
+    swapped = oracle.rhs_terms_lowrank(n, V.T.copy(), U.T.copy(), 0.05)
+    assert np.linalg.norm(swapped["death"] - d["death"]) > 1e-6 * np.linalg.norm(d["death"])
+
+
+def test_kernel_factors_reproduce_closed_forms():
+    M = 300
+    for kind, a in (("const", 0.0), ("brownian", 0.3), ("brownian", 0.9), ("brownian_const", 1 / 3)):
+        U, V = kernel_factors(kind, M, a=a)
+        K = oracle.kernel_closed_form(kind, M, a=a)
+        assert np.max(np.abs(U @ V - K) / K) <= 1e-14
+
+
+def test_entries_direct_matches_full_direct():
+    M, lam = 200, 0.01
+    n = sample_state(M, lam)
+    K = oracle.kernel_closed_form("brownian", M, a=0.9)
+    full = oracle.rhs_terms_direct(n, K, lam)["total"]
+    sizes = [2, 3, 50, 199, 200]
+    got = oracle.rhs_entries_direct(n, lambda i, j: (i / j) ** 0.9 + (j / i) ** 0.9, lam, sizes)
+    ref = full[np.array(sizes) - 1]
+    assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Runge-Kutta tableaux
+# ---------------------------------------------------------------------------
+def _poly(coefs, z):
+    return sum(float(Fraction(num, den)) * z ** k for k, (num, den) in enumerate(coefs))
+
+
+@pytest.mark.parametrize("z", [-0.3, 0.7, -1.9, 1.3 - 0.4j, -2.2 + 1.1j])
+def test_stability_polynomials(z):
+    g = json.load(open(os.path.join(GOLDEN, "rk_stability.json")))["polys"]
+    S = lambda y: z * y  # noqa: E731
+    y0 = np.array([1.0 + 0j])
+    assert abs(oracle.rk2_step(S, y0, 1.0)[0] - _poly(g["rk2"], z)) <= 1e-14
+    assert abs(oracle.rk4_step(S, y0, 1.0)[0] - _poly(g["rk4"], z)) <= 1e-14
+    n4, n5 = oracle.rkf45_step(S, y0, 1.0)
+    assert abs(n4[0] - _poly(g["rkf45_n4"], z)) <= 1e-13
+    assert abs(n5[0] - _poly(g["rkf45_n5"], z)) <= 1e-13
+
+
+def test_observed_orders():
+    """y' = -y^2 + cos t style smooth scalar ODE; errors at t=1 shrink as tau^p."""
+    def S(y, t=[0.0]):
+        return -y * y
+    y0 = np.array([1.0])
+    exact = 1.0 / (1.0 + 1.0)  # y = 1/(1+t) at t = 1
+    def run(step, N, pick=0):
+        y = y0.copy()
+        for _ in range(N):
+            r = step(S, y, 1.0 / N)
+            y = r[pick] if isinstance(r, tuple) else r
+        return abs(y[0] - exact)
+    for step, p, pick in ((oracle.rk2_step, 2, 0), (oracle.rk4_step, 4, 0), (oracle.rkf45_step, 4, 0),
+                          (oracle.rkf45_step, 5, 1)):
+        e1, e2 = run(step, 8, pick), run(step, 16, pick)
+        rate = math.log2(e1 / e2)
+        assert rate > p - 0.35, (step.__name__, p, rate)
+        if pick == 0:                     # the propagated solutions have exactly order p
+            assert rate < p + 0.35, (step.__name__, p, rate)
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk4", "rkf45"])
+def test_linear_invariant_mass_plus_flux(scheme):
+    """Explicit RK preserves linear invariants: augmenting Eq. (4) with F' = -flux(n),
+    sum_s s n_s + F is the same before and after a step, to rounding."""
+    M, lam = 48, 0.05
+    K = oracle.kernel_closed_form("brownian", M, a=0.6)
+    s = np.arange(1, M + 1, dtype=np.float64)
+
+    def S_aug(v):
+        n = v[:M]
+        return np.concatenate([oracle.rhs_terms_direct(n, K, lam)["total"], [-oracle.mass_flux_direct(n, K)]])
+
+    n = sample_state(M, lam)
+    v = np.concatenate([n, [0.0]])
+    step = {"rk2": oracle.rk2_step, "rk4": oracle.rk4_step, "rkf45": oracle.rkf45_step}[scheme]
+    r = step(S_aug, v, 0.7)
+    w = r[0] if isinstance(r, tuple) else r
+    inv0 = float(np.dot(s, v[:M]) + v[M])
+    inv1 = float(np.dot(s, w[:M]) + w[M])
+    assert abs(inv1 - inv0) <= 1e-14 * abs(inv0)
+    assert abs(float(np.dot(s, w[:M])) - float(np.dot(s, v[:M]))) > 1e-8  # flux actually acts
+
+
+# ---------------------------------------------------------------------------
+# Step-size controllers
+# ---------------------------------------------------------------------------
+def test_rkf45_controller_worked_examples():
+    g = json.load(open(os.path.join(GOLDEN, "rkf45_controller.json")))
+    tol, tau = 1e-8, 0.37
+    for case in g["cases"]:
+        acc, tau_new = oracle.ctrl_rkf45(tau, case["err_over_tol"] * tol, tol)
+        assert acc == case["accept"]
+        assert abs(tau_new / tau - case["factor"]) <= case["abs_tol"]
+
+
+def test_double_halve_and_formula_controllers():
+    assert oracle.ctrl_double_halve(0.2, 2e-8, 1e-8) == (False, 0.1)
+    assert oracle.ctrl_double_halve(0.2, 1e-8, 1e-8) == (True, 0.4)
+    acc, tn = oracle.ctrl_formula(1.0, 1e-8 / 16.0, 1e-8, p=4)
+    assert acc and abs(tn - 0.25 * 2.0) < 1e-15        # s (tol/err)^(1/p) = 1/4 * 16^(1/4)
+    acc, tn = oracle.ctrl_formula(1.0, 4e-8, 1e-8, p=2)
+    assert (not acc) and abs(tn - 0.125) < 1e-15         # 1/4 * (1/4)^(1/2)
+
+
+# ---------------------------------------------------------------------------
+# Whole trajectories
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme,tol", [("rk2", 1e-9), ("rk4", 1e-10), ("rkf45", 1e-10)])
+def test_integrate_constant_kernel_closed_form(scheme, tol):
+    """K = 1, lambda = 0, monodisperse start: the adaptive integrator tracks the exact
+    solution; M = 128 keeps the truncation below 1e-19 up to t = 3."""
+    M, t1 = 128, 3.0
+    U, V = kernel_factors("const", M)
+    sysm = oracle.System(M, 0.0, U=U, V=V, route="lowrank")
+    n, st, _ = oracle.integrate(sysm, monodisperse(M), 0.0, t1, tol, oracle.Options(scheme=scheme))
+    assert st["status"] == oracle.OK and st["t"] == t1
+    ref = closed_form(M, t1)
+    err = np.linalg.norm(n - ref)
+    assert err <= 200 * tol * max(1.0, st["accepted"]) ** 0.5, (err, st)
+    assert st["rhs_evals_paper"] % oracle.STAGES[scheme] == 0
+
+
+def test_integrate_stats_conventions():
+    M = 64
+    U, V = kernel_factors("brownian", M, a=0.3)
+    sysm = oracle.System(M, 0.01, U=U, V=V, route="direct")
+    n, st, log = oracle.integrate(sysm, monodisperse(M), 0.0, 2.0, 1e-8,
+                                  oracle.Options(scheme="rkf45", log=True))
+    assert st["status"] == oracle.OK and st["t"] == 2.0
+    assert st["accepted"] + st["rejected"] == len(log)
+    assert st["rhs_evals_paper"] == 6 * len(log)
+    assert st["rhs_evals"] == 6 * len(log)
+    # a fixed-step replay of the accepted steps reproduces the trajectory bit for bit
+    taus = [h for (_, h, _, acc) in log if acc]
+    m = monodisperse(M)
+    for h in taus:
+        m, _ = oracle.rkf45_step(sysm, m, h)
+    assert np.array_equal(m, n)
+
+
+def test_integrate_status_codes():
+    M = 32
+    U, V = kernel_factors("brownian", M, a=0.3)
+    sysm = oracle.System(M, 0.01, U=U, V=V)
+    n0 = monodisperse(M)
+    _, st, _ = oracle.integrate(sysm, n0, 0.0, 10.0, 1e-300, oracle.Options(scheme="rkf45"))
+    assert st["status"] == oracle.ESTEP_UNDERFLOW
+    _, st, _ = oracle.integrate(sysm, n0, 0.0, 10.0, 1e-8, oracle.Options(scheme="rkf45", max_attempts=3))
+    assert st["status"] == oracle.EMAXATTEMPTS and st["accepted"] + st["rejected"] == 3
+    bad = n0.copy()
+    bad[3] = np.nan
+    _, st, _ = oracle.integrate(sysm, bad, 0.0, 10.0, 1e-8, oracle.Options(scheme="rk2", tau0=0.01))
+    assert st["status"] == oracle.ENONFINITE
+
+
+def test_steady_tail_constant_kernel_shattering():
+    """Sec. 3.2: with K = 1 and shattering, the stationary distribution decays like
+    k^{-3/2} exp(-lambda^2 k). With lambda = 1 and M = 64 the truncation flux is small,
+    so the run must stop on the residual test ||S(n)||_2 / ||n||_2 < 1e-8 before t = 1e4
+    with mass sum_s s n_s still within 1e-4 of 1."""
+    M, lam = 64, 1.0
+    U, V = kernel_factors("const", M)
+    sysm = oracle.System(M, lam, U=U, V=V, route="lowrank")
+    n, st, _ = oracle.integrate(sysm, monodisperse(M), 0.0, 1e4, 1e-9,
+                                oracle.Options(scheme="rkf45", steady_rtol=1e-8))
+    assert st["status"] == oracle.STEADY and st["t"] < 1e4
+    S = sysm.rhs(n)
+    assert np.linalg.norm(S) / np.linalg.norm(n) < 1e-8
+    assert abs(oracle.total_mass(n) - 1.0) < 1e-4
