@@ -283,6 +283,20 @@ def test_integrate_stats_conventions():
     assert np.array_equal(m, n)
 
 
+@pytest.mark.parametrize("scheme,opts", [("rk2", {}), ("rk4", {}), ("rkf45", {}), ("rk4", {"fixed_tau": 0.05})])
+def test_rhs_eval_counts_match_calls(scheme, opts):
+    """rhs_evals counts the calls of S actually made (step doubling shares S(n^k));
+    rhs_evals_paper counts stages x RK steps evaluated, the tables' convention."""
+    M = 32
+    U, V = kernel_factors("brownian", M, a=0.3)
+    sysm = oracle.System(M, 0.01, U=U, V=V)
+    _, st, log = oracle.integrate(sysm, monodisperse(M), 0.0, 1.0, 1e-8,
+                                  oracle.Options(scheme=scheme, tau0=0.05, log=True, **opts))
+    assert st["rhs_evals"] == sysm.evals
+    per = oracle.STAGES[scheme] * (1 if (scheme == "rkf45" or opts) else 3)
+    assert st["rhs_evals_paper"] == per * len(log)
+
+
 def test_integrate_status_codes():
     M = 32
     U, V = kernel_factors("brownian", M, a=0.3)
