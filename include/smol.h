@@ -1,0 +1,186 @@
+/*
+ * smol.h - C interface of the GB300 (sm_103a) solver for the truncated
+ * aggregation-shattering Smoluchowski system with a low-rank kernel.
+ *
+ * What is computed (Matveev, Zhilin, Smirnov, "Adaptive time-stepping for
+ * aggregation-shattering kinetics", arXiv 2407.16559):
+ *
+ *   Eq. (4), sizes s = 1..M (stored 0-based, n[s-1] = n_s):
+ *     dn_1/dt = - n_1 sum_{i=1}^{M} K_{1,i} n_i
+ *               + (lambda/2) sum_{i>=2} sum_{j>=2} (i+j) K_{i,j} n_i n_j
+ *               + lambda n_1 sum_{j>=2} j K_{1,j} n_j
+ *     dn_s/dt = 1/2 sum_{i+j=s} K_{i,j} n_i n_j - (1+lambda) n_s sum_{i=1}^{M} K_{s,i} n_i,
+ *               s = 2..M.
+ *   The last monomer term is read with the factor n_1 (every collision term is
+ *   quadratic in n, and only then does shattering conserve mass).
+ *   Births above M are dropped; death sums run to M (Eq. (2)).
+ *
+ *   Low-rank kernel (Sec. 1): K_{i,j} = sum_{alpha=1}^{R} U_{i,alpha} V_{alpha,j}.
+ *   The birth term is evaluated as 1/2 sum_alpha (U_alpha . n) * (V_alpha . n), a
+ *   linear convolution computed with zero-padded FFTs, and the death and monomer
+ *   terms from rank-R moment sums, O(M R log M) per evaluation (Sec. 1, Sec. 2).
+ *
+ *   Operator form (Eq. (5)): dn/dt = S(n), n(0) = n_0, integrated with the explicit
+ *   RK2, RK4 and Runge-Kutta-Fehlberg 4(5) schemes of Sec. 2 with adaptive steps:
+ *   step doubling for RK2 / RK4 (error ||n_hat - n||_2, Eq. (6) or the halve/double
+ *   rule) and Fehlberg's rule for RKF45 (tau <- 0.9 tau (tol/err)^(1/5)).
+ *
+ * Conventions for every call:
+ *   - 0 (SMOL_OK) is success; errors are negative SMOL_E* codes; smol_strerror()
+ *     names them. A call that fails leaves the caller's buffers unspecified but
+ *     valid; the system object stays usable unless SMOL_ECUDA was returned.
+ *   - Device pointers ("d_") point to memory of the current CUDA device, 16-byte
+ *     aligned, owned by the caller. Host pointers ("h_") are plain host memory.
+ *   - Work is enqueued on the stream given in smol_opts.stream (NULL = legacy
+ *     default stream). smol_rhs returns without synchronising; smol_integrate
+ *     synchronises that stream once before it returns.
+ *   - The library never allocates device memory: every device buffer it uses lives
+ *     in the caller's workspace (smol_workspace_bytes) or is a caller argument.
+ *     It allocates a small pinned host block per system for status read-back.
+ */
+#ifndef SMOL_H
+#define SMOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SMOL_OK                0   /* success; integrate reached t1 */
+#define SMOL_STEADY            1   /* integrate stopped: ||S(n)||_2 / ||n||_2 < steady_rtol */
+#define SMOL_EINVAL           -1   /* bad argument (M < 1, R outside 1..8, NULL, t1 < t0, tol <= 0, ...) */
+#define SMOL_ECUDA            -2   /* a CUDA runtime call failed */
+#define SMOL_ENONFINITE       -3   /* NaN or Inf in the error estimate or the candidate state */
+#define SMOL_ESTEP_UNDERFLOW  -4   /* step fell below tau_min_rel * max(1, |t|) */
+#define SMOL_EMAXATTEMPTS     -5   /* max_attempts step attempts used before t1 */
+#define SMOL_ETIMEOUT         -6   /* a bounded device wait gave up */
+#define SMOL_ENOSPACE         -7   /* workspace smaller than smol_workspace_bytes() */
+#define SMOL_EUNSUPPORTED     -8   /* shape beyond what the kernels support (see smol_max_m) */
+
+/* Schemes of Sec. 2. */
+#define SMOL_RK2    0
+#define SMOL_RK4    1
+#define SMOL_RKF45  2
+
+/* Arithmetic of the birth-term convolution.
+ *   SMOL_FP64:     everything in FP64 (the plain solver).
+ *   SMOL_FP32CONV: FFTs, spectral products and the inverse in FP32 with each
+ *                  transform's input scaled by a power of two; state, moments,
+ *                  death and shattering terms, RK combination, error and step
+ *                  control stay FP64. */
+#define SMOL_FP64      0
+#define SMOL_FP32CONV  1
+
+/* Step rule for RK2 / RK4 with step doubling (Sec. 2).
+ *   SMOL_CTRL_DOUBLE_HALVE: err > tol -> reject, tau /= 2; else accept, tau *= 2.
+ *   SMOL_CTRL_FORMULA:      Eq. (6) tau_new = s tau (tol/err)^(1/p), s = 1/4,
+ *                           accept iff err <= tol, factor clamped to [fac_min, fac_max]. */
+#define SMOL_CTRL_DOUBLE_HALVE 0
+#define SMOL_CTRL_FORMULA      1
+
+/* Error norm: absolute ||.||_2 over all M entries, or divided by ||n^k||_2. */
+#define SMOL_NORM_ABS 0
+#define SMOL_NORM_REL 1
+
+typedef struct smol_system smol_system;   /* opaque, created by smol_init_system */
+
+typedef struct smol_opts {
+    int32_t precision;      /* SMOL_FP64 | SMOL_FP32CONV */
+    int32_t ctrl;           /* SMOL_CTRL_* (RK2 / RK4 only) */
+    int32_t norm;           /* SMOL_NORM_* */
+    int32_t log_capacity;   /* attempts kept in the device step log (ring); 0 = no log */
+    double  tau0;           /* first step; <= 0: Euler criterion of Sec. 1 with a = euler_a */
+    double  euler_a;        /* a of tau <= a [max_i sum_j K_ij n_j]^{-1}; default 0.1 */
+    double  tau_min_rel;    /* SMOL_ESTEP_UNDERFLOW below tau_min_rel * max(1,|t|); default 1e-12 */
+    double  steady_rtol;    /* > 0: stop with SMOL_STEADY when ||S(n)||_2/||n||_2 < steady_rtol */
+    double  fixed_tau;      /* > 0: constant steps of this size, no error control */
+    double  fac_min;        /* bounds of the step factor; defaults 0.1 and 4 */
+    double  fac_max;
+    int64_t max_attempts;   /* default 2^62 */
+    int32_t chunk;          /* step attempts per CUDA-graph launch; default 32 */
+    int32_t reserved;
+    void*   stream;         /* cudaStream_t; NULL = legacy default stream */
+} smol_opts;
+
+typedef struct smol_stats {
+    double  t;               /* time reached */
+    double  tau_next;        /* proposed next step (resume with tau0 = tau_next) */
+    double  err_last;        /* error estimate of the last attempt */
+    int64_t rhs_evals;       /* S(n) evaluations actually made */
+    int64_t rhs_evals_paper; /* stages x RK steps evaluated, the count of the paper's tables */
+    int64_t accepted;
+    int64_t rejected;
+    int64_t attempts;
+    int32_t status;          /* SMOL_OK, SMOL_STEADY or a negative code */
+    int32_t reserved;
+} smol_stats;
+
+/* Fills *opts with the defaults listed above. Never fails for a non-NULL pointer. */
+void smol_default_opts(smol_opts* opts);
+
+/* Largest M the kernels accept for rank R and precision, or 0 if R is unsupported. */
+int64_t smol_max_m(int32_t R, int32_t precision);
+
+/* Bytes of device workspace a system of size M, rank R needs under opts (NULL =
+ * defaults). The workspace must stay allocated, untouched by the caller and
+ * unused by other systems until smol_destroy. Returns 0 for an unsupported shape. */
+size_t smol_workspace_bytes(int64_t M, int32_t R, const smol_opts* opts);
+
+/* Creates a system for Eq. (4) with kernel K = U V and shattering rate lambda.
+ *   h_U: host, M x R row-major (U[(s-1)*R + alpha] = U_{s,alpha}); copied.
+ *   h_V: host, R x M row-major (V[alpha*M + (s-1)] = V_{alpha,s});  copied.
+ *   lambda >= 0. opts may be NULL (defaults); it is copied.
+ *   d_workspace: device, >= smol_workspace_bytes(M, R, opts) bytes, 256-byte aligned.
+ * Columns of U and rows of V that are equal up to a constant factor share one
+ * forward transform. Synchronises the stream once (tables are uploaded).
+ * Errors: SMOL_EINVAL, SMOL_ENOSPACE, SMOL_EUNSUPPORTED, SMOL_ECUDA. */
+int smol_init_system(smol_system** sys, int64_t M, int32_t R, const double* h_U,
+                     const double* h_V, double lambda, const smol_opts* opts,
+                     void* d_workspace, size_t workspace_bytes);
+
+/* Re-targets the stream of later calls. */
+int smol_set_stream(smol_system* sys, void* stream);
+
+/* out = S(n), Eq. (4)-(5), FP64 in and out (d_n and d_out: device, M doubles each;
+ * they may not overlap). Stream-ordered; does not synchronise. */
+int smol_rhs(smol_system* sys, const double* d_n, double* d_out);
+
+/* The terms of S(n) separately (device, M doubles each; any may be NULL):
+ *   d_birth[s-1] = 1/2 sum_{i+j=s} K_ij n_i n_j          (0 for s = 1)
+ *   d_loss[s-1]  = (1 + lambda [s>=2]) n_s sum_i K_si n_i (aggregation + shattering loss)
+ *   d_source[0]  = monomer source from shattering (a single double)
+ * so that S = birth - loss, plus source at s = 1. */
+int smol_rhs_terms(smol_system* sys, const double* d_n, double* d_birth, double* d_loss,
+                   double* d_source);
+
+/* Integrates Eq. (5) from t0 to t1 with the given scheme (SMOL_RK2 / SMOL_RK4 /
+ * SMOL_RKF45) and tolerance tol (> 0), starting from d_n (device, M doubles), and
+ * writes n(t_end) back to d_n. Step control runs on the device; the host launches
+ * captured CUDA graphs of opts.chunk attempts and reads a status block between
+ * launches. Returns the final status (SMOL_OK or SMOL_STEADY on success) and fills
+ * *stats when non-NULL. */
+int smol_integrate(smol_system* sys, double* d_n, double t0, double t1, double tol,
+                   int32_t scheme, smol_stats* stats);
+
+/* Copies the step log of the last smol_integrate (the most recent min(count, cap)
+ * attempts, oldest first) to host arrays of cap entries each (any may be NULL).
+ * *count receives the number of attempts made. */
+int smol_get_log(smol_system* sys, double* h_t, double* h_tau, double* h_err,
+                 int32_t* h_accepted, int32_t cap, int64_t* count);
+
+/* Number of distinct forward transforms T used per evaluation (<= 2R). */
+int smol_num_transforms(const smol_system* sys);
+
+/* Releases the system (not the workspace). Safe on NULL. */
+void smol_destroy(smol_system* sys);
+
+/* Static description of a status code. */
+const char* smol_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMOL_H */

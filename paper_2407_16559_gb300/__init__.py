@@ -1,0 +1,231 @@
+"""GB300 (sm_103a) solver for the truncated aggregation-shattering Smoluchowski system
+with a low-rank kernel, after Matveev, Zhilin, Smirnov, "Adaptive time-stepping for
+aggregation-shattering kinetics" (arXiv 2407.16559).
+
+This module is a thin ctypes binding of the C interface in ``include/smol.h``: it only
+marshals arguments. Every step of the computation (right-hand side of Eq. (4), RK
+stages, error norms, step control) runs in the CUDA kernels of ``libsmol.so``.
+PyTorch provides the device memory (workspace, state vectors) and the stream.
+There is no CPU fallback: importing this package fails if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsmol.so")
+
+OK, STEADY = 0, 1
+EINVAL, ECUDA, ENONFINITE, ESTEP_UNDERFLOW, EMAXATTEMPTS, ETIMEOUT, ENOSPACE, EUNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
+SCHEMES = {"rk2": 0, "rk4": 1, "rkf45": 2}
+PRECISIONS = {"fp64": 0, "fp32conv": 1}
+CTRLS = {"double_halve": 0, "formula": 1}
+NORMS = {"abs": 0, "rel": 1}
+
+
+class SmolError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32), ("ctrl", ctypes.c_int32), ("norm", ctypes.c_int32),
+        ("log_capacity", ctypes.c_int32), ("tau0", ctypes.c_double), ("euler_a", ctypes.c_double),
+        ("tau_min_rel", ctypes.c_double), ("steady_rtol", ctypes.c_double), ("fixed_tau", ctypes.c_double),
+        ("fac_min", ctypes.c_double), ("fac_max", ctypes.c_double), ("max_attempts", ctypes.c_int64),
+        ("chunk", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("tau_next", ctypes.c_double), ("err_last", ctypes.c_double),
+        ("rhs_evals", ctypes.c_int64), ("rhs_evals_paper", ctypes.c_int64), ("accepted", ctypes.c_int64),
+        ("rejected", ctypes.c_int64), ("attempts", ctypes.c_int64), ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_P, _D, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+
+# name -> (restype, argtypes); the exported symbols of include/smol.h
+SIGNATURES = {
+    "smol_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "smol_max_m": (_I64, [_I32, _I32]),
+    "smol_workspace_bytes": (_SZ, [_I64, _I32, ctypes.POINTER(Opts)]),
+    "smol_init_system": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I32, _P, _P, _D, ctypes.POINTER(Opts), _P, _SZ]),
+    "smol_set_stream": (ctypes.c_int, [_P, _P]),
+    "smol_rhs": (ctypes.c_int, [_P, _P, _P]),
+    "smol_rhs_terms": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "smol_integrate": (ctypes.c_int, [_P, _P, _D, _D, _D, _I32, ctypes.POINTER(Stats)]),
+    "smol_get_log": (ctypes.c_int, [_P, _P, _P, _P, _P, _I32, ctypes.POINTER(_I64)]),
+    "smol_num_transforms": (ctypes.c_int, [_P]),
+    "smol_destroy": (None, [_P]),
+    "smol_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libsmol.so not built at {path}; run `python paper_2407_16559_gb300/build.py` "
+                          "(needs nvcc; the kernels are the only implementation, there is no fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def strerror(code: int) -> str:
+    return _lib.smol_strerror(int(code)).decode()
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    _lib.smol_default_opts(ctypes.byref(o))
+    return o
+
+
+def max_m(R: int, precision: str = "fp64") -> int:
+    return int(_lib.smol_max_m(R, PRECISIONS[precision]))
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        raise SmolError(rc, what)
+    return rc
+
+
+def _torch():
+    import torch  # imported lazily: the CPU-only symbol tests need no torch
+    return torch
+
+
+class System:
+    """One system of Eq. (4) with kernel K = U V on the current CUDA device.
+
+    U: (M, R) and V: (R, M) float64 arrays (host; copied). lam: shattering rate.
+    Options map to the fields of smol_opts (precision 'fp64' | 'fp32conv', ctrl
+    'double_halve' | 'formula', norm 'abs' | 'rel', tau0, euler_a, tau_min_rel,
+    steady_rtol, fixed_tau, fac_min, fac_max, max_attempts, chunk, log_capacity).
+    The workspace is a torch uint8 tensor owned by this object.
+    """
+
+    def __init__(self, U, V, lam: float, precision: str = "fp64", stream=None, device=None, **opts):
+        torch = _torch()
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        if U.ndim != 2 or V.ndim != 2 or V.shape != (U.shape[1], U.shape[0]):
+            raise ValueError("U must be (M, R) and V (R, M)")
+        self.M, self.R = U.shape
+        self.lam = float(lam)
+        self.device = torch.device(device if device is not None else "cuda")
+        self.opts = default_opts()
+        self.opts.precision = PRECISIONS[precision]
+        for k, v in opts.items():
+            if k == "ctrl":
+                v = CTRLS[v]
+            elif k == "norm":
+                v = NORMS[v]
+            if not hasattr(self.opts, k):
+                raise TypeError(f"unknown option {k!r}")
+            setattr(self.opts, k, v)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self.opts.stream = ctypes.c_void_p(stream.cuda_stream)
+        nbytes = int(_lib.smol_workspace_bytes(self.M, self.R, ctypes.byref(self.opts)))
+        if nbytes == 0:
+            raise SmolError(EUNSUPPORTED, f"M={self.M}, R={self.R}")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self._h = ctypes.c_void_p()
+        self._U, self._V = U, V
+        _check(_lib.smol_init_system(ctypes.byref(self._h), self.M, self.R, U.ctypes.data, V.ctypes.data,
+                                     self.lam, ctypes.byref(self.opts), self._ws_ptr, nbytes), "smol_init_system")
+
+    # -- helpers -------------------------------------------------------------
+    def _vec(self, n):
+        torch = _torch()
+        if not isinstance(n, torch.Tensor):
+            n = torch.as_tensor(np.asarray(n, dtype=np.float64))
+        n = n.to(device=self.device, dtype=torch.float64).contiguous()
+        if n.numel() != self.M:
+            raise ValueError(f"state has {n.numel()} entries, expected M={self.M}")
+        return n
+
+    @property
+    def num_transforms(self) -> int:
+        return int(_lib.smol_num_transforms(self._h))
+
+    # -- C interface ------------------------------------------------------------
+    def rhs(self, n, out=None):
+        """S(n) of Eq. (4) (device tensor of M doubles)."""
+        torch = _torch()
+        n = self._vec(n)
+        if out is None:
+            out = torch.empty_like(n)
+        _check(_lib.smol_rhs(self._h, n.data_ptr(), out.data_ptr()), "smol_rhs")
+        return out
+
+    def rhs_terms(self, n):
+        """(birth, loss, source): S = birth - loss, plus source at s = 1."""
+        torch = _torch()
+        n = self._vec(n)
+        birth, loss = torch.empty_like(n), torch.empty_like(n)
+        src = torch.empty(1, dtype=torch.float64, device=self.device)
+        _check(_lib.smol_rhs_terms(self._h, n.data_ptr(), birth.data_ptr(), loss.data_ptr(), src.data_ptr()),
+               "smol_rhs_terms")
+        return birth, loss, src
+
+    def integrate(self, n0, t0: float, t1: float, tol: float, scheme: str = "rkf45", inplace: bool = False):
+        """Integrates from t0 to t1; returns (n(t_end) device tensor, stats dict).
+        Negative statuses (errors) are returned in stats, not raised, so that the caller
+        can inspect the state reached; SMOL_EINVAL / SMOL_ECUDA raise."""
+        n = self._vec(n0)
+        if not inplace:
+            n = n.clone()
+        st = Stats()
+        rc = _lib.smol_integrate(self._h, n.data_ptr(), float(t0), float(t1), float(tol), SCHEMES[scheme],
+                                 ctypes.byref(st))
+        if rc in (EINVAL, ECUDA, ENOSPACE, EUNSUPPORTED):
+            raise SmolError(rc, "smol_integrate")
+        return n, st.as_dict()
+
+    def get_log(self, cap: int | None = None):
+        """Step log of the last integrate: arrays t, tau, err, accepted (oldest first)."""
+        cnt = ctypes.c_int64()
+        cap = int(cap if cap is not None else self.opts.log_capacity)
+        t = np.zeros(cap)
+        h = np.zeros(cap)
+        e = np.zeros(cap)
+        a = np.zeros(cap, dtype=np.int32)
+        _check(_lib.smol_get_log(self._h, t.ctypes.data, h.ctypes.data, e.ctypes.data, a.ctypes.data, cap,
+                                 ctypes.byref(cnt)), "smol_get_log")
+        k = min(cnt.value, cap, max(self.opts.log_capacity, 0))
+        return t[:k], h[:k], e[:k], a[:k].astype(bool), cnt.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.smol_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,155 @@
+"""Parity of the device-resident adaptive integrators (Sec. 2) with the FP64 oracle.
+
+Modes:
+  * constant steps (fixed_tau): the same arithmetic step by step, so the states agree
+    to the RHS tolerance times the number of steps;
+  * free-running adaptive runs on the relaxation problem: both sides take the same
+    accept / reject decisions (counts equal) and the states agree far below tol;
+  * the closed-form constant-kernel solution;
+  * error statuses (non-finite state, step underflow, attempt limit) and the steady stop.
+The error estimate of one attempt is compared at 1e-6 relative: it is a difference of
+two O(1) states of size ~tol, so the 1e-13 normwise RHS difference (FFT vs direct sums)
+is amplified by ||n|| / err.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import kernel_factors, monodisperse, sample_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def smol():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_16559_gb300 as m
+    return m
+
+
+def run_both(smol, M, kind, a, lam, t1, tol, scheme, n0=None, route="lowrank", **opts):
+    import torch
+    U, V = kernel_factors(kind, M, a=a)
+    n0 = monodisperse(M) if n0 is None else n0
+    gopts = {k: v for k, v in opts.items() if k not in ("log",)}
+    sysm = smol.System(U, V, lam, log_capacity=4096, **gopts)
+    n, st = sysm.integrate(torch.from_numpy(n0).cuda(), 0.0, t1, tol, scheme=scheme)
+    osys = oracle.System(M, lam, U=U, V=V, route=route)
+    oo = oracle.Options(scheme=scheme, log=True, **{k: v for k, v in opts.items() if k in oracle.Options.__dataclass_fields__})
+    m, ost, olog = oracle.integrate(osys, n0, 0.0, t1, tol, oo)
+    return n.cpu().numpy(), st, m, ost, olog, sysm
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk4", "rkf45"])
+def test_fixed_step_parity(smol, scheme):
+    M = 512
+    n, st, m, ost, _, _ = run_both(smol, M, "brownian", 0.3, 0.01, 5.0, 1e-8, scheme, fixed_tau=0.01)
+    assert st["status"] == 0 and ost["status"] == 0
+    assert st["accepted"] == ost["accepted"] and st["accepted"] in (500, 501)
+    assert st["rhs_evals_paper"] == ost["rhs_evals_paper"]
+    assert np.linalg.norm(n - m) <= 1e-11 * np.linalg.norm(m) * 500 ** 0.5
+
+
+@pytest.mark.parametrize("scheme,ctrl", [("rk2", "double_halve"), ("rk2", "formula"), ("rk4", "double_halve"),
+                                         ("rk4", "formula"), ("rkf45", "double_halve")])
+def test_adaptive_parity_relaxation(smol, scheme, ctrl):
+    """The shattering workload at M = 512 (kernel (i/j)^0.3 + (j/i)^0.3, lambda = 0.01,
+    monodisperse start) on t in [0, 20]."""
+    M = 512
+    n, st, m, ost, olog, sysm = run_both(smol, M, "brownian", 0.3, 0.01, 20.0, 1e-8, scheme, ctrl=ctrl, tau0=0.01)
+    assert st["status"] == ost["status"] == 0
+    assert st["t"] == ost["t"] == 20.0
+    assert (st["accepted"], st["rejected"]) == (ost["accepted"], ost["rejected"]), (st, ost)
+    assert st["rhs_evals"] == ost["rhs_evals"] and st["rhs_evals_paper"] == ost["rhs_evals_paper"]
+    assert np.linalg.norm(n - m) <= 1e-9 * np.linalg.norm(m), np.linalg.norm(n - m) / np.linalg.norm(m)
+    # step log: same decisions and step sizes
+    t, h, e, acc, cnt = sysm.get_log()
+    assert cnt == len(olog)
+    k = len(t)
+    oh = np.array([x[1] for x in olog])[-k:]
+    oe = np.array([x[2] for x in olog])[-k:]
+    oa = np.array([x[3] for x in olog])[-k:]
+    assert np.array_equal(acc, oa)
+    assert np.allclose(h, oh, rtol=1e-7, atol=0)
+    assert np.allclose(e, oe, rtol=1e-5, atol=1e-18)
+
+
+def test_euler_initial_step(smol):
+    """No tau0: the Euler criterion tau0 = a / max_i sum_j K_ij n_j (a = 1/10)."""
+    M = 256
+    n, st, m, ost, olog, sysm = run_both(smol, M, "brownian", 0.3, 0.01, 1.0, 1e-8, "rkf45")
+    t, h, *_ = sysm.get_log()
+    assert abs(h[0] - olog[0][1]) <= 1e-14 * olog[0][1]
+    assert (st["accepted"], st["rejected"]) == (ost["accepted"], ost["rejected"])
+
+
+@pytest.mark.parametrize("scheme,tol", [("rk2", 1e-9), ("rk4", 1e-10), ("rkf45", 1e-10)])
+def test_closed_form_constant_kernel(smol, scheme, tol):
+    import torch
+    M, t1 = 128, 3.0
+    U, V = kernel_factors("const", M)
+    sysm = smol.System(U, V, 0.0)
+    n, st = sysm.integrate(torch.from_numpy(monodisperse(M)).cuda(), 0.0, t1, tol, scheme=scheme)
+    s = np.arange(1, M + 1, dtype=np.float64)
+    ref = (t1 / 2) ** (s - 1) / (1 + t1 / 2) ** (s + 1)
+    assert st["status"] == 0
+    assert np.linalg.norm(n.cpu().numpy() - ref) <= 200 * tol * max(1, st["accepted"]) ** 0.5
+
+
+def test_statuses(smol):
+    import torch
+    M = 64
+    U, V = kernel_factors("brownian", M, a=0.3)
+    n0 = torch.from_numpy(monodisperse(M)).cuda()
+    s = smol.System(U, V, 0.01)
+    _, st = s.integrate(n0, 0.0, 10.0, 1e-300, scheme="rkf45")
+    assert st["status"] == smol.ESTEP_UNDERFLOW
+    s = smol.System(U, V, 0.01, max_attempts=3)
+    _, st = s.integrate(n0, 0.0, 10.0, 1e-8, scheme="rkf45")
+    assert st["status"] == smol.EMAXATTEMPTS and st["attempts"] == 3
+    bad = monodisperse(M)
+    bad[3] = np.nan
+    s = smol.System(U, V, 0.01, tau0=0.01)
+    _, st = s.integrate(torch.from_numpy(bad).cuda(), 0.0, 10.0, 1e-8, scheme="rk2")
+    assert st["status"] == smol.ENONFINITE
+    # t1 == t0: nothing to do
+    n, st = s.integrate(n0, 1.0, 1.0, 1e-8)
+    assert st["status"] == 0 and st["attempts"] == 0 and torch.equal(n, n0)
+
+
+def test_steady_stop(smol):
+    M, lam = 64, 1.0
+    n, st, m, ost, _, _ = run_both(smol, M, "const", 0.0, lam, 1e4, 1e-9, "rkf45", steady_rtol=1e-8, tau0=0.01)
+    assert st["status"] == ost["status"] == smol.STEADY
+    assert abs(st["t"] - ost["t"]) <= 1e-6 * ost["t"]
+    assert np.linalg.norm(n - m) <= 1e-7 * np.linalg.norm(m)
+
+
+def test_resume_equals_single_run(smol):
+    """Checkpoint / resume: a run split at t = 1 with tau0 = tau_next continues the
+    same step sequence."""
+    import torch
+    M = 256
+    U, V = kernel_factors("brownian", M, a=0.3)
+    s = smol.System(U, V, 0.01, tau0=0.01)
+    n0 = torch.from_numpy(monodisperse(M)).cuda()
+    full, st = s.integrate(n0, 0.0, 2.0, 1e-8)
+    half, st1 = s.integrate(n0, 0.0, 1.0, 1e-8)
+    s2 = smol.System(U, V, 0.01, tau0=st1["tau_next"])
+    rest, st2 = s2.integrate(half, st1["t"], 2.0, 1e-8)
+    assert st2["status"] == 0
+    assert torch.allclose(rest, full, rtol=0, atol=1e-8 * float(full.norm()))
+
+
+def test_fp32conv_integrate_accuracy(smol):
+    """FP32 convolutions with FP64 control on the relaxation workload: the state stays
+    within 1e-5 relative of the FP64 oracle and the mass balance holds."""
+    M = 4096
+    n, st, m, ost, _, _ = run_both(smol, M, "brownian_const", 1 / 3, 0.1, 10.0, 1e-8, "rkf45",
+                                   precision="fp32conv", tau0=0.01)
+    assert st["status"] == 0 and ost["status"] == 0
+    assert np.linalg.norm(n - m) <= 1e-5 * np.linalg.norm(m)

@@ -1,0 +1,162 @@
+"""Parity of the CUDA right-hand side of Eq. (4) with the FP64 oracle.
+
+Tolerances are normwise: an FFT's rounding error is bounded relative to the norm of
+the convolution, not entrywise, so the small tail entries carry an absolute error of
+order eps * ||birth||. Each term is checked as
+    ||x - x_ref||_2 <= rtol ||x_ref||_2  and  ||x - x_ref||_inf <= rtol ||x_ref||_inf,
+and the total S, whose terms cancel near a steady state, against the scale
+|| |birth| + |loss| + |source| ||. rtol = 1e-10 for FP64, 1e-4 for the FP32
+convolution form (FP32 FFT error ~ 1e-7 log2(M) relative).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import kernel_factors, random_factors, random_state, sample_state
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {"fp64": 1e-10, "fp32conv": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def smol():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_16559_gb300 as m
+    return m
+
+
+def _ref_terms(n, U, V, lam, route):
+    if route == "direct":
+        d = oracle.rhs_terms_direct(n, U @ V, lam)
+    else:
+        d = oracle.rhs_terms_lowrank(n, U, V, lam)
+    loss = d["death"] + d["shatter_loss"]
+    return d["birth"], loss, float(d["monomer_source"][0]), d["total"]
+
+
+def _close(x, ref, rtol, scale=None, what=""):
+    x = np.asarray(x)
+    ref = np.asarray(ref)
+    s2 = np.linalg.norm(ref) if scale is None else np.linalg.norm(scale)
+    si = np.max(np.abs(ref)) if scale is None else np.max(np.abs(scale))
+    e2 = np.linalg.norm(x - ref)
+    ei = np.max(np.abs(x - ref)) if x.size else 0.0
+    assert e2 <= rtol * s2 + 1e-300, f"{what}: l2 {e2:.3e} > {rtol:.0e} * {s2:.3e}"
+    assert ei <= rtol * si + 1e-300, f"{what}: linf {ei:.3e} > {rtol:.0e} * {si:.3e}"
+
+
+def check_rhs(smol, n, U, V, lam, precision="fp64", route=None):
+    import torch
+    M = n.size
+    if route is None:
+        route = "direct" if M <= 2048 else "lowrank"
+    sysm = smol.System(U, V, lam, precision=precision)
+    dn = torch.from_numpy(n).cuda()
+    S = sysm.rhs(dn).cpu().numpy()
+    b, l, src = (t.cpu().numpy() for t in sysm.rhs_terms(dn))
+    rb, rl, rsrc, rS = _ref_terms(n, U, V, lam, route)
+    rtol = RTOL[precision]
+    _close(b, rb, rtol, what="birth")
+    _close(l, rl, rtol, what="loss")
+    assert abs(src[0] - rsrc) <= rtol * (abs(rsrc) + np.max(np.abs(rl)) * 1e-3 + 1e-300), (src[0], rsrc)
+    scale = np.abs(rb) + np.abs(rl)
+    scale[0] += abs(rsrc)
+    _close(S, rS, rtol, scale=scale, what="total")
+    return sysm
+
+
+KERNELS = [("const", 0.0), ("brownian", 0.3), ("brownian", 0.9), ("brownian_const", 1.0 / 3.0)]
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5, 8, 17, 64, 100, 257, 1000, 1024, 2048])
+@pytest.mark.parametrize("kind,a", KERNELS)
+def test_rhs_small_sizes(smol, M, kind, a):
+    """Several tiles and ragged tails; M not a power of two is zero-padded to Mp."""
+    U, V = kernel_factors(kind, M, a=a)
+    n = random_state(M, seed=M + 3)
+    check_rhs(smol, n, U, V, 0.01)
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.005, 0.1, 1.0])
+def test_rhs_lambda(smol, lam):
+    M = 777
+    U, V = kernel_factors("brownian", M, a=0.9)
+    check_rhs(smol, sample_state(M, lam), U, V, lam)
+
+
+@pytest.mark.parametrize("M,R", [(50, 1), (300, 3), (1500, 4), (4096, 8)])
+def test_rhs_random_nonsymmetric_factors(smol, M, R):
+    """Non-symmetric factors with no shared transforms (T = 2R): a transposed U / V or
+    a wrong pairing in the spectral product fails the loss or source term."""
+    U, V = random_factors(M, R, seed=5 * M + R)
+    n = random_state(M, seed=M)
+    s = check_rhs(smol, n, U, V, 0.2)
+    assert s.num_transforms == 2 * R
+
+
+def test_transform_sharing(smol):
+    M = 128
+    for kind, a, T in (("const", 0.0, 1), ("brownian", 0.5, 2), ("brownian_const", 1 / 3, 3)):
+        U, V = kernel_factors(kind, M, a=a)
+        assert smol.System(U, V, 0.0).num_transforms == T
+
+
+@pytest.mark.parametrize("M", [4096, 8192, 16384, 65536, 65537, 131072])
+@pytest.mark.parametrize("kind,a", [("brownian", 0.9), ("brownian_const", 1.0 / 3.0)])
+def test_rhs_large_vs_lowrank_oracle(smol, M, kind, a):
+    """Up to the bench size M = 2^17: against the oracle's numpy-FFT route (itself
+    pinned to the direct sums)."""
+    U, V = kernel_factors(kind, M, a=a)
+    check_rhs(smol, sample_state(M, 0.005, seed=M), U, V, 0.005)
+
+
+def test_rhs_full_size_sampled_direct_entries(smol):
+    """M = 2^17, the size the bench times: sampled outputs against the direct O(M)
+    per-entry sums of Eq. (4), including the first and last sizes."""
+    import torch
+    M, a, lam = 131072, 0.9, 0.005
+    U, V = kernel_factors("brownian", M, a=a)
+    n = sample_state(M, lam, seed=11)
+    sysm = smol.System(U, V, lam)
+    S = sysm.rhs(torch.from_numpy(n).cuda()).cpu().numpy()
+    b, l, _ = (t.cpu().numpy() for t in sysm.rhs_terms(torch.from_numpy(n).cuda()))
+    rng = np.random.default_rng(0)
+    sizes = sorted(set([2, 3, M // 2, M - 1, M] + list(rng.integers(2, M + 1, 40))))
+    ref = oracle.rhs_entries_direct(n, lambda i, j: (i / j) ** a + (j / i) ** a, lam, sizes)
+    got = S[np.array(sizes) - 1]
+    scale = np.max(np.abs(b)) + np.abs(l[np.array(sizes) - 1])
+    assert np.all(np.abs(got - ref) <= 1e-10 * scale), np.max(np.abs(got - ref) / scale)
+
+
+@pytest.mark.parametrize("M", [64, 1000, 4096, 65536, 131072])
+@pytest.mark.parametrize("kind,a", [("brownian", 0.9), ("brownian_const", 1.0 / 3.0)])
+def test_rhs_fp32conv(smol, M, kind, a):
+    U, V = kernel_factors(kind, M, a=a)
+    check_rhs(smol, sample_state(M, 0.1, seed=M), U, V, 0.1, precision="fp32conv")
+
+
+def test_rhs_fp32conv_tiny_concentrations(smol):
+    """Per-transform power-of-two scaling keeps FP32 spectra in range when the state is
+    very dilute (1e-30) or very large (1e+30)."""
+    M = 4096
+    U, V = kernel_factors("brownian", M, a=0.6)
+    for mag in (1e-30, 1e30):
+        check_rhs(smol, sample_state(M, 0.01) * mag, U, V, 0.01, precision="fp32conv")
+
+
+def test_rhs_zero_state_and_repeat(smol):
+    import torch
+    M = 300
+    U, V = kernel_factors("brownian", M, a=0.4)
+    sysm = smol.System(U, V, 0.01)
+    z = sysm.rhs(torch.zeros(M, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.all(z == 0.0)
+    n = torch.from_numpy(random_state(M, seed=1)).cuda()
+    a1 = sysm.rhs(n).cpu().numpy()
+    a2 = sysm.rhs(n).cpu().numpy()
+    assert np.array_equal(a1, a2)  # deterministic reductions
