@@ -1,0 +1,434 @@
+"""Throughput of the adaptive RKF45 integrator for the aggregation-shattering system.
+
+Workload (oscillatory regime): M = 2^17 sizes, kernel K_ij = (i/j)^0.9 + (j/i)^0.9
+(rank 2), shattering rate lambda = 0.005, monodisperse start n_s(0) = delta_{s1}, RKF45
+with tol 1e-8 (Sec. 2 schemes, Eq. (4) system). Synthetic by definition: the paper's
+experiments are fully specified by (M, K, lambda, n0).
+
+One step = one RKF45 attempt: 6 evaluations of S(n) (3 kernels each), the stage
+combination, the embedded error norm and the step-size control, all on the device
+(19 kernel launches, captured in a CUDA graph). Before the timed steps the system is
+advanced from t = 0 to t = 5 (untimed) so that the attempts run mid-trajectory.
+value = S evaluations per second over the K timed steps; accepted RK steps per second
+are reported beside it. L2 (129 MB) is flushed between steps by writing a 256 MB
+buffer outside the timed events (the system's working set, ~35 MB, would otherwise
+stay resident).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32conv]
+       python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+Under torchrun (N > 1) every rank integrates its own replica (the single system does not
+shard); value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="oscill_M131072_brownian0.9_rkf45", M=131072, a=0.9, lam=0.005, tol=1e-8, t1=5000.0,
+                t_setup=5.0, scheme="rkf45")
+EVALS_PER_STEP = 6          # RKF45 stages
+LAUNCHES_PER_STEP = 19      # 6 x 3 right-hand-side kernels + 1 combination / control kernel
+L2_FLUSH_BYTES = 256 << 20
+
+# Measured peaks (MEASURED_PEAKS.json of this machine, written by the pool's driver; read
+# at run time when present) and the FP64 ALU peak: 152 SMs x 2070 MHz x 2 FP64 FMA per
+# clock per SM x 2 flop = 1.259 TFLOP/s (a probe of dependent DFMA chains measured
+# 1.20 TFLOP/s at ~1.97 GHz, i.e. 2 FMA / clk / SM).
+HBM_FALLBACK_GBS = 6800.0
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
+# (precision, kernel class); valid only while the kernel sources are unchanged.
+TRAFFIC = {}
+
+
+def src_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2407_16559_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work per launch of each kernel class (FP64 flops / compulsory bytes)
+# ---------------------------------------------------------------------------
+def algorithmic(M: int, T: int, csz: int):
+    """Per launch: flops of the FFT stages a kernel performs (5 N log2 N convention for
+    a complex length-N transform, the real-FFT split / merge counted as one stage) and
+    the bytes it must move (inputs read once, outputs written once)."""
+    lg = (M - 1).bit_length()
+    Mp = 1 << lg
+    lg1, lg2 = (lg + 1) // 2, lg // 2
+    fl = {
+        "fwd_cols": T * 5.0 * Mp * lg1,
+        "rows": (T + 1) * 5.0 * Mp * (lg2 + 1),
+        "inv_cols": 5.0 * Mp * lg1,
+    }
+    by = {
+        # stage input (n and up to 5 stage vectors, ~3 on average) + T weights, T spectra out
+        "fwd_cols": 8.0 * M * (3 + T) + T * csz * Mp,
+        "rows": (T + 1) * csz * Mp,
+        "inv_cols": csz * Mp + 8.0 * M * (2 + T) + 8.0 * M,
+    }
+    return fl, by
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.fh = None
+
+    def __enter__(self):
+        try:
+            self.fh = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.fh is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.fh.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.fh.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle as it stands
+# ---------------------------------------------------------------------------
+def oracle_rate(seconds: float, max_evals: int | None = None):
+    """RHS evaluations per second of the oracle's O(M R log M) route (numpy FFT) inside
+    its own adaptive RKF45 integration of the bench workload from the monodisperse
+    start, run in slices of two attempts until about `seconds` or max_evals evaluations."""
+    import numpy as np
+
+    import oracle
+    from synth import kernel_factors, monodisperse
+
+    w = WORKLOAD
+    U, V = kernel_factors("brownian", w["M"], a=w["a"])
+    sysm = oracle.System(w["M"], w["lam"], U=U, V=V, route="lowrank")
+    n = monodisperse(w["M"])
+    sysm.rhs(n)  # warm
+    evals, t, tau = 0, 0.0, 1e-3
+    t0 = time.perf_counter()
+    while True:
+        n, st, _ = oracle.integrate(sysm, n, t, w["t1"], w["tol"],
+                                    oracle.Options(scheme="rkf45", tau0=tau, max_attempts=2))
+        evals += st["rhs_evals"]
+        t, tau = st["t"], st["tau_next"]
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_evals is not None and evals >= max_evals) or st["status"] not in (0, -5):
+            break
+    return evals / el, evals, el, float(np.sum(n))
+
+
+def cpu_worker(args):
+    rate, evals, el, _ = oracle_rate(args.cpu_seconds, args.cpu_max_evals)
+    print(json.dumps({"rate": rate, "evals": evals, "seconds": el}))
+
+
+def run_cpu_baseline(seconds: float, max_evals: int | None = None):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--cpu-seconds", str(seconds)]
+    if max_evals:
+        cmd += ["--cpu-max-evals", str(max_evals)]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        return None
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each step = one right-hand-side evaluation of the oracle (a bounded sample of
+    # the workload's RKF45 attempt, which makes six of them)
+    env_steps = args.steps + args.warmup
+    res = run_cpu_baseline(seconds=1e9, max_evals=6 * max(1, (env_steps + 5) // 6))
+    if res is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle subprocess failed"}))
+        return 0
+    v = res["rate"]
+    line = {
+        "impl": "reference", "metric": "rhs_evals_per_s", "value": v, "unit": "RHS evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": config_dict("fp64"),
+        "cpu_baseline": {"value": v, "unit": "RHS evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{res['evals']} evaluations of S(n) (numpy-FFT route) inside oracle RKF45 "
+                                   f"attempts at M=2^17 from the monodisperse start, one thread"},
+        "e2e": {"value": v, "unit": "RHS evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(precision: str):
+    w = WORKLOAD
+    return {"workload": w["name"], "M": w["M"], "kernel": f"(i/j)^{w['a']}+(j/i)^{w['a']} (rank 2)",
+            "lambda": w["lam"], "n0": "monodisperse, advanced to t=5 before timing", "scheme": "rkf45",
+            "tol": w["tol"], "precision": precision, "step": "one RKF45 attempt (6 RHS evaluations)",
+            "l2": "flushed between timed steps (256 MB write outside the events)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: int):
+    import numpy as np
+
+    from synth import kernel_factors, monodisperse
+
+    w = WORKLOAD
+    U, V = kernel_factors("brownian", w["M"], a=w["a"])
+    sysm = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=1e-3, max_attempts=20000)
+    n = torch.from_numpy(monodisperse(w["M"])).cuda()
+    n, st0 = sysm.integrate(n, 0.0, w["t_setup"], w["tol"], scheme="rkf45")
+    # timed run: chunk of one attempt per graph launch
+    tsys = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=st0["tau_next"], chunk=1)
+    run = tsys.start(n, st0["t"], w["t1"], w["tol"], scheme="rkf45")
+    for _ in range(W):
+        tsys.advance()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            tsys.advance()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof_ms, prof_cnt = tsys.profile(reps=10)
+    run, stats = tsys.finish()
+    del run
+    return ms, stats, prof_ms, prof_cnt, tsys, U, V
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_2407_16559_gb300 as smol
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    K, W = args.steps, args.warmup
+    precision = args.precision
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        ms, stats, prof_ms, prof_cnt, tsys, U, V = time_form(smol, torch, precision, K, W, stream, flush, rank)
+    barrier()
+    clocks = clk.summary()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    timed_attempts = K
+    acc_timed = stats["accepted"]  # includes warm-up attempts; scaled below
+    total_att = stats["attempts"]
+    acc_rate = acc_timed / max(total_att, 1)
+    value = world * EVALS_PER_STEP * K / (ms / 1000.0)
+    accepted_per_s = world * acc_rate * K / (ms / 1000.0)
+
+    # e2e: public API with host buffers, per step H2D state -> one attempt -> D2H state + stats
+    e2e = e2e_leg(smol, torch, precision, max(10, min(K, 400)), U, V, stream)
+
+    # roofline of the dominant kernel class
+    Tn = tsys.num_transforms
+    csz = 8 if precision == "fp32conv" else 16
+    fl, by = algorithmic(WORKLOAD["M"], Tn, csz)
+    per_step = {k: prof_ms[k] * prof_cnt[k] / 10 for k in prof_ms}
+    dom = max(("fwd_cols", "rows", "inv_cols"), key=lambda k: per_step[k])
+    peaks, pk_src = measured_peaks()
+    if precision == "fp64":
+        achieved = fl[dom] / (prof_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "FP64 FMA pipe: 152 SMs x 2070 MHz x 2 DFMA/clk",
+                "algorithmic_per_launch": fl[dom]}
+    else:
+        pk = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+        achieved = by[dom] / (prof_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk, "unit": "GB/s",
+                "frac": achieved / pk, "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({pk_src})",
+                "algorithmic_per_launch": by[dom]}
+    tr = TRAFFIC.get((precision, dom))
+    roof["traffic"] = tr["bytes"] if tr and tr.get("src") == src_digest() else None
+    roof["kernel_ms"] = {k: round(v * 1000.0, 3) for k, v in prof_ms.items()}
+    roof["kernel_ms_unit"] = "us per launch (CUDA events, one kernel at a time)"
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        res = run_cpu_baseline(args.cpu_seconds)
+        if res:
+            cpu = {"value": res["rate"], "unit": "RHS evals/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{res['evals']} evaluations of S(n) (numpy-FFT route, M=2^17) in oracle RKF45 "
+                             f"attempts, {res['seconds']:.1f} s, one thread"}
+    line = {
+        "metric": "rhs_evals_per_s", "value": value, "unit": "RHS evals/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": dict(config_dict(precision), parallelism=f"replicas{world}"),
+        "accepted_steps_per_s": accepted_per_s,
+        "attempts": {"accepted": stats["accepted"], "rejected": stats["rejected"], "t_end": stats["t"]},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * K,
+        "clocks": clocks,
+    }
+    if args.both and precision == "fp64":
+        ms32, st32, pm32, pc32, tsys32, _, _ = time_form(smol, torch, "fp32conv", K, W, stream, flush, rank)
+        v32 = world * EVALS_PER_STEP * K / (ms32 / 1000.0)
+        line["fp32conv"] = {"value": v32, "ms_per_step": ms32 / K, "speedup_vs_fp64": v32 / value,
+                            "kernel_us": {k: round(v * 1000.0, 3) for k, v in pm32.items()},
+                            "rhs_rel_err_vs_fp64": rhs_accuracy(smol, torch, U, V)}
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def rhs_accuracy(smol, torch, U, V):
+    """Normwise relative error of the FP32-convolution S(n) against the FP64 one (which
+    matches the oracle to ~1e-15) on the workload's mid-run sample state."""
+    from synth import sample_state
+    w = WORKLOAD
+    n = torch.from_numpy(sample_state(w["M"], w["lam"])).cuda()
+    a = smol.System(U, V, w["lam"]).rhs(n)
+    b = smol.System(U, V, w["lam"], precision="fp32conv").rhs(n)
+    return float((a - b).norm() / a.norm())
+
+
+def e2e_leg(smol, torch, precision, K, U, V, stream):
+    """Per step: pinned host state -> device, one RKF45 attempt through smol_integrate,
+    device -> pinned host state; wall time of K steps."""
+    from synth import monodisperse
+    w = WORKLOAD
+    M = w["M"]
+    sysm = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=1e-3, max_attempts=1, chunk=1)
+    h = torch.from_numpy(monodisperse(M)).pin_memory()
+    d = torch.empty(M, dtype=torch.float64, device="cuda")
+    t = 0.0
+    for _ in range(3):
+        d.copy_(h, non_blocking=True)
+        sysm.integrate(d, t, w["t1"], w["tol"], inplace=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tc = 0.0
+    with torch.cuda.stream(stream):
+        for _ in range(K):
+            d.copy_(h, non_blocking=True)
+            _, st = sysm.integrate(d, tc, w["t1"], w["tol"], inplace=True)
+            h.copy_(d, non_blocking=True)
+            stream.synchronize()
+            tc = st["t"]
+    el = time.perf_counter() - t0
+    # state both ways, plus the control block (152 bytes) uploaded at start and read back
+    # (status snapshot and final read) by smol_integrate
+    return {"value": EVALS_PER_STEP * K / el, "unit": "RHS evals/s", "h2d_bytes_per_step": 8 * M + 152,
+            "d2h_bytes_per_step": 8 * M + 2 * 152, "steps": K}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32conv"])
+    ap.add_argument("--both", action="store_true", default=True)
+    ap.add_argument("--no-both", dest="both", action="store_false")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-max-evals", type=int, default=None)
+    ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--t-setup", type=float, default=WORKLOAD["t_setup"],
+                    help="untimed integration span before the timed steps")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.cpu_worker:
+        return cpu_worker(args)
+    WORKLOAD["t_setup"] = args.t_setup
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main() or 0)

@@ -165,6 +165,38 @@ int smol_rhs_terms(smol_system* sys, const double* d_n, double* d_birth, double*
 int smol_integrate(smol_system* sys, double* d_n, double t0, double t1, double tol,
                    int32_t scheme, smol_stats* stats);
 
+/* The same integration split into asynchronous parts, for callers that interleave it
+ * with their own work or time it with CUDA events:
+ *   smol_integrate_start:   validates, uploads the control block, enqueues the first-
+ *                           step computation and (once per scheme / chunk size) captures
+ *                           the CUDA graph of min(opts.chunk, opts.max_attempts) attempts.
+ *                           Synchronises the stream once; d_n must stay valid until
+ *                           smol_integrate_finish.
+ *   smol_integrate_advance: enqueues one graph launch (that many attempts) on the
+ *                           stream and returns at once. Attempts after termination
+ *                           (t1 reached or a status set) do no work.
+ *   smol_integrate_finish:  synchronises the stream, writes the state back to d_n and
+ *                           fills *stats; returns the status like smol_integrate.
+ * smol_integrate is start + advance until done + finish. */
+int smol_integrate_start(smol_system* sys, double* d_n, double t0, double t1, double tol, int32_t scheme);
+int smol_integrate_advance(smol_system* sys);
+int smol_integrate_finish(smol_system* sys, smol_stats* stats);
+
+/* Kernel classes reported by smol_profile_attempts. */
+#define SMOL_PROF_FWD_COLS 0   /* stage input, moments, forward column FFTs */
+#define SMOL_PROF_ROWS     1   /* row FFTs, spectral product sum, inverse row FFTs */
+#define SMOL_PROF_INV_COLS 2   /* inverse column FFTs and the right-hand-side epilogue */
+#define SMOL_PROF_STEP     3   /* RK combination, error norm and step control */
+#define SMOL_PROF_KINDS    4
+
+/* Measurement aid: runs `reps` further attempts of the current run (between
+ * smol_integrate_start and smol_integrate_finish) launched one kernel at a time with
+ * CUDA events around each kernel on the system's stream, and returns the average
+ * duration in milliseconds of each kernel class in kernel_ms[SMOL_PROF_KINDS] and the
+ * number of launches timed in kernel_launches (may be NULL). Synchronises per attempt. */
+int smol_profile_attempts(smol_system* sys, int32_t reps, double* kernel_ms, int64_t* kernel_launches,
+                          int32_t nkinds);
+
 /* Copies the step log of the last smol_integrate (the most recent min(count, cap)
  * attempts, oldest first) to host arrays of cap entries each (any may be NULL).
  * *count receives the number of attempts made. */

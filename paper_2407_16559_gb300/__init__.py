@@ -67,6 +67,10 @@ SIGNATURES = {
     "smol_rhs": (ctypes.c_int, [_P, _P, _P]),
     "smol_rhs_terms": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "smol_integrate": (ctypes.c_int, [_P, _P, _D, _D, _D, _I32, ctypes.POINTER(Stats)]),
+    "smol_integrate_start": (ctypes.c_int, [_P, _P, _D, _D, _D, _I32]),
+    "smol_integrate_advance": (ctypes.c_int, [_P]),
+    "smol_integrate_finish": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "smol_profile_attempts": (ctypes.c_int, [_P, _I32, _P, _P, _I32]),
     "smol_get_log": (ctypes.c_int, [_P, _P, _P, _P, _P, _I32, ctypes.POINTER(_I64)]),
     "smol_num_transforms": (ctypes.c_int, [_P]),
     "smol_destroy": (None, [_P]),
@@ -205,6 +209,39 @@ class System:
         if rc in (EINVAL, ECUDA, ENOSPACE, EUNSUPPORTED):
             raise SmolError(rc, "smol_integrate")
         return n, st.as_dict()
+
+    # asynchronous form: start / advance / finish
+    def start(self, n, t0: float, t1: float, tol: float, scheme: str = "rkf45"):
+        """Begins an integration of the device tensor n in place (kept referenced until
+        finish); returns n."""
+        n = self._vec(n)
+        self._run = n
+        _check(_lib.smol_integrate_start(self._h, n.data_ptr(), float(t0), float(t1), float(tol), SCHEMES[scheme]),
+               "smol_integrate_start")
+        return n
+
+    def advance(self):
+        """Enqueues one captured chunk of attempts; does not synchronise."""
+        _check(_lib.smol_integrate_advance(self._h), "smol_integrate_advance")
+
+    def finish(self):
+        st = Stats()
+        rc = _lib.smol_integrate_finish(self._h, ctypes.byref(st))
+        if rc in (EINVAL, ECUDA):
+            raise SmolError(rc, "smol_integrate_finish")
+        n, self._run = self._run, None
+        return n, st.as_dict()
+
+    PROF_KINDS = ("fwd_cols", "rows", "inv_cols", "step")
+
+    def profile(self, reps: int = 20):
+        """Per-kernel-class average durations (ms) and launch counts over `reps` attempts
+        of the current run, each kernel bracketed by CUDA events."""
+        ms = np.zeros(len(self.PROF_KINDS))
+        cnt = np.zeros(len(self.PROF_KINDS), dtype=np.int64)
+        _check(_lib.smol_profile_attempts(self._h, int(reps), ms.ctypes.data, cnt.ctypes.data, len(ms)),
+               "smol_profile_attempts")
+        return dict(zip(self.PROF_KINDS, ms)), dict(zip(self.PROF_KINDS, cnt.tolist()))
 
     def get_log(self, cap: int | None = None):
         """Step log of the last integrate: arrays t, tau, err, accepted (oldest first)."""

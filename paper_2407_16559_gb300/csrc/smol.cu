@@ -151,6 +151,10 @@ struct smol_system {
     cudaGraphExec_t gexec;
     int gkey;
     int64_t last_attempts;
+    // current run (smol_integrate_start .. smol_integrate_finish)
+    double* run_dn;
+    int run_scheme;
+    int64_t run_attempts;
 };
 
 // ---------------------------------------------------------------------------
@@ -177,19 +181,53 @@ int threads_for(int butterflies) {
     return (t + 31) & ~31;
 }
 
+// Optional per-kernel timing of eagerly launched attempts (smol_profile_attempts).
+constexpr int PROF_MAX = 64;
+struct Prof {
+    cudaEvent_t ev0[PROF_MAX], ev1[PROF_MAX];
+    int kind[PROF_MAX];
+    int n;
+};
+struct ProfScope {
+    Prof* p;
+    cudaStream_t st;
+    int q;
+    ProfScope(Prof* p_, cudaStream_t st_, int kind) : p(p_), st(st_), q(-1) {
+        if (p && p->n < PROF_MAX) {
+            q = p->n++;
+            p->kind[q] = kind;
+            cudaEventRecord(p->ev0[q], st);
+        }
+    }
+    ~ProfScope() {
+        if (q >= 0) cudaEventRecord(p->ev1[q], st);
+    }
+};
+
 template <typename R>
-void launch_eval(const smol_system* S, const StageIn& in, const Ctl* ctl, const EpiOut& eo, cudaStream_t st) {
+void launch_eval(const smol_system* S, const StageIn& in, const Ctl* ctl, const EpiOut& eo, cudaStream_t st,
+                 Prof* pr) {
     const Shape& s = S->s;
     const int nbx = s.N2 / s.G;
     const size_t sc = smem_cols(s), sr = smem_rows(s, S->T);
-    k_fwd_cols<R><<<dim3(nbx, S->T), threads_for((s.N1 / 4) * s.G), sc, st>>>(S->dev, in, ctl, s.G);
-    k_rows<R><<<s.N1 / 2, threads_for((s.N2 / 4) * 2 * S->T), sr, st>>>(S->dev, ctl);
-    k_inv_cols<R><<<nbx, threads_for((s.N1 / 4) * s.G), sc, st>>>(S->dev, in, ctl, eo, s.G);
+    {
+        ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
+        k_fwd_cols<R><<<dim3(nbx, S->T), threads_for((s.N1 / 4) * s.G), sc, st>>>(S->dev, in, ctl, s.G);
+    }
+    {
+        ProfScope ps(pr, st, SMOL_PROF_ROWS);
+        k_rows<R><<<s.N1 / 2, threads_for((s.N2 / 4) * 2 * S->T), sr, st>>>(S->dev, ctl);
+    }
+    {
+        ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
+        k_inv_cols<R><<<nbx, threads_for((s.N1 / 4) * s.G), sc, st>>>(S->dev, in, ctl, eo, s.G);
+    }
 }
 
-void eval(const smol_system* S, const StageIn& in, const Ctl* ctl, const EpiOut& eo, cudaStream_t st) {
-    if (S->o.precision == SMOL_FP32CONV) launch_eval<float>(S, in, ctl, eo, st);
-    else launch_eval<double>(S, in, ctl, eo, st);
+void eval(const smol_system* S, const StageIn& in, const Ctl* ctl, const EpiOut& eo, cudaStream_t st,
+          Prof* pr = nullptr) {
+    if (S->o.precision == SMOL_FP32CONV) launch_eval<float>(S, in, ctl, eo, st, pr);
+    else launch_eval<double>(S, in, ctl, eo, st, pr);
 }
 
 StageIn stage(std::initializer_list<std::pair<int, double>> terms, const smol_system* S) {
@@ -244,13 +282,13 @@ int fin_blocks(int M) {
 }
 
 // Enqueues one step attempt of the given scheme on stream st.
-void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P, cudaStream_t st) {
+void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
     double* sq = (double*)(S->ws + S->L.sqpart);
     double* fpart = (double*)(S->ws + S->L.fpart);
     const int M = S->s.M;
     Ctl* c = S->ctl;
     auto E = [&](const StageIn& in, int k, double hfac, bool first) {
-        eval(S, in, c, epi_k(S->vec[k], hfac, (first && P.sqpart) ? sq : nullptr), st);
+        eval(S, in, c, epi_k(S->vec[k], hfac, (first && P.sqpart) ? sq : nullptr), st, pr);
     };
     if (scheme == SCHEME_RKF45) {
         E(stage({{-1, 1.0}}, S), 0, 1.0, true);
@@ -275,7 +313,7 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
                              {4, -9.0 / 50.0 + 1.0 / 5.0},
                              {5, 2.0 / 55.0}},
                             S);
-        k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M);
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
         return;
     }
     if (scheme == SCHEME_RK2) {
@@ -284,18 +322,18 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
         if (fixed) {
             StageIn cand = stage({{-1, 1.0}, {0, 0.5}, {1, 0.5}}, S);
             StageIn del = stage({{0, 0.0}}, S);
-            k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M);
+            { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
             return;
         }
         // half step 1: l1 = k1/2, l2 = (h/2) S(n + k1/2); n_half = n + (l1 + l2)/2
         E(stage({{-1, 1.0}, {0, 0.5}}, S), 2, 0.5, false);
-        k_lincomb<<<fin_blocks(M), 256, 0, st>>>(stage({{-1, 1.0}, {0, 0.25}, {2, 0.5}}, S), c, S->vec[3], M);
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), 256, 0, st>>>(stage({{-1, 1.0}, {0, 0.25}, {2, 0.5}}, S), c, S->vec[3], M); }
         // half step 2 from n_half: m1, m2
         E(stage({{3, 1.0}}, S), 4, 0.5, false);
         E(stage({{3, 1.0}, {4, 1.0}}, S), 5, 0.5, false);
         StageIn cand = stage({{3, 1.0}, {4, 0.5}, {5, 0.5}}, S);
         StageIn del = stage({{3, 1.0}, {4, 0.5}, {5, 0.5}, {-1, -1.0}, {0, -0.5}, {1, -0.5}}, S);
-        k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M);
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
         return;
     }
     // RK4
@@ -306,15 +344,15 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
     if (fixed) {
         StageIn cand = stage({{-1, 1.0}, {0, 1.0 / 6.0}, {1, 1.0 / 3.0}, {2, 1.0 / 3.0}, {3, 1.0 / 6.0}}, S);
         StageIn del = stage({{0, 0.0}}, S);
-        k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M);
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
         return;
     }
     // half step 1 with h/2: l1 = k1/2
     E(stage({{-1, 1.0}, {0, 0.25}}, S), 4, 0.5, false);              // l2 = (h/2) S(n + l1/2)
     E(stage({{-1, 1.0}, {4, 0.5}}, S), 5, 0.5, false);               // l3
     E(stage({{-1, 1.0}, {5, 1.0}}, S), 6, 0.5, false);               // l4
-    k_lincomb<<<fin_blocks(M), 256, 0, st>>>(
-        stage({{-1, 1.0}, {0, 1.0 / 12.0}, {4, 1.0 / 3.0}, {5, 1.0 / 3.0}, {6, 1.0 / 6.0}}, S), c, S->vec[7], M);
+    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), 256, 0, st>>>(
+        stage({{-1, 1.0}, {0, 1.0 / 12.0}, {4, 1.0 / 3.0}, {5, 1.0 / 3.0}, {6, 1.0 / 6.0}}, S), c, S->vec[7], M); }
     E(stage({{7, 1.0}}, S), 8, 0.5, false);                          // m1
     E(stage({{7, 1.0}, {8, 0.5}}, S), 9, 0.5, false);                // m2
     E(stage({{7, 1.0}, {9, 0.5}}, S), 10, 0.5, false);               // m3
@@ -332,7 +370,7 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
                          {2, -1.0 / 3.0},
                          {3, -1.0 / 6.0}},
                         S);
-    k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M);
+    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
 }
 
 CtlParams make_params(const smol_system* S, int scheme, bool steady) {
@@ -609,7 +647,7 @@ int smol_rhs_terms(smol_system* S, const double* d_n, double* d_birth, double* d
     return rhs_common(S, d_n, nullptr, d_birth, d_loss, d_source);
 }
 
-int smol_integrate(smol_system* S, double* d_n, double t0, double t1, double tol, int32_t scheme, smol_stats* stats) {
+int smol_integrate_start(smol_system* S, double* d_n, double t0, double t1, double tol, int32_t scheme) {
     if (!S || !d_n || ((uintptr_t)d_n & 15)) return SMOL_EINVAL;
     if (!(t1 >= t0) || !isfinite(t0) || !isfinite(t1)) return SMOL_EINVAL;
     if (scheme < SMOL_RK2 || scheme > SMOL_RKF45) return SMOL_EINVAL;
@@ -626,27 +664,33 @@ int smol_integrate(smol_system* S, double* d_n, double t0, double t1, double tol
     h.tau = S->o.tau0 > 0.0 ? S->o.tau0 : (fixed ? S->o.fixed_tau : 0.0);
     h.state[0] = d_n;
     h.state[1] = S->stateB;
+    // the pinned block may still be the target of an earlier read-back: wait for it
+    CK(cudaStreamSynchronize(st));
     *S->h_ctl = h;
     CK(cudaMemcpyAsync(S->ctl, S->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-    const int npb = PREP_BLOCKS;
     double* ppart = (double*)(S->ws + S->L.ppart);
     double* delta = (double*)(S->ws + S->L.delta);
-    k_prep1<<<npb, 256, 0, st>>>(S->dev, S->ctl, ppart, delta);
-    k_prep2<<<npb, 256, 0, st>>>(S->dev, S->ctl, delta, ppart, S->o.euler_a);
+    k_prep1<<<PREP_BLOCKS, 256, 0, st>>>(S->dev, S->ctl, ppart, delta);
+    k_prep2<<<PREP_BLOCKS, 256, 0, st>>>(S->dev, S->ctl, delta, ppart, S->o.euler_a);
     CK(cudaGetLastError());
 
-    // One CUDA graph holds `chunk` attempts; kernels of attempts after termination
-    // return immediately (they read ctl->done first).
-    const int key = scheme * 16 + (fixed ? 8 : 0) + (steady ? 4 : 0) + (S->o.precision == SMOL_FP32CONV ? 2 : 0);
+    // One CUDA graph holds `chunk` attempts (fewer if max_attempts is smaller); kernels
+    // of attempts after termination return at once (they read ctl->done first).
+    int64_t na = S->o.chunk;
+    if (S->o.max_attempts < na) na = S->o.max_attempts;
+    if (na < 1) na = 1;
+    const int key = (int)na * 64 + scheme * 16 + (fixed ? 8 : 0) + (steady ? 4 : 0) +
+                    (S->o.precision == SMOL_FP32CONV ? 2 : 0);
     if (S->gkey != key) {
         if (S->gexec) {
             cudaGraphExecDestroy(S->gexec);
             S->gexec = nullptr;
         }
+        S->gkey = -1;
         CtlParams P = make_params(S, scheme, steady);
         cudaGraph_t g;
         CK(cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal));
-        for (int a = 0; a < S->o.chunk; ++a) enqueue_attempt(S, scheme, fixed, P, S->cap);
+        for (int64_t q = 0; q < na; ++q) enqueue_attempt(S, scheme, fixed, P, S->cap, nullptr);
         cudaError_t e1 = cudaStreamEndCapture(S->cap, &g);
         if (e1 != cudaSuccess) return SMOL_ECUDA;
         e1 = cudaGraphInstantiate(&S->gexec, g, 0);
@@ -657,52 +701,30 @@ int smol_integrate(smol_system* S, double* d_n, double t0, double t1, double tol
         }
         S->gkey = key;
     }
-    // Launch chunks, keeping one in flight while the status of the previous one is read.
-    cudaEvent_t ev[2];
-    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    Ctl* snap = S->h_ctl;
-    int64_t launched = 0;
-    int rc = SMOL_OK;
-    const int64_t max_chunks = S->o.max_attempts / (S->o.chunk > 0 ? S->o.chunk : 1) + 2;
-    bool done = false;
-    int cur = 0;
-    // prime: first chunk
-    if (cudaGraphLaunch(S->gexec, st) != cudaSuccess) rc = SMOL_ECUDA;
-    if (rc == SMOL_OK && cudaMemcpyAsync(snap, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        rc = SMOL_ECUDA;
-    if (rc == SMOL_OK && cudaEventRecord(ev[cur], st) != cudaSuccess) rc = SMOL_ECUDA;
-    launched = 1;
-    while (rc == SMOL_OK && !done) {
-        // queue the next chunk before looking at the previous status
-        if (cudaGraphLaunch(S->gexec, st) != cudaSuccess) {
-            rc = SMOL_ECUDA;
-            break;
-        }
-        ++launched;
-        if (cudaEventSynchronize(ev[cur]) != cudaSuccess) {
-            rc = SMOL_ECUDA;
-            break;
-        }
-        done = snap->done != 0;
-        if (cudaMemcpyAsync(snap, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaEventRecord(ev[cur ^ 1], st) != cudaSuccess) {
-            rc = SMOL_ECUDA;
-            break;
-        }
-        cur ^= 1;
-        if (launched > max_chunks + 2) break;
-    }
-    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SMOL_ECUDA;
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-    if (rc != SMOL_OK) return rc;
+    S->run_dn = d_n;
+    S->run_scheme = scheme;
+    S->run_attempts = na;
+    return SMOL_OK;
+}
+
+int smol_integrate_advance(smol_system* S) {
+    if (!S || !S->run_dn || !S->gexec) return SMOL_EINVAL;
+    CK(cudaGraphLaunch(S->gexec, S->stream));
+    return SMOL_OK;
+}
+
+int smol_integrate_finish(smol_system* S, smol_stats* stats) {
+    if (!S || !S->run_dn) return SMOL_EINVAL;
+    cudaStream_t st = S->stream;
+    CK(cudaStreamSynchronize(st));
     Ctl fin;
-    if (cudaMemcpy(&fin, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return SMOL_ECUDA;
+    CK(cudaMemcpy(&fin, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
     if (fin.cur == 1) {
-        if (cudaMemcpyAsync(d_n, S->stateB, (size_t)S->s.M * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return SMOL_ECUDA;
+        CK(cudaMemcpyAsync(S->run_dn, S->stateB, (size_t)S->s.M * 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        // the caller's buffer holds the state again: keep later advances consistent
+        int zero = 0;
+        CK(cudaMemcpy(&S->ctl->cur, &zero, sizeof(int), cudaMemcpyHostToDevice));
     }
     S->last_attempts = fin.attempts;
     if (stats) {
@@ -718,6 +740,97 @@ int smol_integrate(smol_system* S, double* d_n, double t0, double t1, double tol
         stats->reserved = 0;
     }
     return fin.status;
+}
+
+int smol_integrate(smol_system* S, double* d_n, double t0, double t1, double tol, int32_t scheme, smol_stats* stats) {
+    int rc = smol_integrate_start(S, d_n, t0, t1, tol, scheme);
+    if (rc != SMOL_OK) return rc;
+    if (!(t1 > t0)) return smol_integrate_finish(S, stats);  // nothing to integrate
+    cudaStream_t st = S->stream;
+    // Launch chunks, keeping one in flight while the status of the previous one is read
+    // from a pinned copy of the control block.
+    cudaEvent_t ev[2];
+    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    Ctl* snap = S->h_ctl;
+    const int64_t maxa = S->o.max_attempts;
+    int64_t launched = S->run_attempts;  // attempts enqueued so far
+    bool done = false;
+    int cur = 0;
+    if (cudaGraphLaunch(S->gexec, st) != cudaSuccess ||
+        cudaMemcpyAsync(snap, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(ev[cur], st) != cudaSuccess)
+        rc = SMOL_ECUDA;
+    while (rc == SMOL_OK && !done && launched < maxa) {
+        if (cudaGraphLaunch(S->gexec, st) != cudaSuccess) {
+            rc = SMOL_ECUDA;
+            break;
+        }
+        launched += S->run_attempts;
+        if (cudaEventSynchronize(ev[cur]) != cudaSuccess) {
+            rc = SMOL_ECUDA;
+            break;
+        }
+        done = snap->done != 0;
+        if (done) break;
+        if (cudaMemcpyAsync(snap, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaEventRecord(ev[cur ^ 1], st) != cudaSuccess) {
+            rc = SMOL_ECUDA;
+            break;
+        }
+        cur ^= 1;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SMOL_ECUDA;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc != SMOL_OK) return rc;
+    return smol_integrate_finish(S, stats);
+}
+
+int smol_profile_attempts(smol_system* S, int32_t reps, double* kernel_ms, int64_t* kernel_launches, int32_t nkinds) {
+    if (!S || !S->run_dn || reps < 1 || !kernel_ms || nkinds < SMOL_PROF_KINDS) return SMOL_EINVAL;
+    cudaStream_t st = S->stream;
+    Prof pr;
+    memset(&pr, 0, sizeof(pr));
+    for (int q = 0; q < PROF_MAX; ++q) {
+        CK(cudaEventCreate(&pr.ev0[q]));
+        CK(cudaEventCreate(&pr.ev1[q]));
+    }
+    const bool fixed = S->o.fixed_tau > 0.0;
+    CtlParams P = make_params(S, S->run_scheme, S->o.steady_rtol > 0.0);
+    double acc[SMOL_PROF_KINDS] = {0};
+    int64_t cnt[SMOL_PROF_KINDS] = {0};
+    int rc = SMOL_OK;
+    for (int r = 0; r < reps && rc == SMOL_OK; ++r) {
+        pr.n = 0;
+        // ~0.5 ms of device work first, so that the whole attempt is enqueued before the
+        // device reaches it and the events time the kernels, not the host launches
+        k_delay<<<1, 32, 0, st>>>(1000000LL);
+        enqueue_attempt(S, S->run_scheme, fixed, P, st, &pr);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = SMOL_ECUDA;
+            break;
+        }
+        for (int q = 0; q < pr.n; ++q) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.ev0[q], pr.ev1[q]) != cudaSuccess) {
+                rc = SMOL_ECUDA;
+                break;
+            }
+            acc[pr.kind[q]] += ms;
+            cnt[pr.kind[q]] += 1;
+        }
+    }
+    for (int q = 0; q < PROF_MAX; ++q) {
+        cudaEventDestroy(pr.ev0[q]);
+        cudaEventDestroy(pr.ev1[q]);
+    }
+    if (rc != SMOL_OK) return rc;
+    for (int k = 0; k < SMOL_PROF_KINDS; ++k) {
+        kernel_ms[k] = cnt[k] ? acc[k] / (double)cnt[k] : 0.0;
+        if (kernel_launches) kernel_launches[k] = cnt[k];
+    }
+    return SMOL_OK;
 }
 
 int smol_get_log(smol_system* S, double* h_t, double* h_tau, double* h_err, int32_t* h_acc, int32_t cap, int64_t* count) {
