@@ -18,7 +18,7 @@ using namespace smol;
 namespace {
 
 constexpr int NVEC = 12;        // stage / work vectors of the integrators
-constexpr int FIN_BLOCKS = 304; // 2 x 152 SMs
+constexpr int FIN_BLOCKS = 608; // 4 x 152 SMs (128-thread CTAs)
 constexpr int PREP_BLOCKS = 152;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -46,10 +46,12 @@ Shape make_shape(int64_t M, int precision) {
     s.lgN2 = s.lgMp / 2;
     s.N1 = 1 << s.lgN1;
     s.N2 = 1 << s.lgN2;
-    // columns per CTA of the column passes: aim at >= 128 CTAs per transform
-    int G = s.N2 / 128;
+    // columns per CTA of the column passes: one column of N1 >= 256 points per CTA
+    // (many small CTAs spread the latency-bound passes over all SMs), more columns for
+    // short columns so that a CTA keeps at least 32 radix-8 butterflies per pass
+    int G = 256 / s.N1;
     if (G < 1) G = 1;
-    if (G > 8) G = 8;
+    if (G > s.N2) G = s.N2;
     s.G = G;
     s.csz = precision == SMOL_FP32CONV ? 8 : 16;
     return s;
@@ -174,10 +176,12 @@ int set_smem_attrs(const smol_system* S) {
     return SMOL_OK;
 }
 
-int threads_for(int butterflies) {
-    int t = butterflies;
+// Threads of a CTA whose passes have `points` points per sequence-group: one thread per
+// radix-8 butterfly, between 32 and 256.
+int threads_for(int points) {
+    int t = points / 8;
     if (t > 256) t = 256;
-    if (t < 64) t = 64;
+    if (t < 32) t = 32;
     return (t + 31) & ~31;
 }
 
@@ -212,15 +216,15 @@ void launch_eval(const smol_system* S, const StageIn& in, const Ctl* ctl, const 
     const size_t sc = smem_cols(s), sr = smem_rows(s, S->T);
     {
         ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
-        k_fwd_cols<R><<<dim3(nbx, S->T), threads_for((s.N1 / 4) * s.G), sc, st>>>(S->dev, in, ctl, s.G);
+        k_fwd_cols<R><<<dim3(nbx, S->T), threads_for(s.N1 * s.G), sc, st>>>(S->dev, in, ctl, s.G);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_ROWS);
-        k_rows<R><<<s.N1 / 2, threads_for((s.N2 / 4) * 2 * S->T), sr, st>>>(S->dev, ctl);
+        k_rows<R><<<s.N1 / 2, threads_for(s.N2 * 2 * S->T), sr, st>>>(S->dev, ctl);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
-        k_inv_cols<R><<<nbx, threads_for((s.N1 / 4) * s.G), sc, st>>>(S->dev, in, ctl, eo, s.G);
+        k_inv_cols<R><<<nbx, threads_for(s.N1 * s.G), sc, st>>>(S->dev, in, ctl, eo, s.G);
     }
 }
 
@@ -274,8 +278,10 @@ EpiOut epi_k(double* out, double hfac, double* sqpart) {
     return e;
 }
 
+constexpr int FIN_THREADS = 128;
+
 int fin_blocks(int M) {
-    int b = (M / 2 + 255) / 256;
+    int b = (M / 2 + FIN_THREADS - 1) / FIN_THREADS;
     if (b < 1) b = 1;
     if (b > FIN_BLOCKS) b = FIN_BLOCKS;
     return b;
@@ -313,7 +319,7 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
                              {4, -9.0 / 50.0 + 1.0 / 5.0},
                              {5, 2.0 / 55.0}},
                             S);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
         return;
     }
     if (scheme == SCHEME_RK2) {
@@ -322,18 +328,18 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
         if (fixed) {
             StageIn cand = stage({{-1, 1.0}, {0, 0.5}, {1, 0.5}}, S);
             StageIn del = stage({{0, 0.0}}, S);
-            { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
+            { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
             return;
         }
         // half step 1: l1 = k1/2, l2 = (h/2) S(n + k1/2); n_half = n + (l1 + l2)/2
         E(stage({{-1, 1.0}, {0, 0.5}}, S), 2, 0.5, false);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), 256, 0, st>>>(stage({{-1, 1.0}, {0, 0.25}, {2, 0.5}}, S), c, S->vec[3], M); }
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), FIN_THREADS, 0, st>>>(stage({{-1, 1.0}, {0, 0.25}, {2, 0.5}}, S), c, S->vec[3], M); }
         // half step 2 from n_half: m1, m2
         E(stage({{3, 1.0}}, S), 4, 0.5, false);
         E(stage({{3, 1.0}, {4, 1.0}}, S), 5, 0.5, false);
         StageIn cand = stage({{3, 1.0}, {4, 0.5}, {5, 0.5}}, S);
         StageIn del = stage({{3, 1.0}, {4, 0.5}, {5, 0.5}, {-1, -1.0}, {0, -0.5}, {1, -0.5}}, S);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
         return;
     }
     // RK4
@@ -344,14 +350,14 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
     if (fixed) {
         StageIn cand = stage({{-1, 1.0}, {0, 1.0 / 6.0}, {1, 1.0 / 3.0}, {2, 1.0 / 3.0}, {3, 1.0 / 6.0}}, S);
         StageIn del = stage({{0, 0.0}}, S);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
+        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
         return;
     }
     // half step 1 with h/2: l1 = k1/2
     E(stage({{-1, 1.0}, {0, 0.25}}, S), 4, 0.5, false);              // l2 = (h/2) S(n + l1/2)
     E(stage({{-1, 1.0}, {4, 0.5}}, S), 5, 0.5, false);               // l3
     E(stage({{-1, 1.0}, {5, 1.0}}, S), 6, 0.5, false);               // l4
-    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), 256, 0, st>>>(
+    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), FIN_THREADS, 0, st>>>(
         stage({{-1, 1.0}, {0, 1.0 / 12.0}, {4, 1.0 / 3.0}, {5, 1.0 / 3.0}, {6, 1.0 / 6.0}}, S), c, S->vec[7], M); }
     E(stage({{7, 1.0}}, S), 8, 0.5, false);                          // m1
     E(stage({{7, 1.0}, {8, 0.5}}, S), 9, 0.5, false);                // m2
@@ -370,7 +376,7 @@ void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P,
                          {2, -1.0 / 3.0},
                          {3, -1.0 / 6.0}},
                         S);
-    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), 256, 0, st>>>(cand, del, c, P, fpart, M); }
+    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
 }
 
 CtlParams make_params(const smol_system* S, int scheme, bool steady) {

@@ -7,8 +7,8 @@
 // on the even/odd-packed sequence. A length-Mp transform is split Mp = N1 * N2
 // ("four-step"): N2 column transforms of length N1, a twiddle W_Mp^{n2 k1}, then N1
 // row transforms of length N2. Each column / row transform runs inside one CTA in
-// shared memory as an autosorting Stockham FFT with radix-4 passes (and one radix-2
-// pass when log2 of the length is odd).
+// shared memory as an autosorting Stockham FFT with radix-8 passes (and one radix-4
+// or radix-2 pass for the remaining factor).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -65,74 +65,107 @@ __device__ __forceinline__ cx<R> twl(const cx<R>* __restrict__ tw, uint32_t e, u
     return (e & Mp) ? -w : w;
 }
 
+// Length-4 DFT in place (forward: W_4 = -i; INV: +i).
+template <typename R, bool INV>
+__device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3) {
+    const cx<R> s0 = x0 + x2, d0 = x0 - x2, s1 = x1 + x3;
+    const cx<R> d1 = INV ? mul_pi(x1 - x3) : mul_mi(x1 - x3);
+    x0 = s0 + s1;
+    x2 = s0 - s1;
+    x1 = d0 + d1;
+    x3 = d0 - d1;
+}
+
+// Length-8 DFT in place: a radix-2 split (u_m +- u_{m+4}, the difference rotated by
+// W_8^m), then two length-4 DFTs giving the even and the odd outputs.
+template <typename R, bool INV>
+__device__ __forceinline__ void dft8(cx<R>* u) {
+    const R h = (R)0.70710678118654752440;
+    cx<R> a0 = u[0] + u[4], a1 = u[1] + u[5], a2 = u[2] + u[6], a3 = u[3] + u[7];
+    cx<R> b0 = u[0] - u[4], b1 = u[1] - u[5], b2 = u[2] - u[6], b3 = u[3] - u[7];
+    if (INV) {
+        b1 = mk<R>((b1.x - b1.y) * h, (b1.x + b1.y) * h);    // * (1 + i)/sqrt 2
+        b2 = mul_pi(b2);                                     // * i
+        b3 = mk<R>(-(b3.x + b3.y) * h, (b3.x - b3.y) * h);   // * (-1 + i)/sqrt 2
+    } else {
+        b1 = mk<R>((b1.x + b1.y) * h, (b1.y - b1.x) * h);    // * (1 - i)/sqrt 2
+        b2 = mul_mi(b2);                                     // * -i
+        b3 = mk<R>((b3.y - b3.x) * h, -(b3.x + b3.y) * h);   // * (-1 - i)/sqrt 2
+    }
+    dft4<R, INV>(a0, a1, a2, a3);
+    dft4<R, INV>(b0, b1, b2, b3);
+    u[0] = a0;
+    u[1] = b0;
+    u[2] = a1;
+    u[3] = b1;
+    u[4] = a2;
+    u[5] = b2;
+    u[6] = a3;
+    u[7] = b3;
+}
+
+// One Stockham pass of radix RAD (8, 4 or 2) on sub-transform length p = 2^lgp of a
+// length-P transform over G interleaved sequences: for butterfly i in [0, P/RAD),
+// k = i mod p, inputs in[i + m P/RAD] (m < RAD) are multiplied by W_{RAD p}^{m k},
+// transformed by a length-RAD DFT and stored at out[(i-k) RAD + k + m p].
+template <typename R, bool INV, int RAD>
+__device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>* __restrict__ b, int lgP, int lgp,
+                                              int G, const cx<R>* __restrict__ tw, int lgMp) {
+    constexpr int LGR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
+    const int P = 1 << lgP;
+    const int p = 1 << lgp;
+    const int q = P >> LGR;
+    const int nb = q * G;
+    const uint32_t Mp = 1u << lgMp;
+    const int sh = (lgMp + 1) - LGR - lgp;  // W_{RAD p}^{e} = W_{2Mp}^{e << sh}
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+        const int g = idx % G;
+        const int i = idx / G;
+        const int k = i & (p - 1);
+        cx<R> u[RAD];
+#pragma unroll
+        for (int m = 0; m < RAD; ++m) u[m] = a[(i + m * q) * G + g];
+        if (k) {
+#pragma unroll
+            for (int m = 1; m < RAD; ++m) {
+                cx<R> w = twl(tw, (uint32_t)(m * k) << sh, Mp);
+                if (INV) w = conj(w);
+                u[m] = u[m] * w;
+            }
+        }
+        if (RAD == 8) {
+            dft8<R, INV>(u);
+        } else if (RAD == 4) {
+            dft4<R, INV>(u[0], u[1], u[2], u[3]);
+        } else {
+            const cx<R> t = u[0] - u[1];
+            u[0] = u[0] + u[1];
+            u[1] = t;
+        }
+        const int j = ((i - k) << LGR) + k;
+#pragma unroll
+        for (int m = 0; m < RAD; ++m) b[(j + m * p) * G + g] = u[m];
+    }
+}
+
 // Stockham autosort FFT of length P = 2^lgP on G interleaved sequences held in shared
-// memory as buf[p * G + g] (g fastest). Ping-pongs between a and b and returns the
+// memory as buf[p * G + g] (g fastest), radix-8 passes first, then one radix-4 or
+// radix-2 pass for the remaining factor. Ping-pongs between a and b and returns the
 // buffer holding the result, in natural order. INV selects the sign +i (unnormalised
 // inverse). Every thread of the block must call it; the caller synchronises before.
-//
-// Pass with radix r on sub-transform length p (product of the radices so far): for
-// butterfly i in [0, P/r), k = i mod p, inputs in[i + m P/r] (m < r) are multiplied
-// by W_{r p}^{m k}, transformed by a length-r DFT and stored at out[(i-k) r + k + m p].
 template <typename R, bool INV>
 __device__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ tw, int lgMp) {
-    const int P = 1 << lgP;
-    const uint32_t Mp = 1u << lgMp;
     int lgp = 0;
     while (lgp < lgP) {
-        const int p = 1 << lgp;
-        if (lgP - lgp >= 2) {
-            const int q = P >> 2;
-            const int nb = q * G;
-            const int sh = (lgMp + 1) - 2 - lgp;   // W_{4p}^{e} = W_{2Mp}^{e << sh}
-            for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-                const int g = idx % G;
-                const int i = idx / G;
-                const int k = i & (p - 1);
-                cx<R> u0 = a[i * G + g];
-                cx<R> u1 = a[(i + q) * G + g];
-                cx<R> u2 = a[(i + 2 * q) * G + g];
-                cx<R> u3 = a[(i + 3 * q) * G + g];
-                if (k) {
-                    cx<R> w1 = twl(tw, (uint32_t)k << sh, Mp);
-                    cx<R> w2 = twl(tw, (uint32_t)(2 * k) << sh, Mp);
-                    cx<R> w3 = twl(tw, (uint32_t)(3 * k) << sh, Mp);
-                    if (INV) {
-                        w1 = conj(w1);
-                        w2 = conj(w2);
-                        w3 = conj(w3);
-                    }
-                    u1 = u1 * w1;
-                    u2 = u2 * w2;
-                    u3 = u3 * w3;
-                }
-                cx<R> a0 = u0 + u2, a1 = u0 - u2, a2 = u1 + u3, a3 = u1 - u3;
-                a3 = INV ? mul_pi(a3) : mul_mi(a3);
-                const int j = ((i - k) << 2) + k;
-                b[j * G + g] = a0 + a2;
-                b[(j + p) * G + g] = a1 + a3;
-                b[(j + 2 * p) * G + g] = a0 - a2;
-                b[(j + 3 * p) * G + g] = a1 - a3;
-            }
+        const int rem = lgP - lgp;
+        if (rem >= 3) {
+            stockham_pass<R, INV, 8>(a, b, lgP, lgp, G, tw, lgMp);
+            lgp += 3;
+        } else if (rem == 2) {
+            stockham_pass<R, INV, 4>(a, b, lgP, lgp, G, tw, lgMp);
             lgp += 2;
         } else {
-            const int q = P >> 1;
-            const int nb = q * G;
-            const int sh = (lgMp + 1) - 1 - lgp;
-            for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-                const int g = idx % G;
-                const int i = idx / G;
-                const int k = i & (p - 1);
-                cx<R> u0 = a[i * G + g];
-                cx<R> u1 = a[(i + q) * G + g];
-                if (k) {
-                    cx<R> w = twl(tw, (uint32_t)k << sh, Mp);
-                    if (INV) w = conj(w);
-                    u1 = u1 * w;
-                }
-                const int j = ((i - k) << 1) + k;
-                b[j * G + g] = u0 + u1;
-                b[(j + p) * G + g] = u0 - u1;
-            }
+            stockham_pass<R, INV, 2>(a, b, lgP, lgp, G, tw, lgMp);
             lgp += 1;
         }
         __syncthreads();

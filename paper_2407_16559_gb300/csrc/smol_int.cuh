@@ -55,9 +55,10 @@ __device__ __forceinline__ void set_next_step(Ctl* c) {
 __global__ void __launch_bounds__(256) k_lincomb(const StageIn in, const Ctl* __restrict__ ctl, double* out, int M) {
     if (ctl->done) return;
     const int np = (M + 1) >> 1;
+    const StagePtrs sp = resolve_all(in, ctl);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         double y0, y1;
-        stage_pair(in, ctl, M, 2 * p, y0, y1);
+        stage_pair(in, sp, M, 2 * p, y0, y1);
         if (2 * p + 1 < M) *reinterpret_cast<double2*>(out + 2 * p) = make_double2(y0, y1);
         else out[2 * p] = y0;
     }
@@ -75,11 +76,13 @@ __global__ void __launch_bounds__(256) k_finish(const StageIn cand, const StageI
     double* outp = ctl->state[ctl->cur ^ 1];
     double se = 0.0, sc = 0.0, mx = 0.0, bad = 0.0;
     const int np = (M + 1) >> 1;
+    const StagePtrs cp = resolve_all(cand, ctl);
+    const StagePtrs dp = resolve_all(del, ctl);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         const int i = 2 * p;
         double y0, y1, d0, d1;
-        stage_pair(cand, ctl, M, i, y0, y1);
-        stage_pair(del, ctl, M, i, d0, d1);
+        stage_pair(cand, cp, M, i, y0, y1);
+        stage_pair(del, dp, M, i, d0, d1);
         if (i + 1 < M) *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
         else outp[i] = y0;
         se += d0 * d0 + d1 * d1;

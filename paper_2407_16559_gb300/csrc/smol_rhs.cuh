@@ -88,18 +88,48 @@ __device__ __forceinline__ const double* resolve(const StageIn& in, const Ctl* c
     return in.sel[j] < 0 ? in.v[j] : ctl->state[ctl->cur ^ in.sel[j]];
 }
 
-// y at indices i and i+1 (i even); zero at and beyond M.
-__device__ __forceinline__ void stage_pair(const StageIn& in, const Ctl* ctl, int M, int i, double& y0, double& y1) {
+// The term pointers of a stage input with the state buffers resolved once (the control
+// block is read a single time per thread).
+struct StagePtrs {
+    const double* p[MAXV];
+};
+
+__device__ __forceinline__ StagePtrs resolve_all(const StageIn& in, const Ctl* ctl) {
+    StagePtrs r;
+    const int cur = ctl->cur;
+    const double* s0 = ctl->state[0];
+    const double* s1 = ctl->state[1];
+#pragma unroll
+    for (int j = 0; j < MAXV; ++j) r.p[j] = in.sel[j] < 0 ? in.v[j] : (((cur ^ in.sel[j]) & 1) ? s1 : s0);
+    return r;
+}
+
+// y at indices i and i+1 (i even); zero at and beyond M. All term loads are issued
+// before the first multiply-add (unrolled over MAXV, predicated on nv) so that their
+// latencies overlap.
+__device__ __forceinline__ void stage_pair(const StageIn& in, const StagePtrs& P, int M, int i, double& y0,
+                                           double& y1) {
     y0 = 0.0;
     y1 = 0.0;
     if (i + 1 < M) {
-        for (int j = 0; j < in.nv; ++j) {
-            const double2 v = __ldg(reinterpret_cast<const double2*>(resolve(in, ctl, j) + i));
-            y0 += in.c[j] * v.x;
-            y1 += in.c[j] * v.y;
-        }
+        double2 v[MAXV];
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) v[j] = __ldg(reinterpret_cast<const double2*>(P.p[j] + i));
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) {
+                y0 += in.c[j] * v[j].x;
+                y1 += in.c[j] * v[j].y;
+            }
     } else if (i < M) {
-        for (int j = 0; j < in.nv; ++j) y0 += in.c[j] * __ldg(resolve(in, ctl, j) + i);
+        double v[MAXV];
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) v[j] = __ldg(P.p[j] + i);
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) y0 += in.c[j] * v[j];
     }
 }
 
@@ -135,13 +165,14 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev S, const StageIn 
     const int half = (S.N1 >> 1) * G;
     double mu = 0.0, nu = 0.0;
     const bool store_y = (t == 0) && !in.direct;
+    const StagePtrs sp = resolve_all(in, ctl);
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
         const int g = idx % G;
         const int n1 = idx / G;
         const int j = (n1 << S.lgN2) + n2b + g;
         const int i = 2 * j;
         double y0, y1;
-        stage_pair(in, ctl, S.M, i, y0, y1);
+        stage_pair(in, sp, S.M, i, y0, y1);
         const double2 w = __ldg(reinterpret_cast<const double2*>(Wt + i));
         const double x0 = w.x * y0, x1 = w.y * y1;
         mu += x0 + x1;
@@ -305,7 +336,7 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev S, const StageIn 
         }
     }
     __syncthreads();
-    const double* ysrc = in.direct ? resolve(in, ctl, 0) : S.ybuf;
+    const double* ysrc = in.direct ? resolve_all(in, ctl).p[0] : S.ybuf;
     if (threadIdx.x == 0) {
         const double y1 = (S.M > 0) ? ysrc[0] : 0.0;
         double sig[MAXT], rho[MAXT];

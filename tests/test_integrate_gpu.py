@@ -76,7 +76,8 @@ def test_adaptive_parity_relaxation(smol, scheme, ctrl):
     oa = np.array([x[3] for x in olog])[-k:]
     assert np.array_equal(acc, oa)
     assert np.allclose(h, oh, rtol=1e-5, atol=0)
-    assert np.allclose(e, oe, rtol=1e-5, atol=1e-18)
+    # atol: the oracle forms err from O(1) states, so below ~1e-14 it is rounding noise
+    assert np.allclose(e, oe, rtol=1e-5, atol=1e-14)
 
 
 def test_euler_initial_step(smol):
