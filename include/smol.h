@@ -206,6 +206,27 @@ int smol_get_log(smol_system* sys, double* h_t, double* h_tau, double* h_err,
 /* Number of distinct forward transforms T used per evaluation (<= 2R). */
 int smol_num_transforms(const smol_system* sys);
 
+/* No-allocation evaluation of S(n), FP64. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory or hand over a
+ * workspace (code running while a CUDA graph is captured, hosts without a device
+ * allocator, plug-ins that do not own the process's memory). It needs no system object
+ * and calls no cudaMalloc / cudaFree or allocating library routine.
+ *   M <= SMOL_STATIC_MAX_M, 1 <= R <= SMOL_STATIC_MAX_R, lambda >= 0.
+ *   d_U: device, M x R row-major; d_V: device, R x M row-major; d_n, d_out: device,
+ *   M doubles each, 16-byte aligned, not overlapping. stream: cudaStream_t or NULL.
+ * Its scratch memory is a fixed device array of 12,157,184 bytes inside the library,
+ * which every GPU that loads the library holds until exit. The first call on a device
+ * looks up that array's device address and sets kernel attributes (once per device);
+ * make that first call before any stream capture. All calls on a device share the
+ * array, which keeps the last call's contents: calls that overlap on the GPU race and
+ * must be serialised by the caller. Every call transforms U and V afresh (no
+ * sharing of proportional factors). Returns SMOL_EUNSUPPORTED beyond the limits,
+ * SMOL_EINVAL for bad pointers; does not synchronise. */
+#define SMOL_STATIC_MAX_M 65536
+#define SMOL_STATIC_MAX_R 3
+int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const double* d_V, double lambda,
+                    const double* d_n, double* d_out, void* stream);
+
 /* Releases the system (not the workspace). Safe on NULL. */
 void smol_destroy(smol_system* sys);
 

@@ -75,6 +75,7 @@ SIGNATURES = {
     "smol_num_transforms": (ctypes.c_int, [_P]),
     "smol_destroy": (None, [_P]),
     "smol_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "smol_rhs_static": (ctypes.c_int, [_I64, _I32, _P, _P, _D, _P, _P, _P]),
 }
 
 
@@ -105,6 +106,25 @@ def default_opts() -> Opts:
 
 def max_m(R: int, precision: str = "fp64") -> int:
     return int(_lib.smol_max_m(R, PRECISIONS[precision]))
+
+
+STATIC_MAX_M, STATIC_MAX_R = 65536, 3
+
+
+def rhs_static(U, V, lam: float, n, out=None, stream=None):
+    """smol_rhs_static: S(n) without a system object or workspace (FP64). U (M, R) and
+    V (R, M) are device tensors (or arrays copied to the device); n a device tensor."""
+    torch = _torch()
+    n = torch.as_tensor(n).to(device="cuda", dtype=torch.float64).contiguous()
+    U = torch.as_tensor(U).to(device=n.device, dtype=torch.float64).contiguous()
+    V = torch.as_tensor(V).to(device=n.device, dtype=torch.float64).contiguous()
+    M, R = U.shape
+    if out is None:
+        out = torch.empty_like(n)
+    st = stream if stream is not None else torch.cuda.current_stream(n.device)
+    _check(_lib.smol_rhs_static(M, R, U.data_ptr(), V.data_ptr(), float(lam), n.data_ptr(), out.data_ptr(),
+                                st.cuda_stream), "smol_rhs_static")
+    return out
 
 
 def _check(rc: int, what: str):

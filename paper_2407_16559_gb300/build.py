@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsmol.so")
-SOURCES = ["smol.cu"]
+SOURCES = ["smol.cu", "smol_static.cu"]
 HEADERS = ["smol_fft.cuh", "smol_rhs.cuh", "smol_int.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,176 @@
+// smol_static.cu - smol_rhs_static: one FP64 evaluation of S(n) that allocates
+// nothing. It is for callers that cannot call cudaMalloc or hand over a workspace:
+// code that runs while a CUDA graph is being captured, allocator-free embedded hosts,
+// or plug-in environments where the memory of the process belongs to someone else.
+// Its scratch memory is the file-scope device array below, which every GPU that loads
+// the library holds until the process exits.
+//
+// Limits: M <= SMOL_STATIC_MAX_M (65536), R <= SMOL_STATIC_MAX_R (3). All calls on one
+// device share the array and it keeps the last call's contents; calls that overlap on
+// the GPU (for instance on two streams) race on it and must be serialised by the
+// caller.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include "../../include/smol.h"
+#include "smol_rhs.cuh"
+
+using namespace smol;
+
+namespace {
+
+constexpr int SMAX_M = SMOL_STATIC_MAX_M;
+constexpr int SMAX_R = SMOL_STATIC_MAX_R;
+constexpr int SMAX_T = 2 * SMAX_R;
+constexpr size_t A256 = 256;
+constexpr size_t al(size_t x) { return (x + A256 - 1) / A256 * A256; }
+
+// Layout of the scratch array (byte offsets); sized for M = SMAX_M, T = 2 SMAX_R.
+constexpr size_t OFF_CTL = 0;
+constexpr size_t OFF_TW = OFF_CTL + al(sizeof(Ctl));
+constexpr size_t OFF_W = OFF_TW + al((size_t)SMAX_M * 16);
+constexpr size_t OFF_Y = OFF_W + al((size_t)SMAX_T * SMAX_M * 8);
+constexpr size_t OFF_G2 = OFF_Y + al((size_t)SMAX_T * SMAX_M * 16);
+constexpr size_t OFF_YBUF = OFF_G2 + al((size_t)SMAX_M * 16);
+constexpr size_t OFF_MPART = OFF_YBUF + al((size_t)SMAX_M * 8);
+constexpr size_t SCRATCH_BYTES = OFF_MPART + al((size_t)SMAX_T * 1024 * 2 * 8);
+
+// The scratch memory of smol_rhs_static.
+static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 12,157,184 bytes
+
+constexpr int MAX_DEVICES = 64;
+unsigned char* g_scratch_ptr[MAX_DEVICES];  // device address of g_scratch per device
+bool g_ready[MAX_DEVICES];
+
+// Weights: W_t = column t of U (t < R) and row t - R of V (t >= R), zero beyond M.
+__global__ void k_static_weights(const double* __restrict__ U, const double* __restrict__ V, int M, int Mp, int R,
+                                 double* W) {
+    const int T = 2 * R;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < T * Mp; q += gridDim.x * blockDim.x) {
+        const int t = q / Mp, i = q % Mp;
+        double w = 0.0;
+        if (i < M) w = (t < R) ? U[(size_t)i * R + t] : V[(size_t)(t - R) * M + i];
+        W[q] = w;
+    }
+}
+
+// Twiddles exp(-i pi e / Mp), e < Mp.
+__global__ void k_static_twiddles(int Mp, double2* tw) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Mp; e += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi((double)e / (double)Mp, &s, &c);
+        tw[e] = make_double2(c, -s);
+    }
+}
+
+int ilog2i(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+// Once per device, with that device current: the device address of the scratch array
+// (host code cannot use the symbol itself) and the shared-memory limits of the kernels.
+int setup_device(int dev) {
+    if (dev < 0 || dev >= MAX_DEVICES) return SMOL_EUNSUPPORTED;
+    if (g_ready[dev]) return SMOL_OK;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return SMOL_ECUDA;
+    const int smax = 2 * 256 * 2 * SMAX_T * 16;  // row pass at Mp = SMAX_M
+    if (cudaFuncSetAttribute(k_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax) != cudaSuccess)
+        return SMOL_ECUDA;
+    if (cudaFuncSetAttribute(k_fwd_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_inv_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) !=
+            cudaSuccess)
+        return SMOL_ECUDA;
+    g_scratch_ptr[dev] = (unsigned char*)p;
+    g_ready[dev] = true;
+    return SMOL_OK;
+}
+
+int threads_for_s(int butterflies) {
+    int t = butterflies;
+    if (t > 256) t = 256;
+    if (t < 64) t = 64;
+    return (t + 31) & ~31;
+}
+
+}  // namespace
+
+extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const double* d_V, double lambda,
+                               const double* d_n, double* d_out, void* stream) {
+    if (M < 1 || R < 1 || !d_U || !d_V || !d_n || !d_out || !(lambda >= 0.0)) return SMOL_EINVAL;
+    if (M > SMAX_M || R > SMAX_R) return SMOL_EUNSUPPORTED;
+    if (((uintptr_t)d_n & 15) || ((uintptr_t)d_out & 15)) return SMOL_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SMOL_ECUDA;
+    int rc = setup_device(dev);
+    if (rc != SMOL_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* base = g_scratch_ptr[dev];
+
+    const int lgMp = ilog2i(M < 4 ? 4 : M);
+    const int Mp = 1 << lgMp;
+    const int lgN1 = (lgMp + 1) / 2, lgN2 = lgMp / 2;
+    const int N1 = 1 << lgN1, N2 = 1 << lgN2;
+    int G = N2 / 128;
+    if (G < 1) G = 1;
+    if (G > 8) G = 8;
+    const int T = 2 * R;
+
+    SysDev d;
+    memset(&d, 0, sizeof(d));
+    d.M = (int)M;
+    d.Mp = Mp;
+    d.lgMp = lgMp;
+    d.N1 = N1;
+    d.N2 = N2;
+    d.lgN1 = lgN1;
+    d.lgN2 = lgN2;
+    d.T = T;
+    d.R = R;
+    d.lambda = lambda;
+    d.nbxA = N2 / G;
+    d.npairs = R;
+    for (int a = 0; a < R; ++a) {
+        d.au[a] = a;
+        d.av[a] = R + a;
+        d.acoef[a] = 1.0;
+        d.pu[a] = a;
+        d.pv[a] = R + a;
+        d.pcoef[a] = 1.0;
+    }
+    d.W = (const double*)(base + OFF_W);
+    d.tw = base + OFF_TW;
+    d.Y = base + OFF_Y;
+    d.G2 = base + OFF_G2;
+    d.ybuf = (double*)(base + OFF_YBUF);
+    d.mpart = (double*)(base + OFF_MPART);
+    Ctl* ctl = (Ctl*)(base + OFF_CTL);
+
+    // The control block must read "not done" and the weights must be zero beyond M:
+    // both are rewritten on every call, since the array keeps the previous call's data.
+    if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), st) != cudaSuccess) return SMOL_ECUDA;
+    k_static_weights<<<256, 256, 0, st>>>(d_U, d_V, (int)M, Mp, R, (double*)(base + OFF_W));
+    k_static_twiddles<<<64, 256, 0, st>>>(Mp, (double2*)(base + OFF_TW));
+
+    StageIn in;
+    memset(&in, 0, sizeof(in));
+    in.nv = 1;
+    in.direct = 1;
+    in.sel[0] = -1;
+    in.v[0] = d_n;
+    in.c[0] = 1.0;
+    EpiOut eo;
+    memset(&eo, 0, sizeof(eo));
+    eo.out = d_out;
+    eo.hfac = 1.0;
+    const size_t sc = 2 * (size_t)N1 * G * 16, sr = 2 * (size_t)N2 * 2 * T * 16;
+    const int nbx = N2 / G;
+    k_fwd_cols<double><<<dim3(nbx, T), threads_for_s((N1 / 4) * G), sc, st>>>(d, in, ctl, G);
+    k_rows<double><<<N1 / 2, threads_for_s((N2 / 4) * 2 * T), sr, st>>>(d, ctl);
+    k_inv_cols<double><<<nbx, threads_for_s((N1 / 4) * G), sc, st>>>(d, in, ctl, eo, G);
+    return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
+}
