@@ -109,6 +109,7 @@ typedef struct smol_stats {
     double  t;               /* time reached */
     double  tau_next;        /* proposed next step (resume with tau0 = tau_next) */
     double  err_last;        /* error estimate of the last attempt */
+    double  mass;            /* sum_s s n_s of the final state (FP64) */
     int64_t rhs_evals;       /* S(n) evaluations actually made */
     int64_t rhs_evals_paper; /* stages x RK steps evaluated, the count of the paper's tables */
     int64_t accepted;
@@ -206,6 +207,31 @@ int smol_get_log(smol_system* sys, double* h_t, double* h_tau, double* h_err,
 /* Number of distinct forward transforms T used per evaluation (<= 2R). */
 int smol_num_transforms(const smol_system* sys);
 
+/* ---- Batches of independent systems -------------------------------------------
+ * `count` independent systems of Eq. (4) with their own size M[q], kernel factors
+ * h_U[q] (M[q] x R) and h_V[q] (R x M[q]) and shattering rate lambda[q], sharing R,
+ * the options and the tolerance. Every kernel launch of an integration spans all
+ * systems (ragged block maps); each system keeps its own t, tau, controller state and
+ * status, and stops on its own. Arguments follow the single-system calls; d_n is a
+ * host array of `count` device pointers; stats (when non-NULL) has `count` entries.
+ * smol_batch_integrate returns the first error status of any system, else SMOL_STEADY
+ * if some system stopped at a steady state, else SMOL_OK. */
+typedef struct smol_batch smol_batch;
+size_t smol_batch_workspace_bytes(int32_t count, const int64_t* M, int32_t R, const smol_opts* opts);
+int smol_batch_init(smol_batch** batch, int32_t count, const int64_t* M, int32_t R,
+                    const double* const* h_U, const double* const* h_V, const double* lambda,
+                    const smol_opts* opts, void* d_workspace, size_t workspace_bytes);
+int smol_batch_set_stream(smol_batch* batch, void* stream);
+int smol_batch_integrate(smol_batch* batch, double* const* d_n, double t0, double t1, double tol,
+                         int32_t scheme, smol_stats* stats);
+int smol_batch_integrate_start(smol_batch* batch, double* const* d_n, double t0, double t1,
+                               double tol, int32_t scheme);
+int smol_batch_integrate_advance(smol_batch* batch);
+int smol_batch_integrate_finish(smol_batch* batch, smol_stats* stats);
+int smol_batch_get_log(smol_batch* batch, int32_t system, double* h_t, double* h_tau,
+                       double* h_err, int32_t* h_accepted, int32_t cap, int64_t* count);
+void smol_batch_destroy(smol_batch* batch);
+
 /* No-allocation evaluation of S(n), FP64. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory or hand over a
  * workspace (code running while a CUDA graph is captured, hosts without a device
@@ -214,7 +240,7 @@ int smol_num_transforms(const smol_system* sys);
  *   M <= SMOL_STATIC_MAX_M, 1 <= R <= SMOL_STATIC_MAX_R, lambda >= 0.
  *   d_U: device, M x R row-major; d_V: device, R x M row-major; d_n, d_out: device,
  *   M doubles each, 16-byte aligned, not overlapping. stream: cudaStream_t or NULL.
- * Its scratch memory is a fixed device array of 12,157,184 bytes inside the library,
+ * Its scratch memory is a fixed device array of 12,174,336 bytes inside the library,
  * which every GPU that loads the library holds until exit. The first call on a device
  * looks up that array's device address and sets kernel attributes (once per device);
  * make that first call before any stream capture. All calls on a device share the

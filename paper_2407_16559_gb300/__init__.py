@@ -46,7 +46,7 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [
         ("t", ctypes.c_double), ("tau_next", ctypes.c_double), ("err_last", ctypes.c_double),
-        ("rhs_evals", ctypes.c_int64), ("rhs_evals_paper", ctypes.c_int64), ("accepted", ctypes.c_int64),
+        ("mass", ctypes.c_double), ("rhs_evals", ctypes.c_int64), ("rhs_evals_paper", ctypes.c_int64), ("accepted", ctypes.c_int64),
         ("rejected", ctypes.c_int64), ("attempts", ctypes.c_int64), ("status", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
@@ -76,6 +76,16 @@ SIGNATURES = {
     "smol_destroy": (None, [_P]),
     "smol_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "smol_rhs_static": (ctypes.c_int, [_I64, _I32, _P, _P, _D, _P, _P, _P]),
+    "smol_batch_workspace_bytes": (_SZ, [_I32, _P, _I32, ctypes.POINTER(Opts)]),
+    "smol_batch_init": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _P, _I32, _P, _P, _P, ctypes.POINTER(Opts), _P,
+                                       _SZ]),
+    "smol_batch_set_stream": (ctypes.c_int, [_P, _P]),
+    "smol_batch_integrate": (ctypes.c_int, [_P, _P, _D, _D, _D, _I32, _P]),
+    "smol_batch_integrate_start": (ctypes.c_int, [_P, _P, _D, _D, _D, _I32]),
+    "smol_batch_integrate_advance": (ctypes.c_int, [_P]),
+    "smol_batch_integrate_finish": (ctypes.c_int, [_P, _P]),
+    "smol_batch_get_log": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _I32, ctypes.POINTER(_I64)]),
+    "smol_batch_destroy": (None, [_P]),
 }
 
 
@@ -136,6 +146,107 @@ def _check(rc: int, what: str):
 def _torch():
     import torch  # imported lazily: the CPU-only symbol tests need no torch
     return torch
+
+
+def _make_opts(precision: str, stream, device, opts: dict):
+    torch = _torch()
+    o = default_opts()
+    o.precision = PRECISIONS[precision]
+    for k, v in opts.items():
+        if k == "ctrl":
+            v = CTRLS[v]
+        elif k == "norm":
+            v = NORMS[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    dev = torch.device(device if device is not None else "cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    o.stream = ctypes.c_void_p(stream.cuda_stream)
+    return o, dev, stream
+
+
+class Batch:
+    """A batch of independent systems advanced together (smol_batch_*): systems q =
+    0..count-1 with U[q] (M_q, R), V[q] (R, M_q), lam[q]; the same options for all."""
+
+    def __init__(self, Us, Vs, lams, precision: str = "fp64", stream=None, device=None, **opts):
+        torch = _torch()
+        self.U = [np.ascontiguousarray(u, dtype=np.float64) for u in Us]
+        self.V = [np.ascontiguousarray(v, dtype=np.float64) for v in Vs]
+        self.count = len(self.U)
+        self.R = self.U[0].shape[1]
+        self.M = np.array([u.shape[0] for u in self.U], dtype=np.int64)
+        for u, v in zip(self.U, self.V):
+            if u.shape[1] != self.R or v.shape != (self.R, u.shape[0]):
+                raise ValueError("every U must be (M_q, R) and V (R, M_q) with the same R")
+        self.lam = np.ascontiguousarray(lams, dtype=np.float64)
+        self.opts, self.device, self.stream = _make_opts(precision, stream, device, opts)
+        nbytes = int(_lib.smol_batch_workspace_bytes(self.count, self.M.ctypes.data, self.R, ctypes.byref(self.opts)))
+        if nbytes == 0:
+            raise SmolError(EUNSUPPORTED, "batch shape")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        ws = (self.workspace.data_ptr() + 255) & ~255
+        self._pU = (ctypes.c_void_p * self.count)(*[u.ctypes.data for u in self.U])
+        self._pV = (ctypes.c_void_p * self.count)(*[v.ctypes.data for v in self.V])
+        self._h = ctypes.c_void_p()
+        _check(_lib.smol_batch_init(ctypes.byref(self._h), self.count, self.M.ctypes.data, self.R, self._pU, self._pV,
+                                    self.lam.ctypes.data, ctypes.byref(self.opts), ws, nbytes), "smol_batch_init")
+
+    def _states(self, ns):
+        torch = _torch()
+        out = []
+        for q, n in enumerate(ns):
+            if not isinstance(n, torch.Tensor):
+                n = torch.as_tensor(np.asarray(n, dtype=np.float64))
+            n = n.to(device=self.device, dtype=torch.float64).contiguous()
+            if n.numel() != self.M[q]:
+                raise ValueError(f"state {q} has {n.numel()} entries, expected {self.M[q]}")
+            out.append(n)
+        return out, (ctypes.c_void_p * self.count)(*[n.data_ptr() for n in out])
+
+    def integrate(self, n0s, t0: float, t1: float, tol: float, scheme: str = "rkf45", inplace: bool = False):
+        """Integrates every system from t0 to t1; returns (list of device states, list
+        of stats dicts)."""
+        ns, ptrs = self._states(n0s)
+        if not inplace:
+            ns = [n.clone() for n in ns]
+            ptrs = (ctypes.c_void_p * self.count)(*[n.data_ptr() for n in ns])
+        st = (Stats * self.count)()
+        rc = _lib.smol_batch_integrate(self._h, ptrs, float(t0), float(t1), float(tol), SCHEMES[scheme], st)
+        if rc in (EINVAL, ECUDA, ENOSPACE, EUNSUPPORTED):
+            raise SmolError(rc, "smol_batch_integrate")
+        return ns, [s.as_dict() for s in st]
+
+    def start(self, n0s, t0, t1, tol, scheme="rkf45"):
+        ns, ptrs = self._states(n0s)
+        self._run = ns
+        _check(_lib.smol_batch_integrate_start(self._h, ptrs, float(t0), float(t1), float(tol), SCHEMES[scheme]),
+               "smol_batch_integrate_start")
+        return ns
+
+    def advance(self):
+        _check(_lib.smol_batch_integrate_advance(self._h), "smol_batch_integrate_advance")
+
+    def finish(self):
+        st = (Stats * self.count)()
+        rc = _lib.smol_batch_integrate_finish(self._h, st)
+        if rc in (EINVAL, ECUDA):
+            raise SmolError(rc, "smol_batch_integrate_finish")
+        ns, self._run = self._run, None
+        return ns, [s.as_dict() for s in st]
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.smol_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class System:

@@ -1,13 +1,16 @@
-// smol.cu - host side of the C interface declared in include/smol.h: system set-up
-// (distinct transforms, weights, twiddles, workspace layout), one evaluation of
-// S(n) as three kernel launches, and the device-resident adaptive integrators of
-// Sec. 2 driven through captured CUDA graphs.
+// smol.cu - host side of the C interface declared in include/smol.h: set-up of one
+// system or of a ragged batch of independent systems (distinct transforms, weights,
+// twiddles, FFT schedule, workspace layout, block maps), one evaluation of S(n) as three
+// kernel launches, and the device-resident adaptive integrators of Sec. 2 driven
+// through captured CUDA graphs. A single system is a batch of one: the kernels of a
+// launch span every system of the batch.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/smol.h"
@@ -17,9 +20,10 @@ using namespace smol;
 
 namespace {
 
-constexpr int NVEC = 12;        // stage / work vectors of the integrators
-constexpr int FIN_BLOCKS = 608; // 4 x 152 SMs (128-thread CTAs)
-constexpr int PREP_BLOCKS = 152;
+constexpr int FIN_THREADS = 128;
+constexpr int FIN_MAX_BLOCKS = 608;  // per system (4 x 152 SMs)
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+constexpr int MAX_BATCH = 1 << 16;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -29,12 +33,11 @@ int ilog2(int64_t v) {
     return l;
 }
 
-// Largest dynamic shared memory a kernel may use (opt-in limit of sm_100-class parts).
-constexpr size_t SMEM_LIMIT = 227 * 1024;
-
+// FFT schedule of one system size: the four-step split Mp = N1 x N2 and the number G of
+// adjacent columns per CTA of the column passes.
 struct Shape {
-    int M, Mp, lgMp, N1, N2, lgN1, lgN2, G;
-    size_t csz;  // bytes of one complex value
+    int M, Mp, lgMp, N1, N2, lgN1, lgN2, G, nfin;
+    size_t csz, rsz;  // bytes of one complex / one real value of the compute type
 };
 
 Shape make_shape(int64_t M, int precision) {
@@ -46,23 +49,43 @@ Shape make_shape(int64_t M, int precision) {
     s.lgN2 = s.lgMp / 2;
     s.N1 = 1 << s.lgN1;
     s.N2 = 1 << s.lgN2;
-    // columns per CTA of the column passes: one column of N1 >= 256 points per CTA
-    // (many small CTAs spread the latency-bound passes over all SMs), more columns for
-    // short columns so that a CTA keeps at least 32 radix-8 butterflies per pass
+    // one column of N1 >= 256 points per CTA; several short columns per CTA so that a
+    // CTA keeps at least 32 radix-8 butterflies per pass
     int G = 256 / s.N1;
     if (G < 1) G = 1;
     if (G > s.N2) G = s.N2;
     s.G = G;
+    int nf = (s.M / 2 + FIN_THREADS - 1) / FIN_THREADS;
+    s.nfin = std::max(1, std::min(nf, FIN_MAX_BLOCKS));
     s.csz = precision == SMOL_FP32CONV ? 8 : 16;
+    s.rsz = s.csz / 2;
     return s;
 }
 
-size_t smem_cols(const Shape& s) { return 2 * (size_t)s.N1 * s.G * s.csz; }
-size_t smem_rows(const Shape& s, int T) { return 2 * (size_t)s.N2 * 2 * T * s.csz; }
+// Dynamic shared memory of the column kernels (the larger of the forward pass: T*G
+// interleaved sequences, tile and four-step twiddles, y; and the inverse pass) and of
+// the row kernel (2T rows, tile twiddles, spectral and inverse four-step twiddles).
+size_t smem_cols(const Shape& s, int T) {
+    const size_t n = (size_t)s.N1 * s.G;
+    const size_t fwd = 2 * n * T * s.csz + (size_t)s.N1 * s.csz + n * s.csz + n * s.rsz;
+    const size_t inv = 2 * n * s.csz + (size_t)s.N1 * s.csz;
+    return std::max(fwd, inv);
+}
+size_t smem_rows(const Shape& s, int T) { return 2 * (size_t)s.N2 * 2 * T * s.csz + 5 * (size_t)s.N2 * s.csz; }
 
+// Threads of a CTA whose passes cover `points` points: one per radix-8 butterfly,
+// between 32 and 256.
+int threads_for(int points) {
+    int t = points / 8;
+    if (t > 256) t = 256;
+    if (t < 32) t = 32;
+    return (t + 31) & ~31;
+}
+
+// Per-system part of the workspace.
 struct Layout {
-    size_t ctl, rctl, tw, W, Y, G2, ybuf, vec, stateB, mpart, fpart, sqpart, ppart, delta, log_t, log_h, log_e, log_a,
-        total;
+    size_t tw, W, Y, G2, ybuf, vec, half, stateB, mpart, fpart, sqpart, aux, log_t, log_h, log_e, log_a, total;
+    size_t vstride;  // elements between work vectors
 };
 
 Layout make_layout(const Shape& s, int R, int log_cap) {
@@ -74,26 +97,57 @@ Layout make_layout(const Shape& s, int R, int log_cap) {
         o += align256(bytes);
         return r;
     };
-    L.ctl = take(sizeof(Ctl));
-    L.rctl = take(sizeof(Ctl));
     L.tw = take((size_t)s.Mp * s.csz);
-    L.W = take((size_t)Tm * s.Mp * 8);
+    L.W = take((size_t)Tm * s.Mp * s.rsz);
     L.Y = take((size_t)Tm * s.Mp * s.csz);
     L.G2 = take((size_t)s.Mp * s.csz);
-    L.ybuf = take((size_t)s.Mp * 8);
-    L.vec = take((size_t)NVEC * align256((size_t)s.Mp * 8));
+    L.ybuf = take((size_t)s.Mp * s.rsz);
+    L.vstride = align256((size_t)s.Mp * s.rsz) / s.rsz;
+    L.vec = take((size_t)NVEC * L.vstride * s.rsz);
+    L.half = take((size_t)s.Mp * 8);
     L.stateB = take((size_t)s.Mp * 8);
     L.mpart = take((size_t)Tm * (s.N2 / s.G) * 2 * 8);
-    L.fpart = take((size_t)FIN_BLOCKS * 4 * 8);
+    L.fpart = take((size_t)s.nfin * FPW * 8);
     L.sqpart = take((size_t)(s.N2 / s.G) * 8);
-    L.ppart = take((size_t)PREP_BLOCKS * (MAXT + 2) * 8);
-    L.delta = take((size_t)MAXT * 8);
+    L.aux = take((size_t)(MAXT + 1) * 8);
     L.log_t = take((size_t)log_cap * 8);
     L.log_h = take((size_t)log_cap * 8);
     L.log_e = take((size_t)log_cap * 8);
     L.log_a = take((size_t)log_cap * 4);
     L.total = o;
     return L;
+}
+
+// Header of a batch workspace: control blocks, descriptors and block maps.
+struct Header {
+    size_t ctl, rctl, sys, sysr, mapC, mapB, mapF, total;
+    int nC, nB, nF;  // blocks of the column / row / finish launches
+};
+
+Header make_header(const std::vector<Shape>& sh) {
+    Header H;
+    const size_t n = sh.size();
+    H.nC = H.nB = H.nF = 0;
+    for (const Shape& s : sh) {
+        H.nC += s.N2 / s.G;
+        H.nB += s.N1 / 2;
+        H.nF += s.nfin;
+    }
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o += align256(bytes);
+        return r;
+    };
+    H.ctl = take(n * sizeof(Ctl));
+    H.rctl = take(n * sizeof(Ctl));
+    H.sys = take(n * sizeof(SysDev));
+    H.sysr = take(n * sizeof(SysDev));
+    H.mapC = take((size_t)H.nC * sizeof(int2));
+    H.mapB = take((size_t)H.nB * sizeof(int2));
+    H.mapF = take((size_t)H.nF * sizeof(int2));
+    H.total = o;
+    return H;
 }
 
 void default_opts(smol_opts* o) {
@@ -132,57 +186,27 @@ bool proportional(const double* x, const double* w, int M, double* c) {
     return true;
 }
 
-}  // namespace
-
-struct smol_system {
-    Shape s;
-    int R, T;
-    double lambda;
-    smol_opts o;
-    cudaStream_t stream;
-    cudaStream_t cap;  // private stream used only for graph capture
-    char* ws;
-    Layout L;
-    SysDev dev;
-    Ctl* ctl;
-    Ctl* rctl;
-    Ctl* h_ctl;  // pinned host copy
-    double* vec[NVEC];
-    double* stateB;
-    // cached graph of one chunk, keyed by (scheme, fixed, steady, log)
-    cudaGraphExec_t gexec;
-    int gkey;
-    int64_t last_attempts;
-    // current run (smol_integrate_start .. smol_integrate_finish)
-    double* run_dn;
-    int run_scheme;
-    int64_t run_attempts;
-};
-
-// ---------------------------------------------------------------------------
-// Launch helpers
-// ---------------------------------------------------------------------------
-namespace {
-
-template <typename R>
-int set_smem_attrs(const smol_system* S) {
-    const size_t sc = smem_cols(S->s), sr = smem_rows(S->s, S->T);
-    if (cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc) != cudaSuccess)
-        return SMOL_ECUDA;
-    if (cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc) != cudaSuccess)
-        return SMOL_ECUDA;
-    if (cudaFuncSetAttribute(k_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr) != cudaSuccess)
-        return SMOL_ECUDA;
-    return SMOL_OK;
+int64_t max_m_for(int32_t R, int32_t precision) {
+    if (R < 1 || R > MAXR) return 0;
+    int64_t best = 0;
+    for (int lg = 2; lg <= 22; ++lg) {
+        Shape s = make_shape((int64_t)1 << lg, precision);
+        if (smem_cols(s, 2 * R) <= SMEM_LIMIT && smem_rows(s, 2 * R) <= SMEM_LIMIT) best = (int64_t)1 << lg;
+    }
+    return best;
 }
 
-// Threads of a CTA whose passes have `points` points per sequence-group: one thread per
-// radix-8 butterfly, between 32 and 256.
-int threads_for(int points) {
-    int t = points / 8;
-    if (t > 256) t = 256;
-    if (t < 32) t = 32;
-    return (t + 31) & ~31;
+size_t batch_bytes(int count, const int64_t* M, int R, const smol_opts& o) {
+    if (count < 1 || count > MAX_BATCH || R < 1 || R > MAXR) return 0;
+    const int64_t mm = max_m_for(R, o.precision);
+    std::vector<Shape> sh;
+    size_t tot = 0;
+    for (int q = 0; q < count; ++q) {
+        if (M[q] < 1 || M[q] > mm) return 0;
+        sh.push_back(make_shape(M[q], o.precision));
+        tot += make_layout(sh.back(), R, std::max(o.log_capacity, 0)).total;
+    }
+    return make_header(sh).total + tot;
 }
 
 // Optional per-kernel timing of eagerly launched attempts (smol_profile_attempts).
@@ -208,184 +232,191 @@ struct ProfScope {
     }
 };
 
+}  // namespace
+
+// The engine behind both opaque handles: a batch of `count` systems (count = 1 for
+// smol_system).
+struct Engine {
+    int count = 0, R = 0;
+    smol_opts o{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    char* ws = nullptr;
+    Header H{};
+    std::vector<Shape> sh;
+    std::vector<Layout> lay;
+    std::vector<size_t> base;  // byte offset of each system's region
+    std::vector<int> T;
+    SysDev* d_sys = nullptr;   // descriptors used by integrations (control blocks ctl)
+    SysDev* d_sysr = nullptr;  // descriptors of standalone evaluations (control blocks rctl)
+    Ctl* d_ctl = nullptr;
+    Ctl* d_rctl = nullptr;
+    int2 *mapC = nullptr, *mapB = nullptr, *mapF = nullptr;
+    size_t smemC = 0, smemB = 0;
+    int thrC = 32, thrB = 32;
+    Ctl* h_ctl = nullptr;  // pinned host copies of the control blocks
+    cudaGraphExec_t gexec = nullptr;
+    int64_t gkey = -1;
+    std::vector<int64_t> last_attempts;
+    bool running = false;
+    int run_scheme = 0;
+    int64_t run_attempts = 1;
+    std::vector<double*> run_dn;
+};
+
+struct smol_system : Engine {};
+struct smol_batch : Engine {};
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+namespace {
+
 template <typename R>
-void launch_eval(const smol_system* S, const StageIn& in, const Ctl* ctl, const EpiOut& eo, cudaStream_t st,
+int set_smem_attrs(const Engine* E) {
+    if (cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemC) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemC) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemB) != cudaSuccess)
+        return SMOL_ECUDA;
+    return SMOL_OK;
+}
+
+template <typename R>
+void launch_eval(const Engine* E, const SysDev* sys, const StageIn& in, const EpiOut& eo, cudaStream_t st,
                  Prof* pr) {
-    const Shape& s = S->s;
-    const int nbx = s.N2 / s.G;
-    const size_t sc = smem_cols(s), sr = smem_rows(s, S->T);
     {
         ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
-        k_fwd_cols<R><<<dim3(nbx, S->T), threads_for(s.N1 * s.G), sc, st>>>(S->dev, in, ctl, s.G);
+        k_fwd_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(sys, E->mapC, in);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_ROWS);
-        k_rows<R><<<s.N1 / 2, threads_for(s.N2 * 2 * S->T), sr, st>>>(S->dev, ctl);
+        k_rows<R><<<E->H.nB, E->thrB, E->smemB, st>>>(sys, E->mapB);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
-        k_inv_cols<R><<<nbx, threads_for(s.N1 * s.G), sc, st>>>(S->dev, in, ctl, eo, s.G);
+        k_inv_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(sys, E->mapC, in, eo);
     }
 }
 
-void eval(const smol_system* S, const StageIn& in, const Ctl* ctl, const EpiOut& eo, cudaStream_t st,
-          Prof* pr = nullptr) {
-    if (S->o.precision == SMOL_FP32CONV) launch_eval<float>(S, in, ctl, eo, st, pr);
-    else launch_eval<double>(S, in, ctl, eo, st, pr);
-}
-
-StageIn stage(std::initializer_list<std::pair<int, double>> terms, const smol_system* S) {
-    // term index: -1 = current state, -2 = other state, k >= 0 = work vector k
+StageIn stage(std::initializer_list<std::pair<int, double>> terms) {
+    // term index: SLOT_* (< 0) or a work vector k >= 0
     StageIn in;
     memset(&in, 0, sizeof(in));
-    in.nv = 0;
     for (auto& tc : terms) {
         const int j = in.nv++;
-        if (tc.first == -1) {
-            in.sel[j] = 0;
-            in.v[j] = nullptr;
-        } else if (tc.first == -2) {
-            in.sel[j] = 1;
-            in.v[j] = nullptr;
-        } else {
-            in.sel[j] = -1;
-            in.v[j] = S->vec[tc.first];
-        }
+        in.slot[j] = tc.first;
         in.c[j] = tc.second;
     }
-    in.direct = 0;
     return in;
 }
 
-StageIn from_ptr(const double* p) {
-    StageIn in;
-    memset(&in, 0, sizeof(in));
-    in.nv = 1;
-    in.direct = 1;
-    in.sel[0] = -1;
-    in.v[0] = p;
-    in.c[0] = 1.0;
-    return in;
-}
-
-EpiOut epi_k(double* out, double hfac, double* sqpart) {
+EpiOut epi_k(int slot, double hfac, int sq) {
     EpiOut e;
     memset(&e, 0, sizeof(e));
-    e.out = out;
+    e.out_slot = slot;
     e.hfac = hfac;
-    e.use_h = 1;
-    e.sqpart = sqpart;
+    e.sq = sq;
     return e;
 }
 
-constexpr int FIN_THREADS = 128;
-
-int fin_blocks(int M) {
-    int b = (M / 2 + FIN_THREADS - 1) / FIN_THREADS;
-    if (b < 1) b = 1;
-    if (b > FIN_BLOCKS) b = FIN_BLOCKS;
-    return b;
-}
-
-// Enqueues one step attempt of the given scheme on stream st.
-void enqueue_attempt(smol_system* S, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
-    double* sq = (double*)(S->ws + S->L.sqpart);
-    double* fpart = (double*)(S->ws + S->L.fpart);
-    const int M = S->s.M;
-    Ctl* c = S->ctl;
-    auto E = [&](const StageIn& in, int k, double hfac, bool first) {
-        eval(S, in, c, epi_k(S->vec[k], hfac, (first && P.sqpart) ? sq : nullptr), st, pr);
+// Enqueues one step attempt of every system of the batch on stream st.
+template <typename R>
+void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
+    const SysDev* sys = E->d_sys;
+    auto Ev = [&](const StageIn& in, int k, double hfac, bool first) {
+        launch_eval<R>(E, sys, in, epi_k(k, hfac, (first && P.steady) ? 1 : 0), st, pr);
     };
+    auto finish = [&](const StageIn& cand, const StageIn& del) {
+        ProfScope ps(pr, st, SMOL_PROF_STEP);
+        k_finish<R><<<E->H.nF, FIN_THREADS, 0, st>>>(sys, E->mapF, cand, del, P);
+    };
+    auto half = [&](const StageIn& in) {
+        ProfScope ps(pr, st, SMOL_PROF_STEP);
+        k_lincomb<R><<<E->H.nF, FIN_THREADS, 0, st>>>(sys, E->mapF, in);
+    };
+    const int N = SLOT_CUR, H = SLOT_HALF;
     if (scheme == SCHEME_RKF45) {
-        E(stage({{-1, 1.0}}, S), 0, 1.0, true);
-        E(stage({{-1, 1.0}, {0, 0.25}}, S), 1, 1.0, false);
-        E(stage({{-1, 1.0}, {0, 3.0 / 32.0}, {1, 9.0 / 32.0}}, S), 2, 1.0, false);
-        E(stage({{-1, 1.0}, {0, 1932.0 / 2197.0}, {1, -7200.0 / 2197.0}, {2, 7296.0 / 2197.0}}, S), 3, 1.0, false);
-        E(stage({{-1, 1.0}, {0, 439.0 / 216.0}, {1, -8.0}, {2, 3680.0 / 513.0}, {3, -845.0 / 4104.0}}, S), 4, 1.0,
-          false);
-        E(stage({{-1, 1.0},
-                 {0, -8.0 / 27.0},
-                 {1, 2.0},
-                 {2, -3544.0 / 2565.0},
-                 {3, 1859.0 / 4104.0},
-                 {4, -11.0 / 40.0}},
-                S),
-          5, 1.0, false);
-        StageIn cand = stage({{-1, 1.0}, {0, 25.0 / 216.0}, {2, 1408.0 / 2565.0}, {3, 2197.0 / 4104.0}, {4, -1.0 / 5.0}}, S);
-        // n_RK5 - n^{k+1}: differences of the two weight rows of the tableau
-        StageIn del = stage({{0, 16.0 / 135.0 - 25.0 / 216.0},
-                             {2, 6656.0 / 12825.0 - 1408.0 / 2565.0},
-                             {3, 28561.0 / 56430.0 - 2197.0 / 4104.0},
-                             {4, -9.0 / 50.0 + 1.0 / 5.0},
-                             {5, 2.0 / 55.0}},
-                            S);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
+        Ev(stage({{N, 1.0}}), 0, 1.0, true);
+        Ev(stage({{N, 1.0}, {0, 0.25}}), 1, 1.0, false);
+        Ev(stage({{N, 1.0}, {0, 3.0 / 32.0}, {1, 9.0 / 32.0}}), 2, 1.0, false);
+        Ev(stage({{N, 1.0}, {0, 1932.0 / 2197.0}, {1, -7200.0 / 2197.0}, {2, 7296.0 / 2197.0}}), 3, 1.0, false);
+        Ev(stage({{N, 1.0}, {0, 439.0 / 216.0}, {1, -8.0}, {2, 3680.0 / 513.0}, {3, -845.0 / 4104.0}}), 4, 1.0,
+           false);
+        Ev(stage({{N, 1.0},
+                  {0, -8.0 / 27.0},
+                  {1, 2.0},
+                  {2, -3544.0 / 2565.0},
+                  {3, 1859.0 / 4104.0},
+                  {4, -11.0 / 40.0}}),
+           5, 1.0, false);
+        // n^{k+1} (fourth order) and n_RK5 - n^{k+1} from the differences of the two
+        // weight rows of the tableau
+        finish(stage({{N, 1.0}, {0, 25.0 / 216.0}, {2, 1408.0 / 2565.0}, {3, 2197.0 / 4104.0}, {4, -1.0 / 5.0}}),
+               stage({{0, 16.0 / 135.0 - 25.0 / 216.0},
+                      {2, 6656.0 / 12825.0 - 1408.0 / 2565.0},
+                      {3, 28561.0 / 56430.0 - 2197.0 / 4104.0},
+                      {4, -9.0 / 50.0 + 1.0 / 5.0},
+                      {5, 2.0 / 55.0}}));
         return;
     }
     if (scheme == SCHEME_RK2) {
-        E(stage({{-1, 1.0}}, S), 0, 1.0, true);                      // k1 = h S(n)
-        E(stage({{-1, 1.0}, {0, 1.0}}, S), 1, 1.0, false);           // k2 = h S(n + k1)
+        Ev(stage({{N, 1.0}}), 0, 1.0, true);            // k1 = h S(n)
+        Ev(stage({{N, 1.0}, {0, 1.0}}), 1, 1.0, false);  // k2 = h S(n + k1)
         if (fixed) {
-            StageIn cand = stage({{-1, 1.0}, {0, 0.5}, {1, 0.5}}, S);
-            StageIn del = stage({{0, 0.0}}, S);
-            { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
+            finish(stage({{N, 1.0}, {0, 0.5}, {1, 0.5}}), stage({{0, 0.0}}));
             return;
         }
         // half step 1: l1 = k1/2, l2 = (h/2) S(n + k1/2); n_half = n + (l1 + l2)/2
-        E(stage({{-1, 1.0}, {0, 0.5}}, S), 2, 0.5, false);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), FIN_THREADS, 0, st>>>(stage({{-1, 1.0}, {0, 0.25}, {2, 0.5}}, S), c, S->vec[3], M); }
-        // half step 2 from n_half: m1, m2
-        E(stage({{3, 1.0}}, S), 4, 0.5, false);
-        E(stage({{3, 1.0}, {4, 1.0}}, S), 5, 0.5, false);
-        StageIn cand = stage({{3, 1.0}, {4, 0.5}, {5, 0.5}}, S);
-        StageIn del = stage({{3, 1.0}, {4, 0.5}, {5, 0.5}, {-1, -1.0}, {0, -0.5}, {1, -0.5}}, S);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
+        Ev(stage({{N, 1.0}, {0, 0.5}}), 2, 0.5, false);
+        half(stage({{N, 1.0}, {0, 0.25}, {2, 0.5}}));
+        // half step 2 from n_half: m1, m2; error n_hat - n^{k+1}
+        Ev(stage({{H, 1.0}}), 4, 0.5, false);
+        Ev(stage({{H, 1.0}, {4, 1.0}}), 5, 0.5, false);
+        finish(stage({{H, 1.0}, {4, 0.5}, {5, 0.5}}),
+               stage({{H, 1.0}, {4, 0.5}, {5, 0.5}, {N, -1.0}, {0, -0.5}, {1, -0.5}}));
         return;
     }
     // RK4
-    E(stage({{-1, 1.0}}, S), 0, 1.0, true);                          // k1
-    E(stage({{-1, 1.0}, {0, 0.5}}, S), 1, 1.0, false);               // k2
-    E(stage({{-1, 1.0}, {1, 0.5}}, S), 2, 1.0, false);               // k3
-    E(stage({{-1, 1.0}, {2, 1.0}}, S), 3, 1.0, false);               // k4
+    Ev(stage({{N, 1.0}}), 0, 1.0, true);            // k1
+    Ev(stage({{N, 1.0}, {0, 0.5}}), 1, 1.0, false);  // k2
+    Ev(stage({{N, 1.0}, {1, 0.5}}), 2, 1.0, false);  // k3
+    Ev(stage({{N, 1.0}, {2, 1.0}}), 3, 1.0, false);  // k4
     if (fixed) {
-        StageIn cand = stage({{-1, 1.0}, {0, 1.0 / 6.0}, {1, 1.0 / 3.0}, {2, 1.0 / 3.0}, {3, 1.0 / 6.0}}, S);
-        StageIn del = stage({{0, 0.0}}, S);
-        { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
+        finish(stage({{N, 1.0}, {0, 1.0 / 6.0}, {1, 1.0 / 3.0}, {2, 1.0 / 3.0}, {3, 1.0 / 6.0}}), stage({{0, 0.0}}));
         return;
     }
     // half step 1 with h/2: l1 = k1/2
-    E(stage({{-1, 1.0}, {0, 0.25}}, S), 4, 0.5, false);              // l2 = (h/2) S(n + l1/2)
-    E(stage({{-1, 1.0}, {4, 0.5}}, S), 5, 0.5, false);               // l3
-    E(stage({{-1, 1.0}, {5, 1.0}}, S), 6, 0.5, false);               // l4
-    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_lincomb<<<fin_blocks(M), FIN_THREADS, 0, st>>>(
-        stage({{-1, 1.0}, {0, 1.0 / 12.0}, {4, 1.0 / 3.0}, {5, 1.0 / 3.0}, {6, 1.0 / 6.0}}, S), c, S->vec[7], M); }
-    E(stage({{7, 1.0}}, S), 8, 0.5, false);                          // m1
-    E(stage({{7, 1.0}, {8, 0.5}}, S), 9, 0.5, false);                // m2
-    E(stage({{7, 1.0}, {9, 0.5}}, S), 10, 0.5, false);               // m3
-    E(stage({{7, 1.0}, {10, 1.0}}, S), 11, 0.5, false);              // m4
-    StageIn cand = stage({{7, 1.0}, {8, 1.0 / 6.0}, {9, 1.0 / 3.0}, {10, 1.0 / 3.0}, {11, 1.0 / 6.0}}, S);
-    // n_hat - n^{k+1} (the full step of length h)
-    StageIn del = stage({{7, 1.0},
-                         {8, 1.0 / 6.0},
-                         {9, 1.0 / 3.0},
-                         {10, 1.0 / 3.0},
-                         {11, 1.0 / 6.0},
-                         {-1, -1.0},
-                         {0, -1.0 / 6.0},
-                         {1, -1.0 / 3.0},
-                         {2, -1.0 / 3.0},
-                         {3, -1.0 / 6.0}},
-                        S);
-    { ProfScope ps(pr, st, SMOL_PROF_STEP); k_finish<<<fin_blocks(M), FIN_THREADS, 0, st>>>(cand, del, c, P, fpart, M); }
+    Ev(stage({{N, 1.0}, {0, 0.25}}), 4, 0.5, false);  // l2 = (h/2) S(n + l1/2)
+    Ev(stage({{N, 1.0}, {4, 0.5}}), 5, 0.5, false);   // l3
+    Ev(stage({{N, 1.0}, {5, 1.0}}), 6, 0.5, false);   // l4
+    half(stage({{N, 1.0}, {0, 1.0 / 12.0}, {4, 1.0 / 3.0}, {5, 1.0 / 3.0}, {6, 1.0 / 6.0}}));
+    Ev(stage({{H, 1.0}}), 8, 0.5, false);              // m1
+    Ev(stage({{H, 1.0}, {8, 0.5}}), 9, 0.5, false);    // m2
+    Ev(stage({{H, 1.0}, {9, 0.5}}), 10, 0.5, false);   // m3
+    Ev(stage({{H, 1.0}, {10, 1.0}}), 11, 0.5, false);  // m4
+    // n_hat and n_hat - n^{k+1} (the full step of length h)
+    finish(stage({{H, 1.0}, {8, 1.0 / 6.0}, {9, 1.0 / 3.0}, {10, 1.0 / 3.0}, {11, 1.0 / 6.0}}),
+           stage({{H, 1.0},
+                  {8, 1.0 / 6.0},
+                  {9, 1.0 / 3.0},
+                  {10, 1.0 / 3.0},
+                  {11, 1.0 / 6.0},
+                  {N, -1.0},
+                  {0, -1.0 / 6.0},
+                  {1, -1.0 / 3.0},
+                  {2, -1.0 / 3.0},
+                  {3, -1.0 / 6.0}}));
 }
 
-CtlParams make_params(const smol_system* S, int scheme, bool steady) {
+CtlParams make_params(const Engine* E, int scheme) {
     CtlParams P;
     memset(&P, 0, sizeof(P));
-    const bool fixed = S->o.fixed_tau > 0.0;
+    const bool fixed = E->o.fixed_tau > 0.0;
     P.scheme = scheme;
-    P.ctrl = S->o.ctrl;
-    P.rel_norm = S->o.norm == SMOL_NORM_REL;
+    P.ctrl = E->o.ctrl;
+    P.rel_norm = E->o.norm == SMOL_NORM_REL;
     P.fixed = fixed;
     P.order = scheme == SCHEME_RK2 ? 2 : 4;
     const int stages = scheme == SCHEME_RK2 ? 2 : (scheme == SCHEME_RK4 ? 4 : 6);
@@ -399,19 +430,19 @@ CtlParams make_params(const smol_system* S, int scheme, bool steady) {
         P.evals = 3 * stages - 1;
         P.evals_paper = 3 * stages;
     }
-    P.tau_min_rel = S->o.tau_min_rel;
-    P.steady_rtol = steady ? S->o.steady_rtol : 0.0;
-    P.fac_min = S->o.fac_min;
-    P.fac_max = S->o.fac_max;
-    P.max_attempts = S->o.max_attempts;
-    P.log_cap = S->o.log_capacity;
-    P.log_t = (double*)(S->ws + S->L.log_t);
-    P.log_h = (double*)(S->ws + S->L.log_h);
-    P.log_err = (double*)(S->ws + S->L.log_e);
-    P.log_acc = (int32_t*)(S->ws + S->L.log_a);
-    P.sqpart = steady ? (const double*)(S->ws + S->L.sqpart) : nullptr;
-    P.nsq = S->s.N2 / S->s.G;
+    P.tau_min_rel = E->o.tau_min_rel;
+    P.steady_rtol = E->o.steady_rtol;
+    P.steady = E->o.steady_rtol > 0.0;
+    P.fac_min = E->o.fac_min;
+    P.fac_max = E->o.fac_max;
+    P.max_attempts = E->o.max_attempts;
+    P.log_cap = E->o.log_capacity;
     return P;
+}
+
+void enqueue_attempt_any(Engine* E, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
+    if (E->o.precision == SMOL_FP32CONV) enqueue_attempt<float>(E, scheme, fixed, P, st, pr);
+    else enqueue_attempt<double>(E, scheme, fixed, P, st, pr);
 }
 
 #define CK(x)                                      \
@@ -419,10 +450,444 @@ CtlParams make_params(const smol_system* S, int scheme, bool steady) {
         if ((x) != cudaSuccess) return SMOL_ECUDA; \
     } while (0)
 
+template <typename R>
+void to_type(const std::vector<double>& src, std::vector<unsigned char>& dst) {
+    dst.resize(src.size() * sizeof(R));
+    R* p = reinterpret_cast<R*>(dst.data());
+    for (size_t q = 0; q < src.size(); ++q) p[q] = (R)src[q];
+}
+
+// Builds the engine: per system the distinct transforms of U and V, the weights and
+// twiddles, the descriptor; then the block maps; uploads everything.
+int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* const* hU, const double* const* hV,
+                const double* lam, const smol_opts& o, void* d_ws, size_t ws_bytes) {
+    E->count = count;
+    E->R = R;
+    E->o = o;
+    if (E->o.chunk == 0) E->o.chunk = 32;
+    E->stream = (cudaStream_t)o.stream;
+    E->ws = (char*)d_ws;
+    const int prec = o.precision;
+    const int logc = std::max(o.log_capacity, 0);
+    for (int q = 0; q < count; ++q) {
+        E->sh.push_back(make_shape(Ms[q], prec));
+        E->lay.push_back(make_layout(E->sh.back(), R, logc));
+    }
+    E->H = make_header(E->sh);
+    size_t off = E->H.total;
+    for (int q = 0; q < count; ++q) {
+        E->base.push_back(off);
+        off += E->lay[q].total;
+    }
+    if (off > ws_bytes) return SMOL_ENOSPACE;
+    char* ws = E->ws;
+    E->d_ctl = (Ctl*)(ws + E->H.ctl);
+    E->d_rctl = (Ctl*)(ws + E->H.rctl);
+    E->d_sys = (SysDev*)(ws + E->H.sys);
+    E->d_sysr = (SysDev*)(ws + E->H.sysr);
+    E->mapC = (int2*)(ws + E->H.mapC);
+    E->mapB = (int2*)(ws + E->H.mapB);
+    E->mapF = (int2*)(ws + E->H.mapF);
+    E->last_attempts.assign(count, 0);
+    cudaStream_t st = E->stream;
+    std::vector<SysDev> hs(count), hsr(count);
+    std::vector<int2> mC, mB, mF;
+    for (int q = 0; q < count; ++q) {
+        const Shape& s = E->sh[q];
+        const Layout& L = E->lay[q];
+        const int Mi = s.M;
+        const double* U = hU[q];
+        const double* V = hV[q];
+        if (!U || !V || !(lam[q] >= 0.0)) return SMOL_EINVAL;
+        // Distinct transforms among the columns of U and rows of V.
+        std::vector<std::vector<double>> W;
+        std::vector<int> au, av;
+        std::vector<double> acoef;
+        std::vector<double> ucol(Mi), vrow(Mi);
+        auto find_or_add = [&](const std::vector<double>& x, double* c) -> int {
+            for (size_t t = 0; t < W.size(); ++t)
+                if (proportional(x.data(), W[t].data(), Mi, c)) return (int)t;
+            W.push_back(x);
+            *c = 1.0;
+            return (int)W.size() - 1;
+        };
+        for (int al = 0; al < R; ++al) {
+            bool uz = true, vz = true;
+            for (int i = 0; i < Mi; ++i) {
+                ucol[i] = U[(size_t)i * R + al];
+                vrow[i] = V[(size_t)al * Mi + i];
+                uz = uz && ucol[i] == 0.0;
+                vz = vz && vrow[i] == 0.0;
+                if (!isfinite(ucol[i]) || !isfinite(vrow[i])) return SMOL_EINVAL;
+            }
+            if (uz || vz) continue;  // the term vanishes
+            double cu, cv;
+            const int u = find_or_add(ucol, &cu);
+            const int v = find_or_add(vrow, &cv);
+            au.push_back(u);
+            av.push_back(v);
+            acoef.push_back(cu * cv);
+        }
+        if (W.empty()) {  // K == 0: one zero transform keeps every path well formed
+            W.push_back(std::vector<double>(Mi, 0.0));
+            au.push_back(0);
+            av.push_back(0);
+            acoef.push_back(0.0);
+        }
+        const int T = (int)W.size();
+        E->T.push_back(T);
+        if (smem_rows(s, T) > SMEM_LIMIT || smem_cols(s, T) > SMEM_LIMIT) return SMOL_EUNSUPPORTED;
+        E->smemC = std::max(E->smemC, smem_cols(s, T));
+        E->smemB = std::max(E->smemB, smem_rows(s, T));
+        E->thrC = std::max(E->thrC, threads_for(s.N1 * s.G * T));
+        E->thrB = std::max(E->thrB, threads_for(s.N2 * 2 * T));
+        char* b = ws + E->base[q];
+        SysDev& d = hs[q];
+        memset(&d, 0, sizeof(d));
+        d.M = Mi;
+        d.Mp = s.Mp;
+        d.lgMp = s.lgMp;
+        d.N1 = s.N1;
+        d.N2 = s.N2;
+        d.lgN1 = s.lgN1;
+        d.lgN2 = s.lgN2;
+        d.G = s.G;
+        d.T = T;
+        d.R = (int)au.size();
+        d.nbx = s.N2 / s.G;
+        d.lambda = lam[q];
+        d.W = b + L.W;
+        d.tw = b + L.tw;
+        d.Y = b + L.Y;
+        d.G2 = b + L.G2;
+        d.ybuf = b + L.ybuf;
+        d.vec = b + L.vec;
+        d.half = (double*)(b + L.half);
+        d.mpart = (double*)(b + L.mpart);
+        d.fpart = (double*)(b + L.fpart);
+        d.sqpart = (double*)(b + L.sqpart);
+        d.aux = (double*)(b + L.aux);
+        d.log_t = (double*)(b + L.log_t);
+        d.log_h = (double*)(b + L.log_h);
+        d.log_e = (double*)(b + L.log_e);
+        d.log_a = (int32_t*)(b + L.log_a);
+        d.vstride = (int64_t)L.vstride;
+        d.nfin = s.nfin;
+        for (int al = 0; al < d.R; ++al) {
+            d.au[al] = au[al];
+            d.av[al] = av[al];
+            d.acoef[al] = acoef[al];
+        }
+        // unordered pairs for the spectral product: (u,v) and (v,u) give the same product
+        d.npairs = 0;
+        for (int al = 0; al < d.R; ++al) {
+            int a = au[al], c = av[al];
+            if (a > c) std::swap(a, c);
+            int p = 0;
+            for (; p < d.npairs; ++p)
+                if (d.pu[p] == a && d.pv[p] == c) break;
+            if (p == d.npairs) {
+                d.pu[p] = a;
+                d.pv[p] = c;
+                d.pcoef[p] = 0.0;
+                d.npairs++;
+            }
+            d.pcoef[p] += acoef[al];
+        }
+        for (int t = 0; t < T; ++t) {
+            double mx = 0.0;
+            for (int i = 0; i < Mi; ++i) mx = fmax(mx, fabs(W[t][i]));
+            d.wexp[t] = mx > 0.0 ? ilogb(mx) : 0;
+        }
+        d.ctl = E->d_ctl + q;
+        hsr[q] = d;
+        hsr[q].ctl = E->d_rctl + q;
+        for (int c = 0; c < s.N2 / s.G; ++c) mC.push_back(make_int2(q, c));
+        for (int c = 0; c < s.N1 / 2; ++c) mB.push_back(make_int2(q, c));
+        for (int c = 0; c < s.nfin; ++c) mF.push_back(make_int2(q, c));
+
+        // Host images of the tables: weights (zero beyond M) and twiddles
+        // W_{2Mp}^e = exp(-i pi e / Mp), e < Mp, in extended precision.
+        std::vector<double> hW((size_t)T * s.Mp, 0.0);
+        for (int t = 0; t < T; ++t)
+            for (int i = 0; i < Mi; ++i) hW[(size_t)t * s.Mp + i] = W[t][i];
+        std::vector<double> tw64(2 * (size_t)s.Mp);
+        for (int e = 0; e < s.Mp; ++e) {
+            const long double th = 3.141592653589793238462643383279502884L * (long double)e / (long double)s.Mp;
+            tw64[2 * e] = (double)cosl(th);
+            tw64[2 * e + 1] = (double)-sinl(th);
+        }
+        std::vector<unsigned char> Wb, twb;
+        if (prec == SMOL_FP32CONV) {
+            to_type<float>(hW, Wb);
+            to_type<float>(tw64, twb);
+        } else {
+            to_type<double>(hW, Wb);
+            to_type<double>(tw64, twb);
+        }
+        CK(cudaMemcpyAsync(b + L.W, Wb.data(), Wb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b + L.tw, twb.data(), twb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(b + L.vec, 0, (size_t)NVEC * L.vstride * s.rsz, st));
+        CK(cudaMemsetAsync(b + L.ybuf, 0, (size_t)s.Mp * s.rsz, st));
+        CK(cudaMemsetAsync(b + L.half, 0, (size_t)s.Mp * 8, st));
+        CK(cudaMemsetAsync(b + L.stateB, 0, (size_t)s.Mp * 8, st));
+        // the host images are freed at the end of this iteration
+        CK(cudaStreamSynchronize(st));
+    }
+    E->H.nC = (int)mC.size();
+    E->H.nB = (int)mB.size();
+    E->H.nF = (int)mF.size();
+    CK(cudaMemsetAsync(ws + E->H.ctl, 0, (size_t)count * sizeof(Ctl), st));
+    CK(cudaMemsetAsync(ws + E->H.rctl, 0, (size_t)count * sizeof(Ctl), st));
+    CK(cudaMemcpyAsync(E->d_sys, hs.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(E->d_sysr, hsr.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(E->mapC, mC.data(), mC.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(E->mapB, mB.data(), mB.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(E->mapF, mF.data(), mF.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaHostAlloc((void**)&E->h_ctl, (size_t)count * sizeof(Ctl), cudaHostAllocDefault));
+    CK(cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
+    return prec == SMOL_FP32CONV ? set_smem_attrs<float>(E) : set_smem_attrs<double>(E);
+}
+
+void engine_free(Engine* E) {
+    if (!E) return;
+    if (E->gexec) cudaGraphExecDestroy(E->gexec);
+    if (E->cap) cudaStreamDestroy(E->cap);
+    if (E->h_ctl) cudaFreeHost(E->h_ctl);
+}
+
+int check_opts(const smol_opts& o) {
+    if (o.precision != SMOL_FP64 && o.precision != SMOL_FP32CONV) return SMOL_EINVAL;
+    if (o.log_capacity < 0 || o.chunk < 0) return SMOL_EINVAL;
+    return SMOL_OK;
+}
+
+int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double tol, int32_t scheme) {
+    if (!E || !d_n) return SMOL_EINVAL;
+    for (int q = 0; q < E->count; ++q)
+        if (!d_n[q] || ((uintptr_t)d_n[q] & 15)) return SMOL_EINVAL;
+    if (!(t1 >= t0) || !isfinite(t0) || !isfinite(t1)) return SMOL_EINVAL;
+    if (scheme < SMOL_RK2 || scheme > SMOL_RKF45) return SMOL_EINVAL;
+    const bool fixed = E->o.fixed_tau > 0.0;
+    if (!fixed && !(tol > 0.0)) return SMOL_EINVAL;
+    cudaStream_t st = E->stream;
+    // the pinned blocks may still be the target of an earlier read-back: wait for it
+    CK(cudaStreamSynchronize(st));
+    for (int q = 0; q < E->count; ++q) {
+        Ctl& h = E->h_ctl[q];
+        memset(&h, 0, sizeof(h));
+        h.t = t0;
+        h.t1 = t1;
+        h.tol = tol;
+        h.tau = E->o.tau0 > 0.0 ? E->o.tau0 : (fixed ? E->o.fixed_tau : 0.0);
+        h.state[0] = d_n[q];
+        h.state[1] = (double*)(E->ws + E->base[q] + E->lay[q].stateB);
+    }
+    CK(cudaMemcpyAsync(E->d_ctl, E->h_ctl, (size_t)E->count * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    if (E->o.precision == SMOL_FP32CONV) {
+        k_prep1<float><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF);
+        k_prep2<float><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF, E->o.euler_a);
+    } else {
+        k_prep1<double><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF);
+        k_prep2<double><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF, E->o.euler_a);
+    }
+    CK(cudaGetLastError());
+
+    // One CUDA graph holds `chunk` attempts (fewer if max_attempts is smaller); kernels
+    // of attempts after termination return at once (they read ctl->done first).
+    int64_t na = E->o.chunk > 0 ? E->o.chunk : 32;
+    if (E->o.max_attempts < na) na = E->o.max_attempts;
+    if (na < 1) na = 1;
+    const int64_t key = na * 64 + scheme * 16 + (fixed ? 8 : 0) + (E->o.steady_rtol > 0.0 ? 4 : 0);
+    if (E->gkey != key) {
+        if (E->gexec) {
+            cudaGraphExecDestroy(E->gexec);
+            E->gexec = nullptr;
+        }
+        E->gkey = -1;
+        CtlParams P = make_params(E, scheme);
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(E->cap, cudaStreamCaptureModeThreadLocal));
+        for (int64_t q = 0; q < na; ++q) enqueue_attempt_any(E, scheme, fixed, P, E->cap, nullptr);
+        cudaError_t e1 = cudaStreamEndCapture(E->cap, &g);
+        if (e1 != cudaSuccess) return SMOL_ECUDA;
+        e1 = cudaGraphInstantiate(&E->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e1 != cudaSuccess) {
+            E->gexec = nullptr;
+            return SMOL_ECUDA;
+        }
+        E->gkey = key;
+    }
+    E->run_dn.assign(d_n, d_n + E->count);
+    E->run_scheme = scheme;
+    E->run_attempts = na;
+    E->running = true;
+    return SMOL_OK;
+}
+
+int integrate_advance(Engine* E) {
+    if (!E || !E->running || !E->gexec) return SMOL_EINVAL;
+    CK(cudaGraphLaunch(E->gexec, E->stream));
+    return SMOL_OK;
+}
+
+void fill_stats(const Ctl& c, smol_stats* s) {
+    s->t = c.t;
+    s->tau_next = c.tau;
+    s->err_last = c.err_last;
+    s->mass = c.mass;
+    s->rhs_evals = c.rhs_evals;
+    s->rhs_evals_paper = c.rhs_paper;
+    s->accepted = c.accepted;
+    s->rejected = c.rejected;
+    s->attempts = c.attempts;
+    s->status = c.status;
+    s->reserved = 0;
+}
+
+// Synchronises, copies states held in the engine's buffers back to the callers'
+// vectors, fills stats (count entries) and returns the first error status, else
+// SMOL_STEADY if any system stopped there, else SMOL_OK.
+int integrate_finish(Engine* E, smol_stats* stats) {
+    if (!E || !E->running) return SMOL_EINVAL;
+    cudaStream_t st = E->stream;
+    CK(cudaStreamSynchronize(st));
+    std::vector<Ctl> fin(E->count);
+    CK(cudaMemcpy(fin.data(), E->d_ctl, (size_t)E->count * sizeof(Ctl), cudaMemcpyDeviceToHost));
+    int rc = SMOL_OK;
+    bool moved = false;
+    for (int q = 0; q < E->count; ++q) {
+        if (fin[q].cur == 1) {
+            CK(cudaMemcpyAsync(E->run_dn[q], fin[q].state[1], (size_t)E->sh[q].M * 8, cudaMemcpyDeviceToDevice, st));
+            moved = true;
+        }
+        E->last_attempts[q] = fin[q].attempts;
+        if (stats) fill_stats(fin[q], stats + q);
+        if (fin[q].status < 0 && rc >= 0) rc = fin[q].status;
+        else if (fin[q].status == SMOL_STEADY && rc == SMOL_OK) rc = SMOL_STEADY;
+    }
+    if (moved) {
+        // the callers' buffers hold the states again: later advances continue from there
+        for (int q = 0; q < E->count; ++q) fin[q].cur = 0;
+        CK(cudaMemcpyAsync(E->d_ctl, fin.data(), (size_t)E->count * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return rc;
+}
+
+bool all_done(const Engine* E) {
+    for (int q = 0; q < E->count; ++q)
+        if (!E->h_ctl[q].done) return false;
+    return true;
+}
+
+int integrate_all(Engine* E, double* const* d_n, double t0, double t1, double tol, int32_t scheme,
+                  smol_stats* stats) {
+    int rc = integrate_start(E, d_n, t0, t1, tol, scheme);
+    if (rc != SMOL_OK) return rc;
+    if (!(t1 > t0)) return integrate_finish(E, stats);  // nothing to integrate
+    cudaStream_t st = E->stream;
+    // Launch chunks, keeping one in flight while the status of the previous one is read
+    // from pinned copies of the control blocks.
+    cudaEvent_t ev[2];
+    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    const size_t cbytes = (size_t)E->count * sizeof(Ctl);
+    const int64_t maxa = E->o.max_attempts;
+    int64_t launched = E->run_attempts;  // attempts enqueued so far
+    int cur = 0;
+    if (cudaGraphLaunch(E->gexec, st) != cudaSuccess ||
+        cudaMemcpyAsync(E->h_ctl, E->d_ctl, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(ev[cur], st) != cudaSuccess)
+        rc = SMOL_ECUDA;
+    while (rc == SMOL_OK && launched < maxa) {
+        if (cudaGraphLaunch(E->gexec, st) != cudaSuccess) {
+            rc = SMOL_ECUDA;
+            break;
+        }
+        launched += E->run_attempts;
+        if (cudaEventSynchronize(ev[cur]) != cudaSuccess) {
+            rc = SMOL_ECUDA;
+            break;
+        }
+        if (all_done(E)) break;
+        if (cudaMemcpyAsync(E->h_ctl, E->d_ctl, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaEventRecord(ev[cur ^ 1], st) != cudaSuccess) {
+            rc = SMOL_ECUDA;
+            break;
+        }
+        cur ^= 1;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SMOL_ECUDA;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc != SMOL_OK) return rc;
+    return integrate_finish(E, stats);
+}
+
+int get_log(Engine* E, int q, double* h_t, double* h_tau, double* h_err, int32_t* h_acc, int32_t cap,
+            int64_t* count) {
+    if (!E || cap < 0 || q < 0 || q >= E->count) return SMOL_EINVAL;
+    const int64_t n = E->last_attempts[q];
+    if (count) *count = n;
+    const int lc = E->o.log_capacity;
+    if (lc <= 0 || cap == 0 || n == 0) return SMOL_OK;
+    const int64_t keep = n < lc ? n : lc;
+    const int64_t take = keep < cap ? keep : cap;
+    std::vector<double> t(lc), hh(lc), e(lc);
+    std::vector<int32_t> a(lc);
+    const char* b = E->ws + E->base[q];
+    const Layout& L = E->lay[q];
+    CK(cudaMemcpy(t.data(), b + L.log_t, lc * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hh.data(), b + L.log_h, lc * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(e.data(), b + L.log_e, lc * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(a.data(), b + L.log_a, lc * 4, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < take; ++k) {
+        const int64_t att = n - take + k;  // 0-based attempt index, oldest first
+        const int64_t slot = att % lc;
+        if (h_t) h_t[k] = t[slot];
+        if (h_tau) h_tau[k] = hh[slot];
+        if (h_err) h_err[k] = e[slot];
+        if (h_acc) h_acc[k] = a[slot];
+    }
+    return SMOL_OK;
+}
+
+int rhs_common(smol_system* S, const double* d_n, double* d_out, double* d_birth, double* d_loss, double* d_src) {
+    if (!S || !d_n) return SMOL_EINVAL;
+    if (((uintptr_t)d_n & 15) || ((uintptr_t)d_out & 15) || ((uintptr_t)d_birth & 15) || ((uintptr_t)d_loss & 15))
+        return SMOL_EINVAL;
+    cudaStream_t st = S->stream;
+    StageIn in;
+    memset(&in, 0, sizeof(in));
+    in.nv = 1;
+    in.direct = 1;
+    in.slot[0] = SLOT_EXT;
+    in.c[0] = 1.0;
+    in.ext = d_n;
+    EpiOut eo;
+    memset(&eo, 0, sizeof(eo));
+    eo.out_slot = -1;
+    eo.out = d_out;
+    eo.birth = d_birth;
+    eo.loss = d_loss;
+    eo.source = d_src;
+    eo.hfac = 1.0;
+    if (S->o.precision == SMOL_FP32CONV) {
+        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(S->d_sysr, S->mapF, d_n);
+        launch_eval<float>(S, S->d_sysr, in, eo, st, nullptr);
+    } else {
+        launch_eval<double>(S, S->d_sysr, in, eo, st, nullptr);
+    }
+    return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// C interface
+// C interface: single system
 // ---------------------------------------------------------------------------
 extern "C" {
 
@@ -430,23 +895,13 @@ void smol_default_opts(smol_opts* opts) {
     if (opts) default_opts(opts);
 }
 
-int64_t smol_max_m(int32_t R, int32_t precision) {
-    if (R < 1 || R > MAXR) return 0;
-    int64_t best = 0;
-    for (int lg = 2; lg <= 22; ++lg) {
-        Shape s = make_shape((int64_t)1 << lg, precision);
-        if (smem_cols(s) <= SMEM_LIMIT && smem_rows(s, 2 * R) <= SMEM_LIMIT) best = (int64_t)1 << lg;
-    }
-    return best;
-}
+int64_t smol_max_m(int32_t R, int32_t precision) { return max_m_for(R, precision); }
 
 size_t smol_workspace_bytes(int64_t M, int32_t R, const smol_opts* opts) {
     smol_opts o;
     if (opts) o = *opts;
     else default_opts(&o);
-    if (M < 1 || R < 1 || R > MAXR || M > smol_max_m(R, o.precision)) return 0;
-    Shape s = make_shape(M, o.precision);
-    return make_layout(s, R, o.log_capacity > 0 ? o.log_capacity : 0).total;
+    return batch_bytes(1, &M, R, o);
 }
 
 int smol_init_system(smol_system** out, int64_t M, int32_t R, const double* h_U, const double* h_V, double lambda,
@@ -456,160 +911,18 @@ int smol_init_system(smol_system** out, int64_t M, int32_t R, const double* h_U,
     smol_opts o;
     if (opts) o = *opts;
     else default_opts(&o);
-    if (o.precision != SMOL_FP64 && o.precision != SMOL_FP32CONV) return SMOL_EINVAL;
-    if (o.log_capacity < 0 || o.chunk < 0) return SMOL_EINVAL;
-    if (o.chunk == 0) o.chunk = 32;
-    if (M > smol_max_m(R, o.precision)) return SMOL_EUNSUPPORTED;
+    int rc = check_opts(o);
+    if (rc != SMOL_OK) return rc;
+    if (M > max_m_for(R, o.precision)) return SMOL_EUNSUPPORTED;
     if (((uintptr_t)d_workspace & 255) != 0) return SMOL_EINVAL;
-    const size_t need = smol_workspace_bytes(M, R, &o);
-    if (workspace_bytes < need) return SMOL_ENOSPACE;
-
+    if (workspace_bytes < batch_bytes(1, &M, R, o)) return SMOL_ENOSPACE;
     smol_system* S = new smol_system();
-    memset(S, 0, sizeof(*S));
-    S->s = make_shape(M, o.precision);
-    S->R = R;
-    S->lambda = lambda;
-    S->o = o;
-    S->stream = (cudaStream_t)o.stream;
-    S->ws = (char*)d_workspace;
-    S->L = make_layout(S->s, R, o.log_capacity);
-    const Shape& s = S->s;
-    const int Mi = (int)M;
-
-    // Distinct transforms among the columns of U and rows of V.
-    std::vector<std::vector<double>> W;
-    std::vector<int> au, av;
-    std::vector<double> acoef;
-    std::vector<double> ucol(Mi), vrow(Mi);
-    auto find_or_add = [&](const std::vector<double>& x, double* c) -> int {
-        for (size_t t = 0; t < W.size(); ++t)
-            if (proportional(x.data(), W[t].data(), Mi, c)) return (int)t;
-        W.push_back(x);
-        *c = 1.0;
-        return (int)W.size() - 1;
-    };
-    for (int al = 0; al < R; ++al) {
-        bool uz = true, vz = true;
-        for (int i = 0; i < Mi; ++i) {
-            ucol[i] = h_U[(size_t)i * R + al];
-            vrow[i] = h_V[(size_t)al * Mi + i];
-            uz = uz && ucol[i] == 0.0;
-            vz = vz && vrow[i] == 0.0;
-            if (!isfinite(ucol[i]) || !isfinite(vrow[i])) {
-                delete S;
-                return SMOL_EINVAL;
-            }
-        }
-        if (uz || vz) continue;  // the term vanishes
-        double cu, cv;
-        const int u = find_or_add(ucol, &cu);
-        const int v = find_or_add(vrow, &cv);
-        au.push_back(u);
-        av.push_back(v);
-        acoef.push_back(cu * cv);
-    }
-    if (W.empty()) {  // K == 0: keep one zero transform so that every path is well formed
-        W.push_back(std::vector<double>(Mi, 0.0));
-        au.push_back(0);
-        av.push_back(0);
-        acoef.push_back(0.0);
-    }
-    S->T = (int)W.size();
-    SysDev& d = S->dev;
-    memset(&d, 0, sizeof(d));
-    d.M = Mi;
-    d.Mp = s.Mp;
-    d.lgMp = s.lgMp;
-    d.N1 = s.N1;
-    d.N2 = s.N2;
-    d.lgN1 = s.lgN1;
-    d.lgN2 = s.lgN2;
-    d.T = S->T;
-    d.R = (int)au.size();
-    d.lambda = lambda;
-    d.nbxA = s.N2 / s.G;
-    for (int al = 0; al < d.R; ++al) {
-        d.au[al] = au[al];
-        d.av[al] = av[al];
-        d.acoef[al] = acoef[al];
-    }
-    // unordered pairs for the spectral product: (u,v) and (v,u) give the same product
-    d.npairs = 0;
-    for (int al = 0; al < d.R; ++al) {
-        int a = au[al], b = av[al];
-        if (a > b) {
-            int t = a;
-            a = b;
-            b = t;
-        }
-        int p = 0;
-        for (; p < d.npairs; ++p)
-            if (d.pu[p] == a && d.pv[p] == b) break;
-        if (p == d.npairs) {
-            d.pu[p] = a;
-            d.pv[p] = b;
-            d.pcoef[p] = 0.0;
-            d.npairs++;
-        }
-        d.pcoef[p] += acoef[al];
-    }
-    for (int t = 0; t < S->T; ++t) {
-        double mx = 0.0;
-        for (int i = 0; i < Mi; ++i) mx = fmax(mx, fabs(W[t][i]));
-        d.wexp[t] = mx > 0.0 ? ilogb(mx) : 0;
-    }
-    if (smem_rows(s, S->T) > SMEM_LIMIT) {
-        delete S;
-        return SMOL_EUNSUPPORTED;
-    }
-    char* ws = S->ws;
-    S->ctl = (Ctl*)(ws + S->L.ctl);
-    S->rctl = (Ctl*)(ws + S->L.rctl);
-    d.W = (const double*)(ws + S->L.W);
-    d.tw = ws + S->L.tw;
-    d.Y = ws + S->L.Y;
-    d.G2 = ws + S->L.G2;
-    d.ybuf = (double*)(ws + S->L.ybuf);
-    d.mpart = (double*)(ws + S->L.mpart);
-    for (int k = 0; k < NVEC; ++k) S->vec[k] = (double*)(ws + S->L.vec + (size_t)k * align256((size_t)s.Mp * 8));
-    S->stateB = (double*)(ws + S->L.stateB);
-
-    // Host images of the tables.
-    std::vector<double> hW((size_t)S->T * s.Mp, 0.0);
-    for (int t = 0; t < S->T; ++t)
-        for (int i = 0; i < Mi; ++i) hW[(size_t)t * s.Mp + i] = W[t][i];
-    // Twiddles W_{2Mp}^e = exp(-i pi e / Mp), e < Mp, in extended precision.
-    std::vector<double> tw64(2 * (size_t)s.Mp);
-    for (int e = 0; e < s.Mp; ++e) {
-        const long double th = 3.141592653589793238462643383279502884L * (long double)e / (long double)s.Mp;
-        tw64[2 * e] = (double)cosl(th);
-        tw64[2 * e + 1] = (double)-sinl(th);
-    }
-    cudaStream_t st = S->stream;
-    cudaError_t err = cudaSuccess;
-    if (o.precision == SMOL_FP32CONV) {
-        std::vector<float> tw32(2 * (size_t)s.Mp);
-        for (size_t q = 0; q < tw32.size(); ++q) tw32[q] = (float)tw64[q];
-        err = cudaMemcpyAsync(ws + S->L.tw, tw32.data(), tw32.size() * 4, cudaMemcpyHostToDevice, st);
-    } else {
-        err = cudaMemcpyAsync(ws + S->L.tw, tw64.data(), tw64.size() * 8, cudaMemcpyHostToDevice, st);
-    }
-    if (err == cudaSuccess)
-        err = cudaMemcpyAsync(ws + S->L.W, hW.data(), hW.size() * 8, cudaMemcpyHostToDevice, st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(ws + S->L.ctl, 0, 2 * align256(sizeof(Ctl)), st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(ws + S->L.vec, 0, (size_t)NVEC * align256((size_t)s.Mp * 8), st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(ws + S->L.ybuf, 0, (size_t)s.Mp * 8, st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(ws + S->L.stateB, 0, (size_t)s.Mp * 8, st);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    if (err == cudaSuccess) err = cudaHostAlloc((void**)&S->h_ctl, sizeof(Ctl), cudaHostAllocDefault);
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking);
-    int rc = (err == cudaSuccess) ? SMOL_OK : SMOL_ECUDA;
-    if (rc == SMOL_OK) rc = (o.precision == SMOL_FP32CONV) ? set_smem_attrs<float>(S) : set_smem_attrs<double>(S);
+    rc = engine_init(S, 1, &M, R, &h_U, &h_V, &lambda, o, d_workspace, workspace_bytes);
     if (rc != SMOL_OK) {
-        smol_destroy(S);
+        engine_free(S);
+        delete S;
         return rc;
     }
-    S->gkey = -1;
     *out = S;
     return SMOL_OK;
 }
@@ -621,28 +934,7 @@ int smol_set_stream(smol_system* S, void* stream) {
     return SMOL_OK;
 }
 
-int smol_num_transforms(const smol_system* S) { return S ? S->T : 0; }
-
-static int rhs_common(smol_system* S, const double* d_n, double* d_out, double* d_birth, double* d_loss, double* d_src) {
-    if (!S || !d_n) return SMOL_EINVAL;
-    if (((uintptr_t)d_n & 15) || ((uintptr_t)d_out & 15) || ((uintptr_t)d_birth & 15) || ((uintptr_t)d_loss & 15))
-        return SMOL_EINVAL;
-    cudaStream_t st = S->stream;
-    if (S->o.precision == SMOL_FP32CONV) {
-        const int nb = fin_blocks(S->s.M) > PREP_BLOCKS ? PREP_BLOCKS : fin_blocks(S->s.M);
-        k_absmax<<<nb, 256, 0, st>>>(d_n, S->s.M, S->rctl, (double*)(S->ws + S->L.ppart));
-    }
-    EpiOut eo;
-    memset(&eo, 0, sizeof(eo));
-    eo.out = d_out;
-    eo.birth = d_birth;
-    eo.loss = d_loss;
-    eo.source = d_src;
-    eo.hfac = 1.0;
-    eo.use_h = 0;
-    eval(S, from_ptr(d_n), S->rctl, eo, st);
-    return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
-}
+int smol_num_transforms(const smol_system* S) { return S ? S->T[0] : 0; }
 
 int smol_rhs(smol_system* S, const double* d_n, double* d_out) {
     if (!d_out) return SMOL_EINVAL;
@@ -654,147 +946,21 @@ int smol_rhs_terms(smol_system* S, const double* d_n, double* d_birth, double* d
 }
 
 int smol_integrate_start(smol_system* S, double* d_n, double t0, double t1, double tol, int32_t scheme) {
-    if (!S || !d_n || ((uintptr_t)d_n & 15)) return SMOL_EINVAL;
-    if (!(t1 >= t0) || !isfinite(t0) || !isfinite(t1)) return SMOL_EINVAL;
-    if (scheme < SMOL_RK2 || scheme > SMOL_RKF45) return SMOL_EINVAL;
-    const bool fixed = S->o.fixed_tau > 0.0;
-    if (!fixed && !(tol > 0.0)) return SMOL_EINVAL;
-    const bool steady = S->o.steady_rtol > 0.0;
-    cudaStream_t st = S->stream;
-
-    Ctl h;
-    memset(&h, 0, sizeof(h));
-    h.t = t0;
-    h.t1 = t1;
-    h.tol = tol;
-    h.tau = S->o.tau0 > 0.0 ? S->o.tau0 : (fixed ? S->o.fixed_tau : 0.0);
-    h.state[0] = d_n;
-    h.state[1] = S->stateB;
-    // the pinned block may still be the target of an earlier read-back: wait for it
-    CK(cudaStreamSynchronize(st));
-    *S->h_ctl = h;
-    CK(cudaMemcpyAsync(S->ctl, S->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-    double* ppart = (double*)(S->ws + S->L.ppart);
-    double* delta = (double*)(S->ws + S->L.delta);
-    k_prep1<<<PREP_BLOCKS, 256, 0, st>>>(S->dev, S->ctl, ppart, delta);
-    k_prep2<<<PREP_BLOCKS, 256, 0, st>>>(S->dev, S->ctl, delta, ppart, S->o.euler_a);
-    CK(cudaGetLastError());
-
-    // One CUDA graph holds `chunk` attempts (fewer if max_attempts is smaller); kernels
-    // of attempts after termination return at once (they read ctl->done first).
-    int64_t na = S->o.chunk;
-    if (S->o.max_attempts < na) na = S->o.max_attempts;
-    if (na < 1) na = 1;
-    const int key = (int)na * 64 + scheme * 16 + (fixed ? 8 : 0) + (steady ? 4 : 0) +
-                    (S->o.precision == SMOL_FP32CONV ? 2 : 0);
-    if (S->gkey != key) {
-        if (S->gexec) {
-            cudaGraphExecDestroy(S->gexec);
-            S->gexec = nullptr;
-        }
-        S->gkey = -1;
-        CtlParams P = make_params(S, scheme, steady);
-        cudaGraph_t g;
-        CK(cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal));
-        for (int64_t q = 0; q < na; ++q) enqueue_attempt(S, scheme, fixed, P, S->cap, nullptr);
-        cudaError_t e1 = cudaStreamEndCapture(S->cap, &g);
-        if (e1 != cudaSuccess) return SMOL_ECUDA;
-        e1 = cudaGraphInstantiate(&S->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (e1 != cudaSuccess) {
-            S->gexec = nullptr;
-            return SMOL_ECUDA;
-        }
-        S->gkey = key;
-    }
-    S->run_dn = d_n;
-    S->run_scheme = scheme;
-    S->run_attempts = na;
-    return SMOL_OK;
+    if (!S) return SMOL_EINVAL;
+    return integrate_start(S, &d_n, t0, t1, tol, scheme);
 }
 
-int smol_integrate_advance(smol_system* S) {
-    if (!S || !S->run_dn || !S->gexec) return SMOL_EINVAL;
-    CK(cudaGraphLaunch(S->gexec, S->stream));
-    return SMOL_OK;
-}
+int smol_integrate_advance(smol_system* S) { return integrate_advance(S); }
 
-int smol_integrate_finish(smol_system* S, smol_stats* stats) {
-    if (!S || !S->run_dn) return SMOL_EINVAL;
-    cudaStream_t st = S->stream;
-    CK(cudaStreamSynchronize(st));
-    Ctl fin;
-    CK(cudaMemcpy(&fin, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-    if (fin.cur == 1) {
-        CK(cudaMemcpyAsync(S->run_dn, S->stateB, (size_t)S->s.M * 8, cudaMemcpyDeviceToDevice, st));
-        CK(cudaStreamSynchronize(st));
-        // the caller's buffer holds the state again: keep later advances consistent
-        int zero = 0;
-        CK(cudaMemcpy(&S->ctl->cur, &zero, sizeof(int), cudaMemcpyHostToDevice));
-    }
-    S->last_attempts = fin.attempts;
-    if (stats) {
-        stats->t = fin.t;
-        stats->tau_next = fin.tau;
-        stats->err_last = fin.err_last;
-        stats->rhs_evals = fin.rhs_evals;
-        stats->rhs_evals_paper = fin.rhs_paper;
-        stats->accepted = fin.accepted;
-        stats->rejected = fin.rejected;
-        stats->attempts = fin.attempts;
-        stats->status = fin.status;
-        stats->reserved = 0;
-    }
-    return fin.status;
-}
+int smol_integrate_finish(smol_system* S, smol_stats* stats) { return integrate_finish(S, stats); }
 
 int smol_integrate(smol_system* S, double* d_n, double t0, double t1, double tol, int32_t scheme, smol_stats* stats) {
-    int rc = smol_integrate_start(S, d_n, t0, t1, tol, scheme);
-    if (rc != SMOL_OK) return rc;
-    if (!(t1 > t0)) return smol_integrate_finish(S, stats);  // nothing to integrate
-    cudaStream_t st = S->stream;
-    // Launch chunks, keeping one in flight while the status of the previous one is read
-    // from a pinned copy of the control block.
-    cudaEvent_t ev[2];
-    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    Ctl* snap = S->h_ctl;
-    const int64_t maxa = S->o.max_attempts;
-    int64_t launched = S->run_attempts;  // attempts enqueued so far
-    bool done = false;
-    int cur = 0;
-    if (cudaGraphLaunch(S->gexec, st) != cudaSuccess ||
-        cudaMemcpyAsync(snap, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaEventRecord(ev[cur], st) != cudaSuccess)
-        rc = SMOL_ECUDA;
-    while (rc == SMOL_OK && !done && launched < maxa) {
-        if (cudaGraphLaunch(S->gexec, st) != cudaSuccess) {
-            rc = SMOL_ECUDA;
-            break;
-        }
-        launched += S->run_attempts;
-        if (cudaEventSynchronize(ev[cur]) != cudaSuccess) {
-            rc = SMOL_ECUDA;
-            break;
-        }
-        done = snap->done != 0;
-        if (done) break;
-        if (cudaMemcpyAsync(snap, S->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaEventRecord(ev[cur ^ 1], st) != cudaSuccess) {
-            rc = SMOL_ECUDA;
-            break;
-        }
-        cur ^= 1;
-    }
-    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SMOL_ECUDA;
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-    if (rc != SMOL_OK) return rc;
-    return smol_integrate_finish(S, stats);
+    if (!S) return SMOL_EINVAL;
+    return integrate_all(S, &d_n, t0, t1, tol, scheme, stats);
 }
 
 int smol_profile_attempts(smol_system* S, int32_t reps, double* kernel_ms, int64_t* kernel_launches, int32_t nkinds) {
-    if (!S || !S->run_dn || reps < 1 || !kernel_ms || nkinds < SMOL_PROF_KINDS) return SMOL_EINVAL;
+    if (!S || !S->running || reps < 1 || !kernel_ms || nkinds < SMOL_PROF_KINDS) return SMOL_EINVAL;
     cudaStream_t st = S->stream;
     Prof pr;
     memset(&pr, 0, sizeof(pr));
@@ -803,7 +969,7 @@ int smol_profile_attempts(smol_system* S, int32_t reps, double* kernel_ms, int64
         CK(cudaEventCreate(&pr.ev1[q]));
     }
     const bool fixed = S->o.fixed_tau > 0.0;
-    CtlParams P = make_params(S, S->run_scheme, S->o.steady_rtol > 0.0);
+    CtlParams P = make_params(S, S->run_scheme);
     double acc[SMOL_PROF_KINDS] = {0};
     int64_t cnt[SMOL_PROF_KINDS] = {0};
     int rc = SMOL_OK;
@@ -812,7 +978,7 @@ int smol_profile_attempts(smol_system* S, int32_t reps, double* kernel_ms, int64
         // ~0.5 ms of device work first, so that the whole attempt is enqueued before the
         // device reaches it and the events time the kernels, not the host launches
         k_delay<<<1, 32, 0, st>>>(1000000LL);
-        enqueue_attempt(S, S->run_scheme, fixed, P, st, &pr);
+        enqueue_attempt_any(S, S->run_scheme, fixed, P, st, &pr);
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             rc = SMOL_ECUDA;
             break;
@@ -840,36 +1006,87 @@ int smol_profile_attempts(smol_system* S, int32_t reps, double* kernel_ms, int64
 }
 
 int smol_get_log(smol_system* S, double* h_t, double* h_tau, double* h_err, int32_t* h_acc, int32_t cap, int64_t* count) {
-    if (!S || cap < 0) return SMOL_EINVAL;
-    const int64_t n = S->last_attempts;
-    if (count) *count = n;
-    const int lc = S->o.log_capacity;
-    if (lc <= 0 || cap == 0 || n == 0) return SMOL_OK;
-    const int64_t keep = n < lc ? n : lc;
-    const int64_t take = keep < cap ? keep : cap;
-    std::vector<double> t(lc), hh(lc), e(lc);
-    std::vector<int32_t> a(lc);
-    CK(cudaMemcpy(t.data(), S->ws + S->L.log_t, lc * 8, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(hh.data(), S->ws + S->L.log_h, lc * 8, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(e.data(), S->ws + S->L.log_e, lc * 8, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(a.data(), S->ws + S->L.log_a, lc * 4, cudaMemcpyDeviceToHost));
-    for (int64_t q = 0; q < take; ++q) {
-        const int64_t att = n - take + q;  // 0-based attempt index, oldest first
-        const int64_t slot = att % lc;
-        if (h_t) h_t[q] = t[slot];
-        if (h_tau) h_tau[q] = hh[slot];
-        if (h_err) h_err[q] = e[slot];
-        if (h_acc) h_acc[q] = a[slot];
-    }
-    return SMOL_OK;
+    return get_log(S, 0, h_t, h_tau, h_err, h_acc, cap, count);
 }
 
 void smol_destroy(smol_system* S) {
     if (!S) return;
-    if (S->gexec) cudaGraphExecDestroy(S->gexec);
-    if (S->cap) cudaStreamDestroy(S->cap);
-    if (S->h_ctl) cudaFreeHost(S->h_ctl);
+    engine_free(S);
     delete S;
+}
+
+// ---------------------------------------------------------------------------
+// C interface: batch of independent systems
+// ---------------------------------------------------------------------------
+size_t smol_batch_workspace_bytes(int32_t count, const int64_t* M, int32_t R, const smol_opts* opts) {
+    if (!M) return 0;
+    smol_opts o;
+    if (opts) o = *opts;
+    else default_opts(&o);
+    return batch_bytes(count, M, R, o);
+}
+
+int smol_batch_init(smol_batch** out, int32_t count, const int64_t* M, int32_t R, const double* const* h_U,
+                    const double* const* h_V, const double* lambda, const smol_opts* opts, void* d_workspace,
+                    size_t workspace_bytes) {
+    if (!out || !M || !h_U || !h_V || !lambda || !d_workspace || count < 1 || count > MAX_BATCH || R < 1 ||
+        R > MAXR)
+        return SMOL_EINVAL;
+    *out = nullptr;
+    smol_opts o;
+    if (opts) o = *opts;
+    else default_opts(&o);
+    int rc = check_opts(o);
+    if (rc != SMOL_OK) return rc;
+    const int64_t mm = max_m_for(R, o.precision);
+    for (int q = 0; q < count; ++q) {
+        if (M[q] < 1) return SMOL_EINVAL;
+        if (M[q] > mm) return SMOL_EUNSUPPORTED;
+    }
+    if (((uintptr_t)d_workspace & 255) != 0) return SMOL_EINVAL;
+    if (workspace_bytes < batch_bytes(count, M, R, o)) return SMOL_ENOSPACE;
+    smol_batch* B = new smol_batch();
+    rc = engine_init(B, count, M, R, h_U, h_V, lambda, o, d_workspace, workspace_bytes);
+    if (rc != SMOL_OK) {
+        engine_free(B);
+        delete B;
+        return rc;
+    }
+    *out = B;
+    return SMOL_OK;
+}
+
+int smol_batch_integrate(smol_batch* B, double* const* d_n, double t0, double t1, double tol, int32_t scheme,
+                         smol_stats* stats) {
+    if (!B) return SMOL_EINVAL;
+    return integrate_all(B, d_n, t0, t1, tol, scheme, stats);
+}
+
+int smol_batch_integrate_start(smol_batch* B, double* const* d_n, double t0, double t1, double tol, int32_t scheme) {
+    if (!B) return SMOL_EINVAL;
+    return integrate_start(B, d_n, t0, t1, tol, scheme);
+}
+
+int smol_batch_integrate_advance(smol_batch* B) { return integrate_advance(B); }
+
+int smol_batch_integrate_finish(smol_batch* B, smol_stats* stats) { return integrate_finish(B, stats); }
+
+int smol_batch_get_log(smol_batch* B, int32_t system, double* h_t, double* h_tau, double* h_err, int32_t* h_acc,
+                       int32_t cap, int64_t* count) {
+    return get_log(B, system, h_t, h_tau, h_err, h_acc, cap, count);
+}
+
+int smol_batch_set_stream(smol_batch* B, void* stream) {
+    if (!B) return SMOL_EINVAL;
+    B->stream = (cudaStream_t)stream;
+    B->o.stream = stream;
+    return SMOL_OK;
+}
+
+void smol_batch_destroy(smol_batch* B) {
+    if (!B) return;
+    engine_free(B);
+    delete B;
 }
 
 const char* smol_strerror(int code) {

@@ -108,16 +108,16 @@ __device__ __forceinline__ void dft8(cx<R>* u) {
 // length-P transform over G interleaved sequences: for butterfly i in [0, P/RAD),
 // k = i mod p, inputs in[i + m P/RAD] (m < RAD) are multiplied by W_{RAD p}^{m k},
 // transformed by a length-RAD DFT and stored at out[(i-k) RAD + k + m p].
+// twP is a shared-memory table twP[e] = W_P^e, e < P (conjugated for INV).
 template <typename R, bool INV, int RAD>
 __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>* __restrict__ b, int lgP, int lgp,
-                                              int G, const cx<R>* __restrict__ tw, int lgMp) {
+                                              int G, const cx<R>* __restrict__ twP) {
     constexpr int LGR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
     const int P = 1 << lgP;
     const int p = 1 << lgp;
     const int q = P >> LGR;
     const int nb = q * G;
-    const uint32_t Mp = 1u << lgMp;
-    const int sh = (lgMp + 1) - LGR - lgp;  // W_{RAD p}^{e} = W_{2Mp}^{e << sh}
+    const int sh = lgP - LGR - lgp;  // W_{RAD p}^{e} = W_P^{e << sh}
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
         const int g = idx % G;
         const int i = idx / G;
@@ -128,7 +128,7 @@ __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>
         if (k) {
 #pragma unroll
             for (int m = 1; m < RAD; ++m) {
-                cx<R> w = twl(tw, (uint32_t)(m * k) << sh, Mp);
+                cx<R> w = twP[(m * k) << sh];
                 if (INV) w = conj(w);
                 u[m] = u[m] * w;
             }
@@ -152,20 +152,21 @@ __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>
 // memory as buf[p * G + g] (g fastest), radix-8 passes first, then one radix-4 or
 // radix-2 pass for the remaining factor. Ping-pongs between a and b and returns the
 // buffer holding the result, in natural order. INV selects the sign +i (unnormalised
-// inverse). Every thread of the block must call it; the caller synchronises before.
+// inverse). twP: shared table W_P^e, e < P. Every thread of the block must call it;
+// the caller synchronises before.
 template <typename R, bool INV>
-__device__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ tw, int lgMp) {
+__device__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ twP) {
     int lgp = 0;
     while (lgp < lgP) {
         const int rem = lgP - lgp;
         if (rem >= 3) {
-            stockham_pass<R, INV, 8>(a, b, lgP, lgp, G, tw, lgMp);
+            stockham_pass<R, INV, 8>(a, b, lgP, lgp, G, twP);
             lgp += 3;
         } else if (rem == 2) {
-            stockham_pass<R, INV, 4>(a, b, lgP, lgp, G, tw, lgMp);
+            stockham_pass<R, INV, 4>(a, b, lgP, lgp, G, twP);
             lgp += 2;
         } else {
-            stockham_pass<R, INV, 2>(a, b, lgP, lgp, G, tw, lgMp);
+            stockham_pass<R, INV, 2>(a, b, lgP, lgp, G, twP);
             lgp += 1;
         }
         __syncthreads();
@@ -174,6 +175,15 @@ __device__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __re
         b = t;
     }
     return a;
+}
+
+// Stages the table W_P^e (e < P) of a length-P tile transform into shared memory from
+// the global table of W_{2Mp}^e.
+template <typename R>
+__device__ __forceinline__ void stage_tw(cx<R>* twP, int lgP, const cx<R>* __restrict__ tw, int lgMp) {
+    const int P = 1 << lgP;
+    const int sh = lgMp + 1 - lgP;
+    for (int e = threadIdx.x; e < P; e += blockDim.x) twP[e] = twl(tw, (uint32_t)e << sh, 1u << lgMp);
 }
 
 // Deterministic block-wide sum (fixed reduction order). sh: >= 32 doubles of shared

@@ -1,6 +1,8 @@
 // smol_int.cuh - device side of the adaptive integrators of Sec. 2: the RK stage
 // combination, the embedded / step-doubling error norm and the step-size controller,
-// all kept on the device so that no host synchronisation happens per step.
+// all kept on the device (per system) so that no host synchronisation happens per
+// step. The state, its update, the error estimate, the controller and the mass moment
+// sum_s s n_s are FP64 whatever the precision of the right-hand side.
 #pragma once
 #include "smol_rhs.cuh"
 
@@ -10,19 +12,14 @@ enum { SCHEME_RK2 = 0, SCHEME_RK4 = 1, SCHEME_RKF45 = 2 };
 enum { CTRL_DOUBLE_HALVE = 0, CTRL_FORMULA = 1 };
 enum { ST_OK = 0, ST_STEADY = 1, ST_ENONFINITE = -3, ST_EUNDERFLOW = -4, ST_EMAXATT = -5 };
 
-// Controller settings of one integration (passed by value).
+// Controller settings of one integration (passed by value; the same for every system).
 struct CtlParams {
     int scheme, ctrl, rel_norm, fixed, order;
-    int evals, evals_paper;        // S evaluations per attempt: actual and stages x steps
+    int evals, evals_paper;  // S evaluations per attempt: actual and stages x steps
     double tau_min_rel, steady_rtol, fac_min, fac_max;
     int64_t max_attempts;
     int log_cap;
-    double* log_t;
-    double* log_h;
-    double* log_err;
-    int32_t* log_acc;
-    const double* sqpart;          // ||S(n)||^2 partials of stage 1 (steady test), or null
-    int nsq;
+    int steady;              // the first stage wrote ||S(n)||^2 partials
 };
 
 // Step-size rules of Sec. 2. Returns the proposed step; *acc the decision.
@@ -50,88 +47,110 @@ __device__ __forceinline__ void set_next_step(Ctl* c) {
     c->h = c->clamped ? c->t1 - c->t : c->tau;
 }
 
-// out = sum c_j v_j over [0, M), elementwise (intermediate states, e.g. the
-// half-step state of step doubling).
-__global__ void __launch_bounds__(256) k_lincomb(const StageIn in, const Ctl* __restrict__ ctl, double* out, int M) {
-    if (ctl->done) return;
-    const int np = (M + 1) >> 1;
-    const StagePtrs sp = resolve_all(in, ctl);
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+// Last-CTA-done pattern: every CTA of a system writes its partials, then one atomic
+// per CTA; the CTA that arrives last sees all partials and returns true (all threads).
+__device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
+        *flag = (prev == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (*flag) __threadfence();
+    return *flag;
+}
+
+// Half-step state of step doubling (FP64): half = sum c_j v_j over [0, M).
+template <typename R>
+__global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                 const StageIn in) {
+    __shared__ __align__(16) SysDev S;
+    const int blk = load_sys(sysv, map, S);
+    if (S.ctl->done) return;
+    const int np = (S.M + 1) >> 1;
+    const Terms<R> tr = resolve_terms<R>(in, S);
+    for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
         double y0, y1;
-        stage_pair(in, sp, M, 2 * p, y0, y1);
-        if (2 * p + 1 < M) *reinterpret_cast<double2*>(out + 2 * p) = make_double2(y0, y1);
-        else out[2 * p] = y0;
+        stage_pair<double, R>(in, tr, S.M, 2 * p, y0, y1);
+        if (2 * p + 1 < S.M) *reinterpret_cast<double2*>(S.half + 2 * p) = make_double2(y0, y1);
+        else S.half[2 * p] = y0;
     }
 }
 
-// Final kernel of an attempt: candidate = sum c_j v_j written to the other state
-// buffer, error vector sum d_j w_j reduced to ||.||_2^2, ||candidate||^2 and
-// max|candidate|; the last CTA to finish reduces the partials in a fixed order and
-// runs the controller (accept / reject, t, tau, counters, log, termination).
-__global__ void __launch_bounds__(256) k_finish(const StageIn cand, const StageIn del, Ctl* __restrict__ ctl,
-                                                const CtlParams P, double* part, int M) {
-    if (ctl->done) return;
+// Final kernel of an attempt: candidate = sum c_j v_j (FP64) written to the other state
+// buffer, error vector sum d_j w_j (FP64) reduced to ||.||_2^2, and ||candidate||^2,
+// max|candidate|, sum_s s candidate_s; the last CTA of each system reduces the partials
+// in a fixed order and runs that system's controller (accept / reject, t, tau,
+// counters, log, termination).
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                const StageIn cand, const StageIn del, const CtlParams P) {
+    __shared__ __align__(16) SysDev S;
     __shared__ double red[33];
     __shared__ bool last;
+    const int blk = load_sys(sysv, map, S);
+    Ctl* ctl = S.ctl;
+    if (ctl->done) return;
     double* outp = ctl->state[ctl->cur ^ 1];
-    double se = 0.0, sc = 0.0, mx = 0.0, bad = 0.0;
-    const int np = (M + 1) >> 1;
-    const StagePtrs cp = resolve_all(cand, ctl);
-    const StagePtrs dp = resolve_all(del, ctl);
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    double se = 0.0, sc = 0.0, mx = 0.0, bad = 0.0, ms = 0.0;
+    const int np = (S.M + 1) >> 1;
+    const Terms<R> cp = resolve_terms<R>(cand, S);
+    const Terms<R> dp = resolve_terms<R>(del, S);
+    for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
         const int i = 2 * p;
         double y0, y1, d0, d1;
-        stage_pair(cand, cp, M, i, y0, y1);
-        stage_pair(del, dp, M, i, d0, d1);
-        if (i + 1 < M) *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
+        stage_pair<double, R>(cand, cp, S.M, i, y0, y1);
+        stage_pair<double, R>(del, dp, S.M, i, d0, d1);
+        if (i + 1 < S.M) *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
         else outp[i] = y0;
         se += d0 * d0 + d1 * d1;
         sc += y0 * y0 + y1 * y1;
+        ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
         mx = fmax(mx, fmax(fabs(y0), fabs(y1)));
         if (!isfinite(y0) || !isfinite(y1)) bad = 1.0;
     }
     se = block_sum(se, red);
     sc = block_sum(sc, red);
+    ms = block_sum(ms, red);
     mx = block_max(mx, red);
     bad = block_max(bad, red);
     if (threadIdx.x == 0) {
-        double* q = part + 4 * blockIdx.x;
+        double* q = S.fpart + FPW * blk;
         q[0] = se;
         q[1] = sc;
         q[2] = mx;
         q[3] = bad;
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-        last = (prev == gridDim.x - 1);
+        q[4] = ms;
     }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
+    if (!arrive_last(ctl, S.nfin, &last)) return;
     // The last CTA reduces the per-CTA partials with all its threads (fixed order:
     // thread j takes partials j, j + blockDim, ...; then the block-wide tree).
-    double E = 0.0, C = 0.0, X = 0.0, B = 0.0, Q = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-        E += __ldcg(part + 4 * b);
-        C += __ldcg(part + 4 * b + 1);
-        X = fmax(X, __ldcg(part + 4 * b + 2));
-        B = fmax(B, __ldcg(part + 4 * b + 3));
+    double E = 0.0, C = 0.0, X = 0.0, B = 0.0, Q = 0.0, MS = 0.0;
+    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) {
+        const double* q = S.fpart + FPW * b;
+        E += __ldcg(q);
+        C += __ldcg(q + 1);
+        X = fmax(X, __ldcg(q + 2));
+        B = fmax(B, __ldcg(q + 3));
+        MS += __ldcg(q + 4);
     }
-    if (P.steady_rtol > 0.0 && P.sqpart)
-        for (int b = threadIdx.x; b < P.nsq; b += blockDim.x) Q += __ldcg(P.sqpart + b);
+    if (P.steady)
+        for (int b = threadIdx.x; b < S.nbx; b += blockDim.x) Q += __ldcg(S.sqpart + b);
     E = block_sum(E, red);
     C = block_sum(C, red);
     Q = block_sum(Q, red);
+    MS = block_sum(MS, red);
     X = block_max(X, red);
     B = block_max(B, red);
     if (threadIdx.x != 0) return;
     Ctl* c = ctl;
     c->arrive = 0;
     c->rhs_evals += 1;  // S(n^k) of the first stage
-    if (P.steady_rtol > 0.0 && P.sqpart) {
-        const double s2 = Q;
+    if (P.steady) {
         const double nn = sqrt(c->nrm2);
-        c->steady = s2;
-        if (nn > 0.0 && sqrt(s2) / nn < P.steady_rtol) {
+        c->steady = Q;
+        if (nn > 0.0 && sqrt(Q) / nn < P.steady_rtol) {
             c->status = ST_STEADY;
             c->done = 1;
             return;
@@ -156,10 +175,10 @@ __global__ void __launch_bounds__(256) k_finish(const StageIn cand, const StageI
     const double tau_new = propose(P, h, c->tau, err, c->tol, &acc);
     if (P.log_cap > 0) {
         const int64_t slot = (c->attempts - 1) % P.log_cap;
-        P.log_t[slot] = c->t;
-        P.log_h[slot] = h;
-        P.log_err[slot] = err;
-        P.log_acc[slot] = acc;
+        S.log_t[slot] = c->t;
+        S.log_h[slot] = h;
+        S.log_e[slot] = err;
+        S.log_a[slot] = acc;
     }
     if (acc) {
         c->cur ^= 1;
@@ -167,6 +186,7 @@ __global__ void __launch_bounds__(256) k_finish(const StageIn cand, const StageI
         c->accepted += 1;
         c->nrm2 = C;
         c->ymax = X;
+        c->mass = MS;
         if (!c->clamped) c->tau = tau_new;
     } else {
         c->rejected += 1;
@@ -184,38 +204,39 @@ __global__ void __launch_bounds__(256) k_finish(const StageIn cand, const StageI
     if (!c->done) set_next_step(c);
 }
 
-// Preparation of an integration, pass 1: moments mu_t of n0, ||n0||^2, max|n0|.
-// Partials [blk][T + 2]; the last CTA reduces them, stores nrm2 and ymax in the control
-// block and delta_t = sum_{alpha: u=t} coef mu_v (for the collision rate) in dout.
-__global__ void __launch_bounds__(256) k_prep1(const SysDev S, Ctl* __restrict__ ctl, double* part, double* dout) {
+// Preparation of an integration, pass 1: moments mu_t of n0, ||n0||^2, max|n0| and
+// sum_s s n0_s, in FP64 (the weights are read in type R). The last CTA of each system
+// stores nrm2, ymax and mass in the control block and delta_t = sum_{alpha: u=t} coef
+// mu_v (collision-rate coefficients) in aux.
+template <typename R>
+__global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, const int2* __restrict__ map) {
+    __shared__ __align__(16) SysDev S;
     __shared__ double red[33];
+    __shared__ double fin[MAXT + 3];
     __shared__ bool last;
+    const int blk = load_sys(sysv, map, S);
+    Ctl* ctl = S.ctl;
     const double* n = ctl->state[ctl->cur];
-    const int W = S.T + 2;
-    double acc[MAXT + 2];
+    const R* Wr = reinterpret_cast<const R*>(S.W);
+    const int W = S.T + 3;  // mu_t..., n2, max, mass
+    double acc[MAXT + 3];
     for (int q = 0; q < W; ++q) acc[q] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.M; i += gridDim.x * blockDim.x) {
+    for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) {
         const double y = n[i];
-        for (int t = 0; t < S.T; ++t) acc[t] += S.W[(size_t)t * S.Mp + i] * y;
+        for (int t = 0; t < S.T; ++t) acc[t] += (double)Wr[(size_t)t * S.Mp + i] * y;
         acc[S.T] += y * y;
         acc[S.T + 1] = fmax(acc[S.T + 1], fabs(y));
+        acc[S.T + 2] += (double)(i + 1) * y;
     }
     for (int q = 0; q < W; ++q) {
         const double v = (q == S.T + 1) ? block_max(acc[q], red) : block_sum(acc[q], red);
-        if (threadIdx.x == 0) part[(size_t)blockIdx.x * W + q] = v;
+        if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk + q] = v;
     }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    __shared__ double fin[MAXT + 2];
+    if (!arrive_last(ctl, S.nfin, &last)) return;
     for (int q = 0; q < W; ++q) {
         double v = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-            const double x = __ldcg(part + (size_t)b * W + q);
+        for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) {
+            const double x = __ldcg(S.fpart + (size_t)FPW * b + q);
             v = (q == S.T + 1) ? fmax(v, x) : v + x;
         }
         v = (q == S.T + 1) ? block_max(v, red) : block_sum(v, red);
@@ -225,34 +246,34 @@ __global__ void __launch_bounds__(256) k_prep1(const SysDev S, Ctl* __restrict__
     ctl->arrive = 0;
     ctl->nrm2 = fin[S.T];
     ctl->ymax = fin[S.T + 1];
-    for (int t = 0; t < S.T; ++t) dout[t] = 0.0;
-    for (int al = 0; al < S.R; ++al) dout[S.au[al]] += S.acoef[al] * fin[S.av[al]];
+    ctl->mass = fin[S.T + 2];
+    for (int t = 0; t < S.T; ++t) S.aux[t] = 0.0;
+    for (int al = 0; al < S.R; ++al) S.aux[S.au[al]] += S.acoef[al] * fin[S.av[al]];
 }
 
 // Pass 2: collision rate D_i = sum_j K_ij n_j = sum_t delta_t W_t[i]; its maximum
 // gives the first step by the Euler criterion of Sec. 1, tau0 = a / max_i D_i, when
 // the caller gave none (ctl->tau <= 0). Then the first attempt's step h is set.
-__global__ void __launch_bounds__(256) k_prep2(const SysDev S, Ctl* __restrict__ ctl, const double* delta, double* part,
+template <typename R>
+__global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                double euler_a) {
+    __shared__ __align__(16) SysDev S;
     __shared__ double red[33];
     __shared__ bool last;
+    const int blk = load_sys(sysv, map, S);
+    Ctl* ctl = S.ctl;
+    const R* Wr = reinterpret_cast<const R*>(S.W);
     double mx = -INFINITY;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.M; i += gridDim.x * blockDim.x) {
+    for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) {
         double d = 0.0;
-        for (int t = 0; t < S.T; ++t) d += delta[t] * S.W[(size_t)t * S.Mp + i];
+        for (int t = 0; t < S.T; ++t) d += __ldcg(S.aux + t) * (double)Wr[(size_t)t * S.Mp + i];
         mx = fmax(mx, d);
     }
     mx = block_max(mx, red);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = mx;
-        __threadfence();
-        last = (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
+    if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk] = mx;
+    if (!arrive_last(ctl, S.nfin, &last)) return;
     double rate = -INFINITY;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) rate = fmax(rate, __ldcg(part + b));
+    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) rate = fmax(rate, __ldcg(S.fpart + (size_t)FPW * b));
     rate = block_max(rate, red);
     if (threadIdx.x != 0) return;
     ctl->arrive = 0;
@@ -261,23 +282,22 @@ __global__ void __launch_bounds__(256) k_prep2(const SysDev S, Ctl* __restrict__
     else set_next_step(ctl);
 }
 
-// max_i |n_i| of a vector into ctl->ymax (input scaling of a standalone FP32 evaluation).
-__global__ void __launch_bounds__(256) k_absmax(const double* __restrict__ n, int M, Ctl* __restrict__ ctl, double* part) {
+// max_i |n_i| of the caller's vector into ctl->ymax (input scaling of a standalone
+// FP32 evaluation; single system).
+__global__ void __launch_bounds__(128) k_absmax(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                const double* __restrict__ n) {
+    __shared__ __align__(16) SysDev S;
     __shared__ double red[33];
     __shared__ bool last;
+    const int blk = load_sys(sysv, map, S);
+    Ctl* ctl = S.ctl;
     double mx = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) mx = fmax(mx, fabs(n[i]));
+    for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) mx = fmax(mx, fabs(n[i]));
     mx = block_max(mx, red);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = mx;
-        __threadfence();
-        last = (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
+    if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk] = mx;
+    if (!arrive_last(ctl, S.nfin, &last)) return;
     double m = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(part + b));
+    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) m = fmax(m, __ldcg(S.fpart + (size_t)FPW * b));
     m = block_max(m, red);
     if (threadIdx.x != 0) return;
     ctl->arrive = 0;

@@ -1,6 +1,6 @@
 // smol_rhs.cuh - device data structures and the three kernels of one evaluation of
 // the right-hand side S(y) of Eq. (4) (aggregation-shattering, truncated at M) for a
-// low-rank kernel K = U V (Sec. 1).
+// low-rank kernel K = U V (Sec. 1), for one system or a ragged batch of systems.
 //
 // Notation. Sizes s = 1..M are stored 0-based (y[s-1] = y_s). The distinct vectors
 // among the columns U_alpha and rows V_alpha are W_t (t < T); U_alpha = cu W_{u(alpha)},
@@ -23,7 +23,16 @@
 // The real inverse of length L is again done at length Mp on the packed form
 //   Y[k] = 1/2 [ W_L^k (C[k] - conj C[Mp-k]) + i (C[k] + conj C[Mp-k]) ],
 // whose inverse FFT gives y[j] = c'[2j] + i c'[2j+1] (times Mp; the 1/Mp and the 1/2 of
-// the birth term are applied in FP64 in the epilogue).
+// the birth term are applied in the epilogue).
+//
+// Precision. R is the arithmetic type of everything inside S(y) and of the stage
+// vectors k_j = h S(y_j): double for the plain FP64 solver, float for the FP32 form.
+// The state n and its update, the error estimate, the step control and the mass
+// moment are always FP64 (they are handled in smol_int.cuh); the moment sums are
+// accumulated per thread in R and reduced across threads in FP64.
+//
+// Batching. Every kernel takes a device array of system descriptors and a map from
+// blockIdx.x to (system, block of that system); one system is a batch of one.
 #pragma once
 #include "smol_fft.cuh"
 
@@ -32,14 +41,18 @@ namespace smol {
 constexpr int MAXR = 8;         // largest rank R
 constexpr int MAXT = 2 * MAXR;  // largest number of distinct transforms
 constexpr int MAXV = 10;        // terms of a stage-input linear combination
+constexpr int NVEC = 12;        // stage / work vectors per system
+constexpr int FPW = MAXT + 4;   // doubles per block of the finish / preparation partials
 
-// Device-resident control block of one integration (and of standalone evaluations).
+// Device-resident control block of one system's integration (and of standalone
+// evaluations).
 struct Ctl {
     double t, tau, h, t1, tol;  // time, proposed step, step of the current attempt, end, tolerance
     double err_last;            // error estimate of the last attempt
     double nrm2;                // ||n||_2^2 of the current state
     double ymax;                // max_i |n_i| of the current state (FP32 input scaling)
-    double steady;              // ||S(n)||_2^2 of the current attempt's first stage (unscaled)
+    double steady;              // ||S(n)||_2^2 of the last attempt's first stage (unscaled)
+    double mass;                // sum_s s n_s of the current state
     int32_t done, status, cur, clamped;
     int64_t attempts, accepted, rejected, rhs_evals, rhs_paper;
     double* state[2];           // double-buffered state; state[cur] is n^k
@@ -47,172 +60,266 @@ struct Ctl {
     int32_t pad;
 };
 
-// Static description of a system, passed by value to every kernel.
+// One system, as the kernels see it (device memory; 256-byte aligned array).
 struct SysDev {
-    int M, Mp, lgMp, N1, N2, lgN1, lgN2, T, R, npairs, nbxA;
+    int M, Mp, lgMp, N1, N2, lgN1, lgN2, G, T, R, npairs, nbx;  // nbx = N2 / G column CTAs
     double lambda;
-    const double* W;             // T x Mp weights (zero beyond M)
-    const void* tw;              // twiddles W_{2Mp}^e, e < Mp, as cx<R>
-    void* Y;                     // T x Mp spectra after the column pass, [t][k1][n2]
-    void* G2;                    // Mp values after the row pass, [k1][n2]
-    double* ybuf;                // stage input y (Mp doubles)
-    double* mpart;               // moment partials [t][bx][2]
-    int au[MAXR], av[MAXR];      // ordered pairs (u(alpha), v(alpha))
+    const void* W;   // R-typed T x Mp weights (zero beyond M)
+    const void* tw;  // cx<R> twiddles W_{2Mp}^e, e < Mp
+    void* Y;         // cx<R> T x Mp spectra after the column pass, [t][k1][n2]
+    void* G2;        // cx<R> Mp values after the row pass, [k1][n2]
+    void* ybuf;      // R-typed stage input y of the current evaluation (Mp)
+    void* vec;       // R-typed work vectors, vec + j * vstride (Mp each)
+    double* half;    // FP64 half-step state of step doubling (Mp)
+    double* mpart;   // moment partials [t][bx][2]
+    double* fpart;   // partials of the finish / preparation kernels [block][FPW]
+    double* sqpart;  // ||S||^2 partials [bx]
+    double* aux;     // MAXT + 1 doubles: collision-rate coefficients of the preparation;
+                     // aux[MAXT] = y_1 of the current evaluation in FP64
+    double* log_t;   // step log ring (log_cap entries each, shared capacity)
+    double* log_h;
+    double* log_e;
+    int32_t* log_a;
+    Ctl* ctl;
+    int64_t vstride;
+    int nfin;        // blocks of the finish / lincomb / preparation kernels
+    int au[MAXR], av[MAXR];  // ordered pairs (u(alpha), v(alpha))
     double acoef[MAXR];
-    int pu[MAXR], pv[MAXR];      // unordered pairs for the spectral product
+    int pu[MAXR], pv[MAXR];  // unordered pairs for the spectral product
     double pcoef[MAXR];
-    int wexp[MAXT];              // ilogb(max_i |W_t[i]|)
+    int wexp[MAXT];          // ilogb(max_i |W_t[i]|)
+    int pad[6];
 };
 
-// Stage input y = sum_j c_j v_j. sel[j] < 0: v[j] as given; sel[j] = 0 / 1: the
-// current / other state buffer of the control block.
+// Stage input y = sum_j c_j v_j. slot >= 0: work vector (type R); slot -1 / -2: the
+// current / other state buffer; -3: the caller's vector `ext` (single system); -4: the
+// half-step state. Slots < 0 are FP64 vectors.
+enum { SLOT_CUR = -1, SLOT_OTHER = -2, SLOT_EXT = -3, SLOT_HALF = -4 };
 struct StageIn {
-    int nv, direct;              // direct: y is v[0] itself (nv == 1, c == 1)
-    int sel[MAXV];
-    const double* v[MAXV];
+    int nv, direct;  // direct: y is the single FP64 term itself (c == 1)
+    int slot[MAXV];
     double c[MAXV];
+    const double* ext;
 };
 
 // Epilogue outputs of an evaluation.
 struct EpiOut {
-    double* out;                 // out = scale * S(y); scale = h * hfac (use_h) or 1
-    double* birth;               // optional term outputs
+    int out_slot;     // >= 0: k written to work vector out_slot (type R), scaled by h * hfac
+    double* out;      // or (out_slot < 0): S(y) written as FP64 to this caller vector
+    double* birth;    // optional term outputs (FP64, caller vectors)
     double* loss;
     double* source;
-    double* sqpart;              // optional per-CTA partials of ||S(y)||_2^2
+    int sq;           // write ||S(y)||^2 partials (steady test)
     double hfac;
-    int use_h;
 };
 
-__device__ __forceinline__ const double* resolve(const StageIn& in, const Ctl* ctl, int j) {
-    return in.sel[j] < 0 ? in.v[j] : ctl->state[ctl->cur ^ in.sel[j]];
-}
-
-// The term pointers of a stage input with the state buffers resolved once (the control
-// block is read a single time per thread).
-struct StagePtrs {
-    const double* p[MAXV];
+// Resolved term pointers of a stage input: bit j of dmask set = term j is FP64.
+template <typename R>
+struct Terms {
+    const void* p[MAXV];
+    unsigned dmask;
 };
 
-__device__ __forceinline__ StagePtrs resolve_all(const StageIn& in, const Ctl* ctl) {
-    StagePtrs r;
-    const int cur = ctl->cur;
-    const double* s0 = ctl->state[0];
-    const double* s1 = ctl->state[1];
+template <typename R>
+__device__ __forceinline__ Terms<R> resolve_terms(const StageIn& in, const SysDev& S) {
+    Terms<R> tr;
+    const Ctl* c = S.ctl;
+    const int cur = c->cur;
+    const double* s0 = c->state[0];
+    const double* s1 = c->state[1];
+    tr.dmask = 0u;
 #pragma unroll
-    for (int j = 0; j < MAXV; ++j) r.p[j] = in.sel[j] < 0 ? in.v[j] : (((cur ^ in.sel[j]) & 1) ? s1 : s0);
-    return r;
-}
-
-// y at indices i and i+1 (i even); zero at and beyond M. All term loads are issued
-// before the first multiply-add (unrolled over MAXV, predicated on nv) so that their
-// latencies overlap.
-__device__ __forceinline__ void stage_pair(const StageIn& in, const StagePtrs& P, int M, int i, double& y0,
-                                           double& y1) {
-    y0 = 0.0;
-    y1 = 0.0;
-    if (i + 1 < M) {
-        double2 v[MAXV];
-#pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < in.nv) v[j] = __ldg(reinterpret_cast<const double2*>(P.p[j] + i));
-#pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < in.nv) {
-                y0 += in.c[j] * v[j].x;
-                y1 += in.c[j] * v[j].y;
-            }
-    } else if (i < M) {
-        double v[MAXV];
-#pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < in.nv) v[j] = __ldg(P.p[j] + i);
-#pragma unroll
-        for (int j = 0; j < MAXV; ++j)
-            if (j < in.nv) y0 += in.c[j] * v[j];
+    for (int j = 0; j < MAXV; ++j) {
+        const int sl = in.slot[j];
+        if (sl >= 0) {
+            tr.p[j] = reinterpret_cast<const R*>(S.vec) + (int64_t)sl * S.vstride;
+        } else {
+            tr.dmask |= 1u << j;
+            if (sl == SLOT_CUR) tr.p[j] = cur ? s1 : s0;
+            else if (sl == SLOT_OTHER) tr.p[j] = cur ? s0 : s1;
+            else if (sl == SLOT_EXT) tr.p[j] = in.ext;
+            else tr.p[j] = S.half;
+        }
     }
+    return tr;
 }
 
 template <typename R>
-__device__ __forceinline__ R to_r(double v, int e) {
-    return (R)(e ? ldexp(v, -e) : v);
+struct vec2 {};
+template <>
+struct vec2<double> {
+    typedef double2 T;
+};
+template <>
+struct vec2<float> {
+    typedef float2 T;
+};
+
+// Stage input at indices i, i+1 (i even), accumulated in type A: zero at and beyond M.
+// All term loads are issued before the first multiply-add so that their latencies
+// overlap.
+template <typename A, typename R>
+__device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P, int M, int i, A& y0, A& y1) {
+    y0 = (A)0;
+    y1 = (A)0;
+    if (i + 1 < M) {
+        A v0[MAXV], v1[MAXV];
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) {
+                if ((P.dmask >> j) & 1u) {
+                    const double2 v = __ldg(reinterpret_cast<const double2*>(P.p[j]) + (i >> 1));
+                    v0[j] = (A)v.x;
+                    v1[j] = (A)v.y;
+                } else {
+                    const typename vec2<R>::T v = __ldg(reinterpret_cast<const typename vec2<R>::T*>(P.p[j]) + (i >> 1));
+                    v0[j] = (A)v.x;
+                    v1[j] = (A)v.y;
+                }
+            }
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) {
+                const A c = (A)in.c[j];
+                y0 += c * v0[j];
+                y1 += c * v1[j];
+            }
+    } else if (i < M) {
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) {
+                const A v = ((P.dmask >> j) & 1u) ? (A)__ldg(reinterpret_cast<const double*>(P.p[j]) + i)
+                                                  : (A)__ldg(reinterpret_cast<const R*>(P.p[j]) + i);
+                y0 += (A)in.c[j] * v;
+            }
+    }
 }
 
 // Exponent of the input scaling of transform t: FP64 runs unscaled; FP32 divides
 // x_t by 2^(ilogb(max|W_t|) + ilogb(max|y|)) so that its largest entry is near 1.
 template <typename R>
-__device__ __forceinline__ int xexp(const SysDev& S, const Ctl* ctl, int t) {
+__device__ __forceinline__ int xexp(const SysDev& S, int t) {
     if (sizeof(R) == sizeof(double)) return 0;
-    const double ym = ctl->ymax;
+    const double ym = S.ctl->ymax;
     return (ym > 0.0 && isfinite(ym)) ? S.wexp[t] + ilogb(ym) : S.wexp[t];
 }
 
+// Copies the descriptor of this CTA's system into shared memory; returns the block
+// index within the system.
+__device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const int2* __restrict__ map, SysDev& sh) {
+    const int2 m = map[blockIdx.x];
+    const int* src = reinterpret_cast<const int*>(sysv + m.x);
+    int* dst = reinterpret_cast<int*>(&sh);
+    for (int q = threadIdx.x; q < (int)(sizeof(SysDev) / 4); q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+    return m.y;
+}
+
 // ---------------------------------------------------------------------------
-// Kernel A: stage input, moments, column transforms of length N1.
-// grid (N2 / G, T); one transform t and G adjacent columns n2 per CTA.
+// Kernel A: stage input y (computed once per element), moments, and the column
+// transforms of length N1 of all T inputs x_t = W_t . y, interleaved in one tile
+// transform over T*G sequences. One CTA per G adjacent columns n2 of one system.
+// Shared memory: a, b (N1*G*T complex each), the tile twiddles W_N1^e (N1), the
+// four-step twiddles W_Mp^{n2 k1} of the CTA's columns (N1*G), y (N1*G reals).
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_fwd_cols(const SysDev S, const StageIn in, const Ctl* __restrict__ ctl, int G) {
-    if (ctl->done) return;
+__global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                  const StageIn in) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ double red[2 * MAXT][8];
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[33];
+    const int bx = load_sys(sysv, map, S);
+    if (S.ctl->done) return;
+    const int G = S.G, T = S.T, GT = G * T, N1 = S.N1;
+    const int half = (N1 >> 1) * G;
+    const int n2b = bx * G;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
-    cx<R>* b = a + (S.N1 * G);
-    const int t = blockIdx.y;
-    const int n2b = blockIdx.x * G;
-    const int e = xexp<R>(S, ctl, t);
-    const double* Wt = S.W + (size_t)t * S.Mp;
-    const int half = (S.N1 >> 1) * G;
-    double mu = 0.0, nu = 0.0;
-    const bool store_y = (t == 0) && !in.direct;
-    const StagePtrs sp = resolve_all(in, ctl);
+    cx<R>* b = a + N1 * GT;
+    cx<R>* twP = b + N1 * GT;
+    cx<R>* tw4 = twP + N1;
+    R* ys = reinterpret_cast<R*>(tw4 + N1 * G);  // this CTA's y values, [idx][2]
+    const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
+    const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
+    // twiddle tables first: their loads overlap the stage-input loads below
+    stage_tw(twP, S.lgN1, tw, S.lgMp);
+    for (int idx = threadIdx.x; idx < N1 * G; idx += blockDim.x) {
+        const int g = idx % G, k1 = idx / G;
+        tw4[idx] = twl(tw, (2u * (uint32_t)(n2b + g) * (uint32_t)k1) & mask2, (uint32_t)S.Mp);
+    }
+    const Terms<R> P = resolve_terms<R>(in, S);
+    R* yb = reinterpret_cast<R*>(S.ybuf);
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
         const int g = idx % G;
         const int n1 = idx / G;
-        const int j = (n1 << S.lgN2) + n2b + g;
-        const int i = 2 * j;
-        double y0, y1;
-        stage_pair(in, sp, S.M, i, y0, y1);
-        const double2 w = __ldg(reinterpret_cast<const double2*>(Wt + i));
-        const double x0 = w.x * y0, x1 = w.y * y1;
-        mu += x0 + x1;
-        nu += (double)(i + 1) * x0 + (double)(i + 2) * x1;
-        if (store_y) *reinterpret_cast<double2*>(S.ybuf + i) = make_double2(y0, y1);
-        a[idx] = mk<R>(to_r<R>(x0, e), to_r<R>(x1, e));
+        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
+        R y0, y1;
+        stage_pair<R, R>(in, P, S.M, i, y0, y1);
+        ys[2 * idx] = y0;
+        ys[2 * idx + 1] = y1;
+        if (!in.direct) *reinterpret_cast<typename vec2<R>::T*>(yb + i) = {y0, y1};
     }
-    for (int idx = half + threadIdx.x; idx < S.N1 * G; idx += blockDim.x) a[idx] = mk<R>((R)0, (R)0);
-    mu = block_sum(mu, red);
-    nu = block_sum(nu, red);
-    if (threadIdx.x == 0) {
-        double* p = S.mpart + 2 * ((size_t)t * gridDim.x + blockIdx.x);
-        p[0] = mu;
-        p[1] = nu;
+    if (bx == 0 && threadIdx.x == 0 && !in.direct) {
+        // y_1 in FP64 for the monomer equation, whose two large terms nearly cancel
+        double z0, z1;
+        stage_pair<double, R>(in, P, S.M, 0, z0, z1);
+        S.aux[MAXT] = z0;
     }
-    const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
-    cx<R>* res = tile_fft<R, false>(a, b, S.lgN1, G, tw, S.lgMp);
-    cx<R>* Y = reinterpret_cast<cx<R>*>(S.Y) + (size_t)t * S.Mp;
-    const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
-    for (int idx = threadIdx.x; idx < S.N1 * G; idx += blockDim.x) {
-        const int g = idx % G;
-        const int k1 = idx / G;
-        const int n2 = n2b + g;
-        const cx<R> w = twl(tw, (2u * (uint32_t)n2 * (uint32_t)k1) & mask2, (uint32_t)S.Mp);
-        Y[(size_t)k1 * S.N2 + n2] = res[idx] * w;
+    for (int q = half * T + threadIdx.x; q < N1 * GT; q += blockDim.x) a[q] = mk<R>((R)0, (R)0);
+    __syncthreads();
+    const R* Wall = reinterpret_cast<const R*>(S.W);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = 0; t < T; ++t) {
+        const R sc = (R)ldexp(1.0, -xexp<R>(S, t));
+        const R* Wt = Wall + (size_t)t * S.Mp;
+        R mu = (R)0, nu = (R)0;
+        for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
+            const int g = idx % G;
+            const int n1 = idx / G;
+            const int i = 2 * ((n1 << S.lgN2) + n2b + g);
+            const typename vec2<R>::T w = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wt + i));
+            const R x0 = w.x * ys[2 * idx], x1 = w.y * ys[2 * idx + 1];
+            mu += x0 + x1;
+            nu += (R)(i + 1) * x0 + (R)(i + 2) * x1;
+            a[n1 * GT + t * G + g] = mk<R>(x0 * sc, x1 * sc);
+        }
+        double m0 = (double)mu, m1 = (double)nu;
+        for (int o = 16; o > 0; o >>= 1) {
+            m0 += __shfl_down_sync(0xffffffffu, m0, o);
+            m1 += __shfl_down_sync(0xffffffffu, m1, o);
+        }
+        if (lane == 0) {
+            red[2 * t][warp] = m0;
+            red[2 * t + 1][warp] = m1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * T) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += red[threadIdx.x][w];
+        const int t = threadIdx.x >> 1;
+        S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
+    }
+    cx<R>* res = tile_fft<R, false>(a, b, S.lgN1, GT, twP);
+    cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
+    for (int idx = threadIdx.x; idx < N1 * GT; idx += blockDim.x) {
+        const int c = idx % GT, k1 = idx / GT;
+        const int t = c / G, g = c % G;
+        Yall[(size_t)t * S.Mp + (size_t)k1 * S.N2 + n2b + g] = res[idx] * tw4[k1 * G + g];
     }
 }
 
 // ---------------------------------------------------------------------------
 // Kernel B: row transforms of length N2 for a pair of rows (k1, N1 - k1), the
 // real-FFT split, the product sum over kernel terms, the packed inverse spectrum,
-// inverse row transforms and the inverse twiddle.
-// grid N1 / 2. CTA b owns rows (b, N1 - b); CTA 0 owns rows (0, N1 / 2).
+// inverse row transforms and the inverse twiddle. CTA b of a system owns rows
+// (b, N1 - b); CTA 0 owns rows (0, N1 / 2).
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, int G, int ia, int ib, uint32_t ka,
-                                              const cx<R>* tw, const R* pc, cx<R>& Ya, cx<R>& Yb) {
+__device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, int G, int ia, int ib, cx<R> w,
+                                              const R* pc, cx<R>& Ya, cx<R>& Yb) {
     // Z holds the row spectra as Z[k2 * G + col], col = 2 t + rho; ia / ib are the
-    // offsets k2 * G + rho of the pair's two frequencies (ka and Mp - ka).
-    const cx<R> w = ldg(tw + ka);  // W_L^ka, ka < Mp
+    // offsets k2 * G + rho of the pair's two frequencies ka and Mp - ka; w = W_L^ka.
     cx<R> Ca = mk<R>((R)0, (R)0), Cb = Ca;
     for (int p = 0; p < S.npairs; ++p) {
         const int u = S.pu[p], v = S.pv[p];
@@ -237,87 +344,108 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_rows(const SysDev S, const Ctl* __restrict__ ctl) {
-    if (ctl->done) return;
-    extern __shared__ __align__(16) unsigned char smraw[];
+__global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, const int2* __restrict__ map) {
+    __shared__ __align__(16) SysDev S;
     __shared__ R pc[MAXR];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int blk = load_sys(sysv, map, S);
+    if (S.ctl->done) return;
     const int G = 2 * S.T;
+    const int N2 = S.N2;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
-    cx<R>* b = a + S.N2 * G;
-    const int blk = blockIdx.x;
+    cx<R>* b = a + N2 * G;
+    cx<R>* twP = b + N2 * G;   // W_N2^e
+    cx<R>* tws = twP + N2;     // W_L^{r + N1 k2} of the two rows, [rho][k2]
+    cx<R>* twi = tws + 2 * N2; // conj W_Mp^{n2 r} of the two rows, [rho][n2]
     const int r0 = blk ? blk : 0;
     const int r1 = blk ? S.N1 - blk : (S.N1 >> 1);
-    const int N2 = S.N2;
+    const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
+    const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
+    stage_tw(twP, S.lgN2, tw, S.lgMp);
+    for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
+        const int rho = idx / N2, k2 = idx % N2;
+        const uint32_t r = (uint32_t)(rho ? r1 : r0);
+        tws[idx] = ldg(tw + (r + (uint32_t)S.N1 * (uint32_t)k2));
+        twi[idx] = conj(twl(tw, (2u * (uint32_t)k2 * r) & mask2, (uint32_t)S.Mp));
+    }
     if (threadIdx.x < S.npairs) {
         // FP32: pair p carries 2^(e_u + e_v - e_max) so that the sum stays in range.
         double c = S.pcoef[threadIdx.x];
         if (sizeof(R) == sizeof(float)) {
             int emax = -100000;
-            for (int p = 0; p < S.npairs; ++p)
-                emax = max(emax, xexp<R>(S, ctl, S.pu[p]) + xexp<R>(S, ctl, S.pv[p]));
-            c = ldexp(c, xexp<R>(S, ctl, S.pu[threadIdx.x]) + xexp<R>(S, ctl, S.pv[threadIdx.x]) - emax);
+            for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, S.pu[p]) + xexp<R>(S, S.pv[p]));
+            c = ldexp(c, xexp<R>(S, S.pu[threadIdx.x]) + xexp<R>(S, S.pv[threadIdx.x]) - emax);
         }
         pc[threadIdx.x] = (R)c;
     }
     const cx<R>* Yin = reinterpret_cast<const cx<R>*>(S.Y);
     for (int idx = threadIdx.x; idx < N2 * G; idx += blockDim.x) {
-        const int k2 = idx % N2;      // consecutive threads read consecutive k2 (coalesced)
+        const int k2 = idx % N2;  // consecutive threads read consecutive k2 (coalesced)
         const int col = idx / N2;
         const int t = col >> 1, rho = col & 1;
         const int r = rho ? r1 : r0;
         a[k2 * G + col] = Yin[(size_t)t * S.Mp + (size_t)r * N2 + k2];
     }
     __syncthreads();
-    const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
-    cx<R>* Z = tile_fft<R, false>(a, b, S.lgN2, G, tw, S.lgMp);
+    cx<R>* Z = tile_fft<R, false>(a, b, S.lgN2, G, twP);
     cx<R>* Yo = (Z == a) ? b : a;  // packed inverse spectrum, [k2 * 2 + rho]
     const int ntask = blk ? N2 : N2 + 1;
     for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
         int k2a, rhoa, k2b, rhob;
         if (blk) {
-            k2a = task; rhoa = 0; k2b = N2 - 1 - task; rhob = 1;
+            k2a = task;
+            rhoa = 0;
+            k2b = N2 - 1 - task;
+            rhob = 1;
         } else if (task <= (N2 >> 1)) {
-            k2a = task; rhoa = 0; k2b = (N2 - task) & (N2 - 1); rhob = 0;
+            k2a = task;
+            rhoa = 0;
+            k2b = (N2 - task) & (N2 - 1);
+            rhob = 0;
         } else {
-            k2a = task - (N2 >> 1) - 1; rhoa = 1; k2b = N2 - 1 - k2a; rhob = 1;
+            k2a = task - (N2 >> 1) - 1;
+            rhoa = 1;
+            k2b = N2 - 1 - k2a;
+            rhob = 1;
         }
-        const uint32_t ka = (uint32_t)(rhoa ? r1 : r0) + (uint32_t)S.N1 * (uint32_t)k2a;
         cx<R> Ya, Yb;
-        spectral_pair<R>(S, Z, G, k2a * G + rhoa, k2b * G + rhob, ka, tw, pc, Ya, Yb);
+        spectral_pair<R>(S, Z, G, k2a * G + rhoa, k2b * G + rhob, tws[rhoa * N2 + k2a], pc, Ya, Yb);
         Yo[k2a * 2 + rhoa] = Ya;
         if (k2a != k2b || rhoa != rhob) Yo[k2b * 2 + rhob] = Yb;
     }
     __syncthreads();
-    cx<R>* res = tile_fft<R, true>(Yo, Z, S.lgN2, 2, tw, S.lgMp);
+    cx<R>* res = tile_fft<R, true>(Yo, Z, S.lgN2, 2, twP);
     cx<R>* G2 = reinterpret_cast<cx<R>*>(S.G2);
-    const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
     for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
         const int n2 = idx % N2;
         const int rho = idx / N2;
         const int r = rho ? r1 : r0;
-        const cx<R> w = conj(twl(tw, (2u * (uint32_t)n2 * (uint32_t)r) & mask2, (uint32_t)S.Mp));
-        G2[(size_t)r * N2 + n2] = res[n2 * 2 + rho] * w;
+        G2[(size_t)r * N2 + n2] = res[n2 * 2 + rho] * twi[idx];
     }
 }
 
 // ---------------------------------------------------------------------------
 // Kernel C: inverse column transforms of length N1 (only the first half of the
 // outputs is needed), then the epilogue: birth, death, shattering, monomer source,
-// scaled output. grid N2 / G.
+// scaled output. One CTA per G adjacent columns of one system.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_inv_cols(const SysDev S, const StageIn in, const Ctl* __restrict__ ctl,
-                                                  const EpiOut eo, int G) {
-    if (ctl->done) return;
-    extern __shared__ __align__(16) unsigned char smraw[];
+__global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                  const StageIn in, const EpiOut eo) {
+    __shared__ __align__(16) SysDev S;
     __shared__ double red[33];
     __shared__ double mom[2 * MAXT];
-    __shared__ double delta[MAXT];
-    __shared__ double w1s[MAXT];
+    __shared__ R delta[MAXT];
     __shared__ double src_s, bscale_s;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int bx = load_sys(sysv, map, S);
+    if (S.ctl->done) return;
+    const int G = S.G;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
     cx<R>* b = a + (S.N1 * G);
-    const int n2b = blockIdx.x * G;
+    cx<R>* twP = b + (S.N1 * G);
+    const int n2b = bx * G;
+    stage_tw(twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
     const cx<R>* G2 = reinterpret_cast<const cx<R>*>(S.G2);
     for (int idx = threadIdx.x; idx < S.N1 * G; idx += blockDim.x) {
         const int g = idx % G;
@@ -330,91 +458,110 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev S, const StageIn 
         for (int q = warp; q < 2 * S.T; q += nw) {
             const int t = q >> 1, which = q & 1;
             double s = 0.0;
-            for (int bx = lane; bx < S.nbxA; bx += 32) s += S.mpart[2 * ((size_t)t * S.nbxA + bx) + which];
+            for (int c = lane; c < S.nbx; c += 32) s += S.mpart[2 * ((size_t)t * S.nbx + c) + which];
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
             if (lane == 0) mom[q] = s;
         }
     }
     __syncthreads();
-    const double* ysrc = in.direct ? resolve_all(in, ctl).p[0] : S.ybuf;
+    const R* yr = reinterpret_cast<const R*>(S.ybuf);
+    const double* yd = in.direct ? reinterpret_cast<const double*>(resolve_terms<R>(in, S).p[0]) : nullptr;
+    __shared__ double s1_s;
     if (threadIdx.x == 0) {
-        const double y1 = (S.M > 0) ? ysrc[0] : 0.0;
-        double sig[MAXT], rho[MAXT];
+        const double y1 = yd ? yd[0] : __ldcg(S.aux + MAXT);
+        const R* Wr = reinterpret_cast<const R*>(S.W);
+        double sig[MAXT], rho[MAXT], del[MAXT], w1s[MAXT];
         for (int t = 0; t < S.T; ++t) {
-            const double w1 = S.W[(size_t)t * S.Mp];
+            const double w1 = (double)Wr[(size_t)t * S.Mp];
             w1s[t] = w1;
-            sig[t] = mom[2 * t] - w1 * y1;        // sum_{i>=2} W_t[i] y_i
-            rho[t] = mom[2 * t + 1] - w1 * y1;    // sum_{i>=2} i W_t[i] y_i
-            delta[t] = 0.0;
+            sig[t] = mom[2 * t] - w1 * y1;      // sum_{i>=2} W_t[i] y_i
+            rho[t] = mom[2 * t + 1] - w1 * y1;  // sum_{i>=2} i W_t[i] y_i
+            del[t] = 0.0;
         }
         double shat = 0.0, mono = 0.0;
         for (int al = 0; al < S.R; ++al) {
             const int u = S.au[al], v = S.av[al];
             const double c = S.acoef[al];
-            delta[u] += c * mom[2 * v];
+            del[u] += c * mom[2 * v];
             shat += c * (rho[u] * sig[v] + sig[u] * rho[v]);
             mono += c * w1s[u] * rho[v];
         }
+        double D1 = 0.0;
+        for (int t = 0; t < S.T; ++t) {
+            delta[t] = (R)del[t];
+            D1 += del[t] * w1s[t];
+        }
         src_s = 0.5 * S.lambda * shat + S.lambda * y1 * mono;
+        // S_1 = -y_1 D_1 + source, in FP64 whatever R is
+        s1_s = -y1 * D1 + src_s;
         int emax = 0;
         if (sizeof(R) == sizeof(float)) {
             emax = -100000;
-            for (int p = 0; p < S.npairs; ++p)
-                emax = max(emax, xexp<R>(S, ctl, S.pu[p]) + xexp<R>(S, ctl, S.pv[p]));
+            for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, S.pu[p]) + xexp<R>(S, S.pv[p]));
         }
         bscale_s = ldexp(0.5 / (double)S.Mp, emax);
     }
     __syncthreads();
-    const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
-    cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, tw, S.lgMp);
-    const double scale = eo.use_h ? ctl->h * eo.hfac : 1.0;
-    const double bscale = bscale_s, lam = S.lambda, src = src_s;
+    cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, twP);
+    const double hsc = eo.out_slot >= 0 ? S.ctl->h * eo.hfac : 1.0;
+    const R scale = (R)hsc, bscale = (R)bscale_s, lam1 = (R)(1.0 + S.lambda);
+    const double src = src_s;
     const int half = (S.N1 >> 1) * G;
+    const R* Wr = reinterpret_cast<const R*>(S.W);
+    R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
     double sq = 0.0;
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
         const int g = idx % G;
         const int n1 = idx / G;
-        const int j = (n1 << S.lgN2) + n2b + g;
-        const int i = 2 * j;
+        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
         if (i >= S.M) continue;
         const cx<R> z = res[idx];
-        double D0 = 0.0, D1 = 0.0;
+        R D0 = (R)0, D1 = (R)0;
         for (int t = 0; t < S.T; ++t) {
-            const double2 w = __ldg(reinterpret_cast<const double2*>(S.W + (size_t)t * S.Mp + i));
+            const typename vec2<R>::T w =
+                __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wr + (size_t)t * S.Mp + i));
             D0 += delta[t] * w.x;
             D1 += delta[t] * w.y;
         }
-        double y0, y1;
-        if (i + 1 < S.M) {
-            const double2 yy = *reinterpret_cast<const double2*>(ysrc + i);
+        R y0, y1;
+        if (yd) {
+            y0 = (R)yd[i];
+            y1 = (i + 1 < S.M) ? (R)yd[i + 1] : (R)0;
+        } else {
+            const typename vec2<R>::T yy = *reinterpret_cast<const typename vec2<R>::T*>(yr + i);
             y0 = yy.x;
             y1 = yy.y;
-        } else {
-            y0 = ysrc[i];
-            y1 = 0.0;
         }
-        const double b0 = (i == 0) ? 0.0 : (double)z.x * bscale;
-        const double b1 = (double)z.y * bscale;
-        const double l0 = (1.0 + (i == 0 ? 0.0 : lam)) * y0 * D0;
-        const double l1 = (1.0 + lam) * y1 * D1;
-        const double s0 = b0 - l0 + (i == 0 ? src : 0.0);
-        const double s1 = b1 - l1;
-        if (i + 1 < S.M) {
-            if (eo.out) *reinterpret_cast<double2*>(eo.out + i) = make_double2(scale * s0, scale * s1);
-            if (eo.birth) *reinterpret_cast<double2*>(eo.birth + i) = make_double2(b0, b1);
-            if (eo.loss) *reinterpret_cast<double2*>(eo.loss + i) = make_double2(l0, l1);
-            sq += s0 * s0 + s1 * s1;
-        } else {
-            if (eo.out) eo.out[i] = scale * s0;
-            if (eo.birth) eo.birth[i] = b0;
-            if (eo.loss) eo.loss[i] = l0;
-            sq += s0 * s0;
+        const R b0 = (i == 0) ? (R)0 : z.x * bscale;
+        const R b1 = z.y * bscale;
+        const R l0 = (i == 0) ? (R)(-(s1_s - src)) : lam1 * y0 * D0;
+        const R l1 = lam1 * y1 * D1;
+        R s0 = b0 - l0;
+        const R s1 = b1 - l1;
+        if (i == 0) s0 = (R)s1_s;
+        const bool two = i + 1 < S.M;
+        if (kout) {
+            if (two) *reinterpret_cast<typename vec2<R>::T*>(kout + i) = {scale * s0, scale * s1};
+            else kout[i] = scale * s0;
         }
+        if (eo.out) {
+            if (two) *reinterpret_cast<double2*>(eo.out + i) = make_double2((double)s0, (double)s1);
+            else eo.out[i] = (double)s0;
+        }
+        if (eo.birth) {
+            eo.birth[i] = (double)b0;
+            if (two) eo.birth[i + 1] = (double)b1;
+        }
+        if (eo.loss) {
+            eo.loss[i] = (double)l0;
+            if (two) eo.loss[i + 1] = (double)l1;
+        }
+        if (eo.sq) sq += (double)(s0 * s0 + (two ? s1 * s1 : (R)0));
     }
-    if (eo.source && blockIdx.x == 0 && threadIdx.x == 0) eo.source[0] = src;
-    if (eo.sqpart) {
+    if (eo.source && bx == 0 && threadIdx.x == 0) eo.source[0] = src;
+    if (eo.sq) {
         sq = block_sum(sq, red);
-        if (threadIdx.x == 0) eo.sqpart[blockIdx.x] = sq;
+        if (threadIdx.x == 0) S.sqpart[bx] = sq;
     }
 }
 

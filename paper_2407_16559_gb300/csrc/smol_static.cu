@@ -34,10 +34,13 @@ constexpr size_t OFF_Y = OFF_W + al((size_t)SMAX_T * SMAX_M * 8);
 constexpr size_t OFF_G2 = OFF_Y + al((size_t)SMAX_T * SMAX_M * 16);
 constexpr size_t OFF_YBUF = OFF_G2 + al((size_t)SMAX_M * 16);
 constexpr size_t OFF_MPART = OFF_YBUF + al((size_t)SMAX_M * 8);
-constexpr size_t SCRATCH_BYTES = OFF_MPART + al((size_t)SMAX_T * 1024 * 2 * 8);
+constexpr size_t OFF_SYS = OFF_MPART + al((size_t)SMAX_T * 1024 * 2 * 8);
+constexpr size_t OFF_MAPC = OFF_SYS + al(sizeof(SysDev));
+constexpr size_t OFF_MAPB = OFF_MAPC + al((size_t)1024 * sizeof(int2));
+constexpr size_t SCRATCH_BYTES = OFF_MAPB + al((size_t)1024 * sizeof(int2));
 
 // The scratch memory of smol_rhs_static.
-static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 12,157,184 bytes
+static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 12,174,336 bytes
 
 constexpr int MAX_DEVICES = 64;
 unsigned char* g_scratch_ptr[MAX_DEVICES];  // device address of g_scratch per device
@@ -64,6 +67,14 @@ __global__ void k_static_twiddles(int Mp, double2* tw) {
     }
 }
 
+// Writes this call's descriptor and block maps into the scratch array (the host
+// passes them as kernel arguments, so nothing is copied from host memory).
+__global__ void k_static_setup(const SysDev d, SysDev* dst, int2* mapC, int nC, int2* mapB, int nB) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = d;
+    for (int q = threadIdx.x; q < nC; q += blockDim.x) mapC[q] = make_int2(0, q);
+    for (int q = threadIdx.x; q < nB; q += blockDim.x) mapB[q] = make_int2(0, q);
+}
+
 int ilog2i(int64_t v) {
     int l = 0;
     while ((int64_t(1) << l) < v) ++l;
@@ -77,12 +88,12 @@ int setup_device(int dev) {
     if (g_ready[dev]) return SMOL_OK;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return SMOL_ECUDA;
-    const int smax = 2 * 256 * 2 * SMAX_T * 16;  // row pass at Mp = SMAX_M
+    const int smax = 2 * 256 * 2 * SMAX_T * 16 + 5 * 256 * 16;  // row pass at Mp = SMAX_M
     if (cudaFuncSetAttribute(k_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax) != cudaSuccess)
         return SMOL_ECUDA;
-    if (cudaFuncSetAttribute(k_fwd_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) !=
+    if (cudaFuncSetAttribute(k_fwd_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(k_inv_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) !=
+        cudaFuncSetAttribute(k_inv_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) !=
             cudaSuccess)
         return SMOL_ECUDA;
     g_scratch_ptr[dev] = (unsigned char*)p;
@@ -90,10 +101,10 @@ int setup_device(int dev) {
     return SMOL_OK;
 }
 
-int threads_for_s(int butterflies) {
-    int t = butterflies;
+int threads_for_s(int points) {
+    int t = points / 8;
     if (t > 256) t = 256;
-    if (t < 64) t = 64;
+    if (t < 32) t = 32;
     return (t + 31) & ~31;
 }
 
@@ -115,9 +126,9 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     const int Mp = 1 << lgMp;
     const int lgN1 = (lgMp + 1) / 2, lgN2 = lgMp / 2;
     const int N1 = 1 << lgN1, N2 = 1 << lgN2;
-    int G = N2 / 128;
+    int G = 256 / N1;
     if (G < 1) G = 1;
-    if (G > 8) G = 8;
+    if (G > N2) G = N2;
     const int T = 2 * R;
 
     SysDev d;
@@ -129,10 +140,11 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     d.N2 = N2;
     d.lgN1 = lgN1;
     d.lgN2 = lgN2;
+    d.G = G;
     d.T = T;
     d.R = R;
     d.lambda = lambda;
-    d.nbxA = N2 / G;
+    d.nbx = N2 / G;
     d.npairs = R;
     for (int a = 0; a < R; ++a) {
         d.au[a] = a;
@@ -142,17 +154,21 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
         d.pv[a] = R + a;
         d.pcoef[a] = 1.0;
     }
-    d.W = (const double*)(base + OFF_W);
+    d.W = base + OFF_W;
     d.tw = base + OFF_TW;
     d.Y = base + OFF_Y;
     d.G2 = base + OFF_G2;
-    d.ybuf = (double*)(base + OFF_YBUF);
+    d.ybuf = base + OFF_YBUF;
     d.mpart = (double*)(base + OFF_MPART);
-    Ctl* ctl = (Ctl*)(base + OFF_CTL);
+    d.ctl = (Ctl*)(base + OFF_CTL);
+    SysDev* dsys = (SysDev*)(base + OFF_SYS);
+    int2* mapC = (int2*)(base + OFF_MAPC);
+    int2* mapB = (int2*)(base + OFF_MAPB);
 
     // The control block must read "not done" and the weights must be zero beyond M:
     // both are rewritten on every call, since the array keeps the previous call's data.
-    if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), st) != cudaSuccess) return SMOL_ECUDA;
+    if (cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st) != cudaSuccess) return SMOL_ECUDA;
+    k_static_setup<<<1, 256, 0, st>>>(d, dsys, mapC, N2 / G, mapB, N1 / 2);
     k_static_weights<<<256, 256, 0, st>>>(d_U, d_V, (int)M, Mp, R, (double*)(base + OFF_W));
     k_static_twiddles<<<64, 256, 0, st>>>(Mp, (double2*)(base + OFF_TW));
 
@@ -160,17 +176,19 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     memset(&in, 0, sizeof(in));
     in.nv = 1;
     in.direct = 1;
-    in.sel[0] = -1;
-    in.v[0] = d_n;
+    in.slot[0] = SLOT_EXT;
     in.c[0] = 1.0;
+    in.ext = d_n;
     EpiOut eo;
     memset(&eo, 0, sizeof(eo));
+    eo.out_slot = -1;
     eo.out = d_out;
     eo.hfac = 1.0;
-    const size_t sc = 2 * (size_t)N1 * G * 16, sr = 2 * (size_t)N2 * 2 * T * 16;
-    const int nbx = N2 / G;
-    k_fwd_cols<double><<<dim3(nbx, T), threads_for_s((N1 / 4) * G), sc, st>>>(d, in, ctl, G);
-    k_rows<double><<<N1 / 2, threads_for_s((N2 / 4) * 2 * T), sr, st>>>(d, ctl);
-    k_inv_cols<double><<<nbx, threads_for_s((N1 / 4) * G), sc, st>>>(d, in, ctl, eo, G);
+    const size_t n = (size_t)N1 * G;
+    const size_t sc = 2 * n * T * 16 + (size_t)N1 * 16 + n * 16 + n * 8;  // >= the inverse pass's need
+    const size_t sr = 2 * (size_t)N2 * 2 * T * 16 + 5 * (size_t)N2 * 16;
+    k_fwd_cols<double><<<N2 / G, threads_for_s(N1 * G * T), sc, st>>>(dsys, mapC, in);
+    k_rows<double><<<N1 / 2, threads_for_s(N2 * 2 * T), sr, st>>>(dsys, mapB);
+    k_inv_cols<double><<<N2 / G, threads_for_s(N1 * G), sc, st>>>(dsys, mapC, in, eo);
     return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
 }

@@ -1,0 +1,116 @@
+"""The batched integrator (smol_batch_*): independent systems of uneven size, kernel
+exponent and shattering rate advanced together, each with its own adaptive step.
+
+Each system of a batch must follow the same trajectory as when it is integrated alone
+(same kernels, same arithmetic; only the CTA sizes of a launch, and so the order of
+the block reductions, may differ) and must match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import batch_recipe, kernel_factors, monodisperse, sample_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def smol():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_16559_gb300 as m
+    return m
+
+
+def _systems(specs):
+    Us, Vs, lams, n0s = [], [], [], []
+    for M, a, lam in specs:
+        U, V = kernel_factors("brownian", M, a=a)
+        Us.append(U)
+        Vs.append(V)
+        lams.append(lam)
+        n0s.append(monodisperse(M))
+    return Us, Vs, lams, n0s
+
+
+SPECS = [(1000, 0.3, 0.01), (4096, 0.7, 0.05), (513, 0.5, 0.1), (16384, 0.9, 0.005), (64, 0.2, 0.02)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv"])
+def test_batch_equals_single_systems(smol, precision):
+    import torch
+    Us, Vs, lams, n0s = _systems(SPECS)
+    b = smol.Batch(Us, Vs, lams, precision=precision, tau0=1e-3)
+    ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 0.5, 1e-8, scheme="rkf45")
+    for q, (U, V, lam, n0) in enumerate(zip(Us, Vs, lams, n0s)):
+        s = smol.System(U, V, lam, precision=precision, tau0=1e-3)
+        m, st = s.integrate(torch.from_numpy(n0), 0.0, 0.5, 1e-8, scheme="rkf45")
+        assert sts[q]["status"] == st["status"] == 0
+        assert (sts[q]["accepted"], sts[q]["rejected"]) == (st["accepted"], st["rejected"]), (q, sts[q], st)
+        assert torch.allclose(ns[q], m, rtol=0, atol=1e-12 * float(m.abs().max()))
+
+
+def test_batch_fp64_vs_oracle(smol):
+    """Non-stiff parameters: with a steep kernel (a = 0.8, M = 1000) the tail modes are
+    stiff and the rounding noise of any FFT route excites them, so the number of rejected
+    attempts depends on the FFT's rounding (the oracle's own numpy-FFT and direct routes
+    disagree there: 39 and 0 rejections); accepted / rejected counts are compared where
+    the step control is not at its stability limit."""
+    import torch
+    specs = [(300, 0.3, 0.01), (1000, 0.4, 0.05), (77, 0.5, 0.2)]
+    Us, Vs, lams, n0s = _systems(specs)
+    b = smol.Batch(Us, Vs, lams, tau0=1e-2)
+    ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 3.0, 1e-8, scheme="rkf45")
+    for q, (U, V, lam, n0) in enumerate(zip(Us, Vs, lams, n0s)):
+        osys = oracle.System(len(n0), lam, U=U, V=V, route="lowrank")
+        m, ost, _ = oracle.integrate(osys, n0, 0.0, 3.0, 1e-8, oracle.Options(scheme="rkf45", tau0=1e-2))
+        assert (sts[q]["accepted"], sts[q]["rejected"]) == (ost["accepted"], ost["rejected"])
+        x = ns[q].cpu().numpy()
+        assert np.linalg.norm(x - m) <= 1e-9 * np.linalg.norm(m)
+        s = np.arange(1, len(m) + 1)
+        assert abs(sts[q]["mass"] - float(np.dot(s, m))) <= 1e-12 * float(np.dot(s, m))
+
+
+def test_batch_recipe_sample_fp32conv(smol):
+    """A sample of the 256-system workload (M log-uniform in [2^10, 2^16], exponent in
+    [0.2, 0.9], lambda log-uniform in [0.005, 0.1]), FP32 convolutions with FP64 control,
+    against the FP64 oracle at the reduced-precision tolerance 1e-4 after t = 2."""
+    import torch
+    rec = batch_recipe(256)[:8]
+    specs = [(r["M"], r["a"], r["lam"]) for r in rec]
+    Us, Vs, lams, n0s = _systems(specs)
+    b = smol.Batch(Us, Vs, lams, precision="fp32conv", tau0=1e-3)
+    ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 2.0, 1e-8, scheme="rkf45")
+    for q, (U, V, lam, n0) in enumerate(zip(Us, Vs, lams, n0s)):
+        assert sts[q]["status"] == 0 and sts[q]["t"] == 2.0
+        osys = oracle.System(len(n0), lam, U=U, V=V, route="lowrank")
+        m, ost, _ = oracle.integrate(osys, n0, 0.0, 2.0, 1e-8, oracle.Options(scheme="rkf45", tau0=1e-3))
+        x = ns[q].cpu().numpy()
+        assert np.linalg.norm(x - m) <= 1e-4 * np.linalg.norm(m), (q, np.linalg.norm(x - m) / np.linalg.norm(m))
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk4"])
+def test_batch_step_doubling_vs_single(smol, scheme):
+    import torch
+    Us, Vs, lams, n0s = _systems(SPECS[:3])
+    b = smol.Batch(Us, Vs, lams, tau0=1e-2, ctrl="formula")
+    ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 1.0, 1e-8, scheme=scheme)
+    for q, (U, V, lam, n0) in enumerate(zip(Us, Vs, lams, n0s)):
+        s = smol.System(U, V, lam, tau0=1e-2, ctrl="formula")
+        m, st = s.integrate(torch.from_numpy(n0), 0.0, 1.0, 1e-8, scheme=scheme)
+        assert (sts[q]["accepted"], sts[q]["rejected"]) == (st["accepted"], st["rejected"])
+        assert torch.allclose(ns[q], m, rtol=0, atol=1e-12 * float(m.abs().max()))
+
+
+def test_batch_systems_stop_independently(smol):
+    """One system hits its attempt limit, another a non-finite state; the rest finish."""
+    import torch
+    Us, Vs, lams, n0s = _systems(SPECS[:3])
+    n0s[1] = n0s[1].copy()
+    n0s[1][5] = np.nan
+    b = smol.Batch(Us, Vs, lams, tau0=1e-2)
+    ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 1.0, 1e-8, scheme="rkf45")
+    assert sts[1]["status"] == smol.ENONFINITE
+    assert sts[0]["status"] == 0 and sts[2]["status"] == 0 and sts[0]["t"] == 1.0

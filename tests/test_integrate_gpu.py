@@ -7,7 +7,7 @@ Modes:
     accept / reject decisions (counts equal) and the states agree far below tol;
   * the closed-form constant-kernel solution;
   * error statuses (non-finite state, step underflow, attempt limit) and the steady stop.
-The error estimate is compared at 1e-5 relative and the step sizes at 1e-5: the oracle
+The error estimate is compared at 1e-5 relative and the step sizes at 1e-3: the oracle
 forms err = ||n_RK5 - n^{k+1}|| from two separately rounded O(1) states (about 1e-8
 relative noise when err ~ tol), the device from the weight differences, and each step
 factor (tol/err)^(1/p) carries that noise into every later step.
@@ -75,7 +75,9 @@ def test_adaptive_parity_relaxation(smol, scheme, ctrl):
     oe = np.array([x[2] for x in olog])[-k:]
     oa = np.array([x[3] for x in olog])[-k:]
     assert np.array_equal(acc, oa)
-    assert np.allclose(h, oh, rtol=1e-5, atol=0)
+    # where err approaches the oracle's rounding floor its relative noise is large and
+    # (tol/err)^(1/p) carries it into the next step; decisions and states agree above
+    assert np.allclose(h, oh, rtol=1e-3, atol=0)
     # atol: the oracle forms err from O(1) states, so below ~1e-14 it is rounding noise
     assert np.allclose(e, oe, rtol=1e-5, atol=1e-14)
 
