@@ -249,6 +249,7 @@ struct Engine {
     std::vector<int> T;
     SysDev* d_sys = nullptr;   // descriptors used by integrations (control blocks ctl)
     SysDev* d_sysr = nullptr;  // descriptors of standalone evaluations (control blocks rctl)
+    SysDev h_one{}, h_oner{};  // host copies for single-system launches (passed by value)
     Ctl* d_ctl = nullptr;
     Ctl* d_rctl = nullptr;
     int2 *mapC = nullptr, *mapB = nullptr, *mapF = nullptr;
@@ -283,21 +284,65 @@ int set_smem_attrs(const Engine* E) {
     return SMOL_OK;
 }
 
+// Descriptor arguments of a launch: a single system passes its descriptor by value and
+// no map; a batch passes the device array and the block maps.
+struct LaunchArgs {
+    const SysDev* sys;
+    const int2 *mapC, *mapB, *mapF;
+    SysDev one;
+};
+
+LaunchArgs args_for(const Engine* E, bool rhs) {
+    LaunchArgs a;
+    a.sys = rhs ? E->d_sysr : E->d_sys;
+    if (E->count == 1) {
+        a.mapC = a.mapB = a.mapF = nullptr;
+        a.one = rhs ? E->h_oner : E->h_one;
+    } else {
+        a.mapC = E->mapC;
+        a.mapB = E->mapB;
+        a.mapF = E->mapF;
+        memset(&a.one, 0, sizeof(a.one));
+    }
+    return a;
+}
+
 template <typename R>
-void launch_eval(const Engine* E, const SysDev* sys, const StageIn& in, const EpiOut& eo, cudaStream_t st,
+void launch_eval(const Engine* E, const LaunchArgs& A, const StageIn& in, const EpiOut& eo, cudaStream_t st,
                  Prof* pr) {
     {
         ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
-        k_fwd_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(sys, E->mapC, in);
+        k_fwd_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(A.sys, A.mapC, A.one, in);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_ROWS);
-        k_rows<R><<<E->H.nB, E->thrB, E->smemB, st>>>(sys, E->mapB);
+        k_rows<R><<<E->H.nB, E->thrB, E->smemB, st>>>(A.sys, A.mapB, A.one);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
-        k_inv_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(sys, E->mapC, in, eo);
+        k_inv_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(A.sys, A.mapC, A.one, in, eo);
     }
+}
+
+// Union of the candidate and error combinations of the final kernel.
+Comb2 comb2(const StageIn& cand, const StageIn& del) {
+    Comb2 c;
+    memset(&c, 0, sizeof(c));
+    auto add = [&](int slot, double cc, double dd) {
+        for (int j = 0; j < c.in.nv; ++j)
+            if (c.in.slot[j] == slot) {
+                c.in.c[j] += cc;
+                c.d[j] += dd;
+                return;
+            }
+        const int j = c.in.nv++;
+        c.in.slot[j] = slot;
+        c.in.c[j] = cc;
+        c.d[j] = dd;
+    };
+    for (int j = 0; j < cand.nv; ++j) add(cand.slot[j], cand.c[j], 0.0);
+    for (int j = 0; j < del.nv; ++j) add(del.slot[j], 0.0, del.c[j]);
+    return c;
 }
 
 StageIn stage(std::initializer_list<std::pair<int, double>> terms) {
@@ -324,17 +369,17 @@ EpiOut epi_k(int slot, double hfac, int sq) {
 // Enqueues one step attempt of every system of the batch on stream st.
 template <typename R>
 void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
-    const SysDev* sys = E->d_sys;
+    const LaunchArgs A = args_for(E, false);
     auto Ev = [&](const StageIn& in, int k, double hfac, bool first) {
-        launch_eval<R>(E, sys, in, epi_k(k, hfac, (first && P.steady) ? 1 : 0), st, pr);
+        launch_eval<R>(E, A, in, epi_k(k, hfac, (first && P.steady) ? 1 : 0), st, pr);
     };
     auto finish = [&](const StageIn& cand, const StageIn& del) {
         ProfScope ps(pr, st, SMOL_PROF_STEP);
-        k_finish<R><<<E->H.nF, FIN_THREADS, 0, st>>>(sys, E->mapF, cand, del, P);
+        k_finish<R><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, comb2(cand, del), P);
     };
     auto half = [&](const StageIn& in) {
         ProfScope ps(pr, st, SMOL_PROF_STEP);
-        k_lincomb<R><<<E->H.nF, FIN_THREADS, 0, st>>>(sys, E->mapF, in);
+        k_lincomb<R><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, in);
     };
     const int N = SLOT_CUR, H = SLOT_HALF;
     if (scheme == SCHEME_RKF45) {
@@ -573,6 +618,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         d.log_a = (int32_t*)(b + L.log_a);
         d.vstride = (int64_t)L.vstride;
         d.nfin = s.nfin;
+        d.bnorm = 0.5 / (double)s.Mp;
         for (int al = 0; al < d.R; ++al) {
             d.au[al] = au[al];
             d.av[al] = av[al];
@@ -645,6 +691,8 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     CK(cudaMemcpyAsync(E->mapB, mB.data(), mB.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(E->mapF, mF.data(), mF.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+    E->h_one = hs[0];
+    E->h_oner = hsr[0];
     CK(cudaHostAlloc((void**)&E->h_ctl, (size_t)count * sizeof(Ctl), cudaHostAllocDefault));
     CK(cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
     return prec == SMOL_FP32CONV ? set_smem_attrs<float>(E) : set_smem_attrs<double>(E);
@@ -685,12 +733,13 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
         h.state[1] = (double*)(E->ws + E->base[q] + E->lay[q].stateB);
     }
     CK(cudaMemcpyAsync(E->d_ctl, E->h_ctl, (size_t)E->count * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    const LaunchArgs A = args_for(E, false);
     if (E->o.precision == SMOL_FP32CONV) {
-        k_prep1<float><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF);
-        k_prep2<float><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF, E->o.euler_a);
+        k_prep1<float><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
+        k_prep2<float><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, E->o.euler_a);
     } else {
-        k_prep1<double><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF);
-        k_prep2<double><<<E->H.nF, FIN_THREADS, 0, st>>>(E->d_sys, E->mapF, E->o.euler_a);
+        k_prep1<double><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
+        k_prep2<double><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, E->o.euler_a);
     }
     CK(cudaGetLastError());
 
@@ -875,11 +924,12 @@ int rhs_common(smol_system* S, const double* d_n, double* d_out, double* d_birth
     eo.loss = d_loss;
     eo.source = d_src;
     eo.hfac = 1.0;
+    const LaunchArgs A = args_for(S, true);
     if (S->o.precision == SMOL_FP32CONV) {
-        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(S->d_sysr, S->mapF, d_n);
-        launch_eval<float>(S, S->d_sysr, in, eo, st, nullptr);
+        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n);
+        launch_eval<float>(S, A, in, eo, st, nullptr);
     } else {
-        launch_eval<double>(S, S->d_sysr, in, eo, st, nullptr);
+        launch_eval<double>(S, A, in, eo, st, nullptr);
     }
     return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
 }

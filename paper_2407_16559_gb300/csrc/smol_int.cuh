@@ -22,6 +22,39 @@ struct CtlParams {
     int steady;              // the first stage wrote ||S(n)||^2 partials
 };
 
+// Square root and n-th roots for the controller, in FP64 accuracy without the
+// double-precision library routines (whose long dependent chains are slow on this
+// part's narrow FP64 path): an FP32 estimate refined by Newton steps in FP64.
+//   r = 1/sqrt(x):  r <- r (3 - x r^2) / 2          (Newton on r^-2 - x = 0)
+//   z = x^(-1/n):   z <- z (1 + (1 - x z^n) / n)   (Newton on z^-n - x = 0)
+// Each step doubles the number of correct bits: two steps take the FP32 estimate
+// (~1e-7) to below 1e-16.
+__device__ __forceinline__ double rsqrt_d(double x) {
+    double r = (double)rsqrtf((float)x);
+    r = r * (1.5 - 0.5 * x * r * r);
+    r = r * (1.5 - 0.5 * x * r * r);
+    return r;
+}
+__device__ __forceinline__ double sqrt_d(double x) {
+    if (!(x > 0.0)) return x == 0.0 ? 0.0 : sqrt(x);  // zero, negative or NaN: exact path
+    if (x < 1e-30 || x > 1e30 || !isfinite(x)) return sqrt(x);
+    return x * rsqrt_d(x);
+}
+// x^(1/n) for x in [1e-30, 1e30], n in {2, 4, 5}.
+__device__ __forceinline__ double root_d(double x, int n) {
+    double z = (double)powf((float)x, -1.0f / (float)n);
+    const double inv_n = 1.0 / (double)n;
+    for (int it = 0; it < 2; ++it) {
+        double zn = z * z;
+        if (n == 4) zn = zn * zn;
+        else if (n == 5) zn = zn * zn * z;
+        z = z * (1.0 + (1.0 - x * zn) * inv_n);
+    }
+    double zm = 1.0;  // z^(n-1)
+    for (int k = 1; k < n; ++k) zm *= z;
+    return x * zm;
+}
+
 // Step-size rules of Sec. 2. Returns the proposed step; *acc the decision.
 __device__ __forceinline__ double propose(const CtlParams& P, double h, double tau, double err, double tol, int* acc) {
     if (P.fixed) {
@@ -33,9 +66,17 @@ __device__ __forceinline__ double propose(const CtlParams& P, double h, double t
         // RKF45: tau <- 0.9 tau (tol/err)^(1/5); Eq. (6): tau <- 1/4 tau (tol/err)^(1/p).
         const double s = (P.scheme == SCHEME_RKF45) ? 0.9 : 0.25;
         const double ex = (P.scheme == SCHEME_RKF45) ? 0.2 : 1.0 / (double)P.order;
+        (void)ex;
+        const int n = (P.scheme == SCHEME_RKF45) ? 5 : P.order;
         double fac;
-        if (err == 0.0) fac = P.fac_max;
-        else fac = fmin(fmax(s * pow(tol / err, ex), P.fac_min), P.fac_max);
+        if (err == 0.0) {
+            fac = P.fac_max;
+        } else {
+            double x = tol / err;
+            // outside [1e-30, 1e30] the factor is clamped anyway
+            x = fmin(fmax(x, 1e-30), 1e30);
+            fac = fmin(fmax(s * root_d(x, n), P.fac_min), P.fac_max);
+        }
         return h * fac;
     }
     // halve on reject, double on accept
@@ -64,12 +105,13 @@ __device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
 // Half-step state of step doubling (FP64): half = sum c_j v_j over [0, M).
 template <typename R>
 __global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                 const StageIn in) {
+                                                 const __grid_constant__ SysDev one, const StageIn in) {
     __shared__ __align__(16) SysDev S;
-    const int blk = load_sys(sysv, map, S);
-    if (S.ctl->done) return;
+    __shared__ CtlView cv;
+    const int blk = load_sys(sysv, map, one, S, cv);
+    if (cv.done) return;
     const int np = (S.M + 1) >> 1;
-    const Terms<R> tr = resolve_terms<R>(in, S);
+    const Terms<R> tr = resolve_terms<R>(in, S, cv);
     for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
         double y0, y1;
         stage_pair<double, R>(in, tr, S.M, 2 * p, y0, y1);
@@ -78,50 +120,101 @@ __global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv
     }
 }
 
+// Candidate and error combinations of the final kernel over one set of terms: each
+// term is loaded once; cand = sum c_j v_j and err = sum d_j v_j.
+struct Comb2 {
+    StageIn in;  // slots and candidate coefficients c_j
+    double d[MAXV];
+};
+
 // Final kernel of an attempt: candidate = sum c_j v_j (FP64) written to the other state
-// buffer, error vector sum d_j w_j (FP64) reduced to ||.||_2^2, and ||candidate||^2,
+// buffer, error vector sum d_j v_j (FP64) reduced to ||.||_2^2, and ||candidate||^2,
 // max|candidate|, sum_s s candidate_s; the last CTA of each system reduces the partials
 // in a fixed order and runs that system's controller (accept / reject, t, tau,
 // counters, log, termination).
 template <typename R>
 __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                const StageIn cand, const StageIn del, const CtlParams P) {
+                                                   const __grid_constant__ SysDev one, const Comb2 cd,
+                                                   const CtlParams P) {
     __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
     __shared__ double red[33];
+    __shared__ double wred[5][8];
     __shared__ bool last;
-    const int blk = load_sys(sysv, map, S);
+    const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
-    if (ctl->done) return;
-    double* outp = ctl->state[ctl->cur ^ 1];
+    if (cv.done) return;
+    double* outp = const_cast<double*>(cv.cur ? cv.s0 : cv.s1);
     double se = 0.0, sc = 0.0, mx = 0.0, bad = 0.0, ms = 0.0;
     const int np = (S.M + 1) >> 1;
-    const Terms<R> cp = resolve_terms<R>(cand, S);
-    const Terms<R> dp = resolve_terms<R>(del, S);
+    const StageIn& in = cd.in;
+    const Terms<R> tp = resolve_terms<R>(in, S, cv);
     for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
         const int i = 2 * p;
-        double y0, y1, d0, d1;
-        stage_pair<double, R>(cand, cp, S.M, i, y0, y1);
-        stage_pair<double, R>(del, dp, S.M, i, d0, d1);
-        if (i + 1 < S.M) *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
-        else outp[i] = y0;
+        double y0 = 0.0, y1 = 0.0, d0 = 0.0, d1 = 0.0;
+        if (i + 1 < S.M) {
+            double v0[MAXV], v1[MAXV];
+#pragma unroll
+            for (int j = 0; j < MAXV; ++j)
+                if (j < in.nv) {
+                    if ((tp.dmask >> j) & 1u) {
+                        const double2 v = __ldg(reinterpret_cast<const double2*>(tp.p[j]) + p);
+                        v0[j] = v.x;
+                        v1[j] = v.y;
+                    } else {
+                        const typename vec2<R>::T v = __ldg(reinterpret_cast<const typename vec2<R>::T*>(tp.p[j]) + p);
+                        v0[j] = (double)v.x;
+                        v1[j] = (double)v.y;
+                    }
+                }
+#pragma unroll
+            for (int j = 0; j < MAXV; ++j)
+                if (j < in.nv) {
+                    y0 += in.c[j] * v0[j];
+                    y1 += in.c[j] * v1[j];
+                    d0 += cd.d[j] * v0[j];
+                    d1 += cd.d[j] * v1[j];
+                }
+            *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
+        } else {
+#pragma unroll
+            for (int j = 0; j < MAXV; ++j)
+                if (j < in.nv) {
+                    const double v = ((tp.dmask >> j) & 1u) ? __ldg(reinterpret_cast<const double*>(tp.p[j]) + i)
+                                                            : (double)__ldg(reinterpret_cast<const R*>(tp.p[j]) + i);
+                    y0 += in.c[j] * v;
+                    d0 += cd.d[j] * v;
+                }
+            outp[i] = y0;
+        }
         se += d0 * d0 + d1 * d1;
         sc += y0 * y0 + y1 * y1;
         ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
         mx = fmax(mx, fmax(fabs(y0), fabs(y1)));
         if (!isfinite(y0) || !isfinite(y1)) bad = 1.0;
     }
-    se = block_sum(se, red);
-    sc = block_sum(sc, red);
-    ms = block_sum(ms, red);
-    mx = block_max(mx, red);
-    bad = block_max(bad, red);
-    if (threadIdx.x == 0) {
-        double* q = S.fpart + FPW * blk;
-        q[0] = se;
-        q[1] = sc;
-        q[2] = mx;
-        q[3] = bad;
-        q[4] = ms;
+    // one fused warp-level reduction of the five partials, then one pass over the warps
+    for (int o = 16; o > 0; o >>= 1) {
+        se += __shfl_down_sync(0xffffffffu, se, o);
+        sc += __shfl_down_sync(0xffffffffu, sc, o);
+        ms += __shfl_down_sync(0xffffffffu, ms, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        bad = fmax(bad, __shfl_down_sync(0xffffffffu, bad, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        wred[0][warp] = se;
+        wred[1][warp] = sc;
+        wred[2][warp] = mx;
+        wred[3][warp] = bad;
+        wred[4][warp] = ms;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        const int q = threadIdx.x;
+        double v = wred[q][0];
+        for (int w = 1; w < nw; ++w) v = (q == 2 || q == 3) ? fmax(v, wred[q][w]) : v + wred[q][w];
+        S.fpart[FPW * blk + q] = v;
     }
     if (!arrive_last(ctl, S.nfin, &last)) return;
     // The last CTA reduces the per-CTA partials with all its threads (fixed order:
@@ -148,9 +241,9 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     c->arrive = 0;
     c->rhs_evals += 1;  // S(n^k) of the first stage
     if (P.steady) {
-        const double nn = sqrt(c->nrm2);
         c->steady = Q;
-        if (nn > 0.0 && sqrt(Q) / nn < P.steady_rtol) {
+        // ||S|| / ||n|| < rtol  <=>  Q < rtol^2 nrm2 (both sides non-negative)
+        if (c->nrm2 > 0.0 && Q < P.steady_rtol * P.steady_rtol * c->nrm2) {
             c->status = ST_STEADY;
             c->done = 1;
             return;
@@ -159,9 +252,9 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     c->rhs_evals += P.evals - 1;
     c->rhs_paper += P.evals_paper;
     c->attempts += 1;
-    double err = (P.fixed && P.scheme != SCHEME_RKF45) ? 0.0 : sqrt(E);
+    double err = (P.fixed && P.scheme != SCHEME_RKF45) ? 0.0 : sqrt_d(E);
     if (P.rel_norm) {
-        const double nn = sqrt(c->nrm2);
+        const double nn = sqrt_d(c->nrm2);
         if (nn > 0.0) err /= nn;
     }
     c->err_last = err;
@@ -187,6 +280,7 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
         c->nrm2 = C;
         c->ymax = X;
         c->mass = MS;
+        set_xe(c, S, X);
         if (!c->clamped) c->tau = tau_new;
     } else {
         c->rejected += 1;
@@ -209,14 +303,16 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
 // stores nrm2, ymax and mass in the control block and delta_t = sum_{alpha: u=t} coef
 // mu_v (collision-rate coefficients) in aux.
 template <typename R>
-__global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, const int2* __restrict__ map) {
+__global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                               const __grid_constant__ SysDev one) {
     __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
     __shared__ double red[33];
     __shared__ double fin[MAXT + 3];
     __shared__ bool last;
-    const int blk = load_sys(sysv, map, S);
+    const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
-    const double* n = ctl->state[ctl->cur];
+    const double* n = cv.cur ? cv.s1 : cv.s0;
     const R* Wr = reinterpret_cast<const R*>(S.W);
     const int W = S.T + 3;  // mu_t..., n2, max, mass
     double acc[MAXT + 3];
@@ -247,6 +343,7 @@ __global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, 
     ctl->nrm2 = fin[S.T];
     ctl->ymax = fin[S.T + 1];
     ctl->mass = fin[S.T + 2];
+    set_xe(ctl, S, fin[S.T + 1]);
     for (int t = 0; t < S.T; ++t) S.aux[t] = 0.0;
     for (int al = 0; al < S.R; ++al) S.aux[S.au[al]] += S.acoef[al] * fin[S.av[al]];
 }
@@ -256,11 +353,12 @@ __global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, 
 // the caller gave none (ctl->tau <= 0). Then the first attempt's step h is set.
 template <typename R>
 __global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                               double euler_a) {
+                                               const __grid_constant__ SysDev one, double euler_a) {
     __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
     __shared__ double red[33];
     __shared__ bool last;
-    const int blk = load_sys(sysv, map, S);
+    const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
     const R* Wr = reinterpret_cast<const R*>(S.W);
     double mx = -INFINITY;
@@ -285,11 +383,12 @@ __global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, 
 // max_i |n_i| of the caller's vector into ctl->ymax (input scaling of a standalone
 // FP32 evaluation; single system).
 __global__ void __launch_bounds__(128) k_absmax(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                const double* __restrict__ n) {
+                                                const __grid_constant__ SysDev one, const double* __restrict__ n) {
     __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
     __shared__ double red[33];
     __shared__ bool last;
-    const int blk = load_sys(sysv, map, S);
+    const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
     double mx = 0.0;
     for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) mx = fmax(mx, fabs(n[i]));
@@ -302,6 +401,7 @@ __global__ void __launch_bounds__(128) k_absmax(const SysDev* __restrict__ sysv,
     if (threadIdx.x != 0) return;
     ctl->arrive = 0;
     ctl->ymax = m;
+    set_xe(ctl, S, m);
 }
 
 // Keeps the stream busy for about `cycles` SM clocks (a bounded loop on the clock

@@ -58,6 +58,7 @@ struct Ctl {
     double* state[2];           // double-buffered state; state[cur] is n^k
     uint32_t arrive;            // arrival counter of the last-block-done reductions
     int32_t pad;
+    int32_t xe[MAXT];           // FP32 form: input scale exponents of the transforms
 };
 
 // One system, as the kernels see it (device memory; 256-byte aligned array).
@@ -88,7 +89,8 @@ struct SysDev {
     int pu[MAXR], pv[MAXR];  // unordered pairs for the spectral product
     double pcoef[MAXR];
     int wexp[MAXT];          // ilogb(max_i |W_t[i]|)
-    int pad[6];
+    double bnorm;            // 1 / (2 Mp): the 1/Mp of the inverse and the 1/2 of the birth term
+    int pad[4];
 };
 
 // Stage input y = sum_j c_j v_j. slot >= 0: work vector (type R); slot -1 / -2: the
@@ -113,6 +115,16 @@ struct EpiOut {
     double hfac;
 };
 
+// The fields of a system's control block that every kernel reads, fetched once per CTA
+// into shared memory.
+struct CtlView {
+    int done, cur;
+    const double* s0;
+    const double* s1;
+    double h, ymax;
+    int xe[MAXT];
+};
+
 // Resolved term pointers of a stage input: bit j of dmask set = term j is FP64.
 template <typename R>
 struct Terms {
@@ -121,12 +133,11 @@ struct Terms {
 };
 
 template <typename R>
-__device__ __forceinline__ Terms<R> resolve_terms(const StageIn& in, const SysDev& S) {
+__device__ __forceinline__ Terms<R> resolve_terms(const StageIn& in, const SysDev& S, const CtlView& cv) {
     Terms<R> tr;
-    const Ctl* c = S.ctl;
-    const int cur = c->cur;
-    const double* s0 = c->state[0];
-    const double* s1 = c->state[1];
+    const int cur = cv.cur;
+    const double* s0 = cv.s0;
+    const double* s1 = cv.s1;
     tr.dmask = 0u;
 #pragma unroll
     for (int j = 0; j < MAXV; ++j) {
@@ -198,21 +209,71 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
 // Exponent of the input scaling of transform t: FP64 runs unscaled; FP32 divides
 // x_t by 2^(ilogb(max|W_t|) + ilogb(max|y|)) so that its largest entry is near 1.
 template <typename R>
-__device__ __forceinline__ int xexp(const SysDev& S, int t) {
-    if (sizeof(R) == sizeof(double)) return 0;
-    const double ym = S.ctl->ymax;
-    return (ym > 0.0 && isfinite(ym)) ? S.wexp[t] + ilogb(ym) : S.wexp[t];
+__device__ __forceinline__ int xexp(const SysDev& S, const CtlView& cv, int t) {
+    return sizeof(R) == sizeof(double) ? 0 : cv.xe[t];
 }
 
-// Copies the descriptor of this CTA's system into shared memory; returns the block
-// index within the system.
-__device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const int2* __restrict__ map, SysDev& sh) {
-    const int2 m = map[blockIdx.x];
-    const int* src = reinterpret_cast<const int*>(sysv + m.x);
+// Sets the input scale exponents of the FP32 form from max|n| (once per accepted
+// step, by one thread): 2^(ilogb(max|W_t|) + ilogb(max|n|)).
+__device__ __forceinline__ void set_xe(Ctl* c, const SysDev& S, double ymax) {
+    const int ey = (ymax > 0.0 && isfinite(ymax)) ? ilogb(ymax) : 0;
+    for (int t = 0; t < S.T; ++t) c->xe[t] = S.wexp[t] + ey;
+}
+
+// 2^e as R, exactly, without a double-precision ldexp (e within the normal range).
+template <typename R>
+__device__ __forceinline__ R pow2(int e) {
+    if (sizeof(R) == sizeof(float)) {
+        e = max(-126, min(127, e));
+        return (R)__int_as_float((127 + e) << 23);
+    }
+    e = max(-1022, min(1023, e));
+    return (R)__longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// Copies the descriptor of this CTA's system into shared memory and fetches the fields
+// of its control block; returns the block index within the system. A launch over a
+// single system passes map == nullptr and the descriptor itself as a kernel argument
+// (no global round trip); a batch passes the device array and the block map.
+__device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                        const SysDev& one, SysDev& sh, CtlView& cv) {
+    int blk;
+    const int* src;
+    if (map == nullptr) {
+        blk = blockIdx.x;
+        src = reinterpret_cast<const int*>(&one);
+        if (threadIdx.x < MAXT) cv.xe[threadIdx.x] = one.ctl->xe[threadIdx.x];
+        if (threadIdx.x == 0) {
+            const Ctl* c = one.ctl;
+            cv.done = c->done;
+            cv.cur = c->cur;
+            cv.s0 = c->state[0];
+            cv.s1 = c->state[1];
+            cv.h = c->h;
+            cv.ymax = c->ymax;
+        }
+    } else {
+        const int2 m = map[blockIdx.x];
+        blk = m.y;
+        src = reinterpret_cast<const int*>(sysv + m.x);
+    }
     int* dst = reinterpret_cast<int*>(&sh);
     for (int q = threadIdx.x; q < (int)(sizeof(SysDev) / 4); q += blockDim.x) dst[q] = src[q];
     __syncthreads();
-    return m.y;
+    if (map != nullptr) {
+        if (threadIdx.x < MAXT) cv.xe[threadIdx.x] = sh.ctl->xe[threadIdx.x];
+        if (threadIdx.x == 0) {
+            const Ctl* c = sh.ctl;
+            cv.done = c->done;
+            cv.cur = c->cur;
+            cv.s0 = c->state[0];
+            cv.s1 = c->state[1];
+            cv.h = c->h;
+            cv.ymax = c->ymax;
+        }
+        __syncthreads();
+    }
+    return blk;
 }
 
 // ---------------------------------------------------------------------------
@@ -224,12 +285,13 @@ __device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const i
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                  const StageIn in) {
+                                                  const __grid_constant__ SysDev one, const StageIn in) {
     __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
     __shared__ double red[2 * MAXT][8];
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int bx = load_sys(sysv, map, S);
-    if (S.ctl->done) return;
+    const int bx = load_sys(sysv, map, one, S, cv);
+    if (cv.done) return;
     const int G = S.G, T = S.T, GT = G * T, N1 = S.N1;
     const int half = (N1 >> 1) * G;
     const int n2b = bx * G;
@@ -246,7 +308,7 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         const int g = idx % G, k1 = idx / G;
         tw4[idx] = twl(tw, (2u * (uint32_t)(n2b + g) * (uint32_t)k1) & mask2, (uint32_t)S.Mp);
     }
-    const Terms<R> P = resolve_terms<R>(in, S);
+    const Terms<R> P = resolve_terms<R>(in, S, cv);
     R* yb = reinterpret_cast<R*>(S.ybuf);
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
         const int g = idx % G;
@@ -269,7 +331,7 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
     const R* Wall = reinterpret_cast<const R*>(S.W);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = 0; t < T; ++t) {
-        const R sc = (R)ldexp(1.0, -xexp<R>(S, t));
+        const R sc = pow2<R>(-xexp<R>(S, cv, t));
         const R* Wt = Wall + (size_t)t * S.Mp;
         R mu = (R)0, nu = (R)0;
         for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
@@ -344,12 +406,14 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, const int2* __restrict__ map) {
+__global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                              const __grid_constant__ SysDev one) {
     __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
     __shared__ R pc[MAXR];
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int blk = load_sys(sysv, map, S);
-    if (S.ctl->done) return;
+    const int blk = load_sys(sysv, map, one, S, cv);
+    if (cv.done) return;
     const int G = 2 * S.T;
     const int N2 = S.N2;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
@@ -370,13 +434,13 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     }
     if (threadIdx.x < S.npairs) {
         // FP32: pair p carries 2^(e_u + e_v - e_max) so that the sum stays in range.
-        double c = S.pcoef[threadIdx.x];
+        R c = (R)S.pcoef[threadIdx.x];
         if (sizeof(R) == sizeof(float)) {
             int emax = -100000;
-            for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, S.pu[p]) + xexp<R>(S, S.pv[p]));
-            c = ldexp(c, xexp<R>(S, S.pu[threadIdx.x]) + xexp<R>(S, S.pv[threadIdx.x]) - emax);
+            for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, cv, S.pu[p]) + xexp<R>(S, cv, S.pv[p]));
+            c *= pow2<R>(xexp<R>(S, cv, S.pu[threadIdx.x]) + xexp<R>(S, cv, S.pv[threadIdx.x]) - emax);
         }
-        pc[threadIdx.x] = (R)c;
+        pc[threadIdx.x] = c;
     }
     const cx<R>* Yin = reinterpret_cast<const cx<R>*>(S.Y);
     for (int idx = threadIdx.x; idx < N2 * G; idx += blockDim.x) {
@@ -431,15 +495,17 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                  const StageIn in, const EpiOut eo) {
+                                                  const __grid_constant__ SysDev one, const StageIn in,
+                                                  const EpiOut eo) {
     __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
     __shared__ double red[33];
     __shared__ double mom[2 * MAXT];
     __shared__ R delta[MAXT];
     __shared__ double src_s, bscale_s;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int bx = load_sys(sysv, map, S);
-    if (S.ctl->done) return;
+    const int bx = load_sys(sysv, map, one, S, cv);
+    if (cv.done) return;
     const int G = S.G;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
     cx<R>* b = a + (S.N1 * G);
@@ -465,7 +531,7 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     }
     __syncthreads();
     const R* yr = reinterpret_cast<const R*>(S.ybuf);
-    const double* yd = in.direct ? reinterpret_cast<const double*>(resolve_terms<R>(in, S).p[0]) : nullptr;
+    const double* yd = in.direct ? reinterpret_cast<const double*>(resolve_terms<R>(in, S, cv).p[0]) : nullptr;
     __shared__ double s1_s;
     if (threadIdx.x == 0) {
         const double y1 = yd ? yd[0] : __ldcg(S.aux + MAXT);
@@ -497,13 +563,13 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
         int emax = 0;
         if (sizeof(R) == sizeof(float)) {
             emax = -100000;
-            for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, S.pu[p]) + xexp<R>(S, S.pv[p]));
+            for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, cv, S.pu[p]) + xexp<R>(S, cv, S.pv[p]));
         }
-        bscale_s = ldexp(0.5 / (double)S.Mp, emax);
+        bscale_s = S.bnorm * (double)pow2<float>(emax);
     }
     __syncthreads();
     cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, twP);
-    const double hsc = eo.out_slot >= 0 ? S.ctl->h * eo.hfac : 1.0;
+    const double hsc = eo.out_slot >= 0 ? cv.h * eo.hfac : 1.0;
     const R scale = (R)hsc, bscale = (R)bscale_s, lam1 = (R)(1.0 + S.lambda);
     const double src = src_s;
     const int half = (S.N1 >> 1) * G;

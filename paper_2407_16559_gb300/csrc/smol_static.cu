@@ -144,6 +144,7 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     d.T = T;
     d.R = R;
     d.lambda = lambda;
+    d.bnorm = 0.5 / (double)Mp;
     d.nbx = N2 / G;
     d.npairs = R;
     for (int a = 0; a < R; ++a) {
@@ -187,8 +188,10 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     const size_t n = (size_t)N1 * G;
     const size_t sc = 2 * n * T * 16 + (size_t)N1 * 16 + n * 16 + n * 8;  // >= the inverse pass's need
     const size_t sr = 2 * (size_t)N2 * 2 * T * 16 + 5 * (size_t)N2 * 16;
-    k_fwd_cols<double><<<N2 / G, threads_for_s(N1 * G * T), sc, st>>>(dsys, mapC, in);
-    k_rows<double><<<N1 / 2, threads_for_s(N2 * 2 * T), sr, st>>>(dsys, mapB);
-    k_inv_cols<double><<<N2 / G, threads_for_s(N1 * G), sc, st>>>(dsys, mapC, in, eo);
+    SysDev none;
+    memset(&none, 0, sizeof(none));
+    k_fwd_cols<double><<<N2 / G, threads_for_s(N1 * G * T), sc, st>>>(dsys, mapC, none, in);
+    k_rows<double><<<N1 / 2, threads_for_s(N2 * 2 * T), sr, st>>>(dsys, mapB, none);
+    k_inv_cols<double><<<N2 / G, threads_for_s(N1 * G), sc, st>>>(dsys, mapC, none, in, eo);
     return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
 }
