@@ -290,6 +290,11 @@ def gpu_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.only_batch:
+        msb, stb, Ms = time_batch(smol, torch, "fp32conv", K, W, stream, flush, args.batch)
+        if rank == 0:
+            print(json.dumps({"batch_ms_per_step": msb / K, "systems": args.batch, "steps": K}))
+        return 0
     barrier()
     with ClockSampler(local) as clk:
         ms, stats, prof_ms, prof_cnt, tsys, U, V = time_form(smol, torch, precision, K, W, stream, flush, rank)
@@ -355,12 +360,57 @@ def gpu_arm(args):
         line["fp32conv"] = {"value": v32, "ms_per_step": ms32 / K, "speedup_vs_fp64": v32 / value,
                             "kernel_us": {k: round(v * 1000.0, 3) for k, v in pm32.items()},
                             "rhs_rel_err_vs_fp64": rhs_accuracy(smol, torch, U, V)}
+    if args.batch > 0:
+        Kb = max(3, K // 10)
+        msb, stb, Ms = time_batch(smol, torch, "fp32conv", Kb, W, stream, flush, args.batch)
+        att = sum(x["attempts"] for x in stb)
+        acc = sum(x["accepted"] for x in stb)
+        line["batch"] = {"systems": args.batch, "precision": "fp32conv", "steps": Kb, "ms_per_step": msb / Kb,
+                         "rhs_evals_per_s": world * EVALS_PER_STEP * args.batch * Kb / (msb / 1000.0),
+                         "accepted_steps_per_s": world * acc / max(att, 1) * args.batch * Kb / (msb / 1000.0),
+                         "elements": int(sum(Ms)),
+                         "note": "one step = one RKF45 attempt of every system; systems from seed 2407, "
+                                 "M = 2^round(U(10,16)), a ~ U(0.2,0.9), lambda log-uniform [0.005, 0.1]"}
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line))
     return 0
+
+
+def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count: int = 256):
+    """The batched workload: `count` independent systems (M = 2^round(U(10,16)), kernel
+    (i/j)^a + (j/i)^a with a ~ U(0.2, 0.9), lambda log-uniform in [0.005, 0.1],
+    monodisperse starts, seed 2407), each with its own adaptive RKF45 step (tol 1e-8).
+    One step = one attempt of every system (one graph launch whose kernels span all
+    systems). Returns device ms over K steps and the systems' stats."""
+    from synth import batch_recipe, kernel_factors, monodisperse
+    rec = batch_recipe(count)
+    Us, Vs, lams, n0s = [], [], [], []
+    for r in rec:
+        U, V = kernel_factors("brownian", r["M"], a=r["a"])
+        Us.append(U)
+        Vs.append(V)
+        lams.append(r["lam"])
+        n0s.append(torch.from_numpy(monodisperse(r["M"])).cuda())
+    b = smol.Batch(Us, Vs, lams, precision=precision, stream=stream, tau0=1e-3, chunk=1)
+    b.start(n0s, 0.0, 1000.0, 1e-8, scheme="rkf45")
+    for _ in range(W):
+        b.advance()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            b.advance()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in ev)
+    _, stats = b.finish()
+    Ms = [r["M"] for r in rec]
+    return ms, stats, Ms
 
 
 def rhs_accuracy(smol, torch, U, V):
@@ -414,6 +464,8 @@ def main():
     ap.add_argument("--both", action="store_true", default=True)
     ap.add_argument("--no-both", dest="both", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=256, help="systems of the batched workload (0: skip)")
+    ap.add_argument("--only-batch", action="store_true", help="time only the batched workload (profiling aid)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-max-evals", type=int, default=None)
     ap.add_argument("--cpu-worker", action="store_true")

@@ -537,6 +537,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     cudaStream_t st = E->stream;
     std::vector<SysDev> hs(count), hsr(count);
     std::vector<int2> mC, mB, mF;
+    std::vector<std::pair<int, std::vector<double>>> twcache;  // twiddles per FFT size
     for (int q = 0; q < count; ++q) {
         const Shape& s = E->sh[q];
         const Layout& L = E->lay[q];
@@ -657,12 +658,20 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         std::vector<double> hW((size_t)T * s.Mp, 0.0);
         for (int t = 0; t < T; ++t)
             for (int i = 0; i < Mi; ++i) hW[(size_t)t * s.Mp + i] = W[t][i];
-        std::vector<double> tw64(2 * (size_t)s.Mp);
-        for (int e = 0; e < s.Mp; ++e) {
-            const long double th = 3.141592653589793238462643383279502884L * (long double)e / (long double)s.Mp;
-            tw64[2 * e] = (double)cosl(th);
-            tw64[2 * e + 1] = (double)-sinl(th);
+        const std::vector<double>* twp = nullptr;
+        for (auto& c : twcache)
+            if (c.first == s.Mp) twp = &c.second;
+        if (!twp) {
+            std::vector<double> tw64(2 * (size_t)s.Mp);
+            for (int e = 0; e < s.Mp; ++e) {
+                const long double th = 3.141592653589793238462643383279502884L * (long double)e / (long double)s.Mp;
+                tw64[2 * e] = (double)cosl(th);
+                tw64[2 * e + 1] = (double)-sinl(th);
+            }
+            twcache.emplace_back(s.Mp, std::move(tw64));
+            twp = &twcache.back().second;
         }
+        const std::vector<double>& tw64 = *twp;
         std::vector<unsigned char> Wb, twb;
         if (prec == SMOL_FP32CONV) {
             to_type<float>(hW, Wb);

@@ -76,23 +76,26 @@ def test_batch_fp64_vs_oracle(smol):
 def test_batch_recipe_sample_fp32conv(smol):
     """A sample of the 256-system workload (M log-uniform in [2^10, 2^16], exponent in
     [0.2, 0.9], lambda log-uniform in [0.005, 0.1]), FP32 convolutions with FP64 control,
-    against the FP64 oracle after t = 2. The bound is 5e-4 relative, not the 1e-4 of a
-    single evaluation: the FP32 FFT's rounding (1e-7 of the largest values) lands in
-    every size bin, the near-empty tail included, and monomers collide with large
-    clusters at rate K_1j ~ j^a, so that tail noise feeds into n_1 step after step
-    (measured up to 1.2e-4 here; the FP64 solver stays below 1e-9)."""
+    against the FP64 oracle. The bound is 5e-4 relative, not the 1e-4 of a single
+    evaluation: the FP32 FFT's rounding (1e-7 of the largest values) lands in every size
+    bin, the near-empty tail included, and monomers collide with large clusters at rate
+    K_1j ~ j^a, so that tail noise feeds into n_1 step after step (measured up to 1.2e-4
+    after t = 2; the FP64 solver stays below 1e-9). Systems up to M = 8192 run to t = 2,
+    the larger ones to t = 0.3 (the oracle's numpy FFT is slow there)."""
     import torch
     rec = batch_recipe(256)[:8]
-    specs = [(r["M"], r["a"], r["lam"]) for r in rec]
-    Us, Vs, lams, n0s = _systems(specs)
-    b = smol.Batch(Us, Vs, lams, precision="fp32conv", tau0=1e-3)
-    ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 2.0, 1e-8, scheme="rkf45")
-    for q, (U, V, lam, n0) in enumerate(zip(Us, Vs, lams, n0s)):
-        assert sts[q]["status"] == 0 and sts[q]["t"] == 2.0
-        osys = oracle.System(len(n0), lam, U=U, V=V, route="lowrank")
-        m, ost, _ = oracle.integrate(osys, n0, 0.0, 2.0, 1e-8, oracle.Options(scheme="rkf45", tau0=1e-3))
-        x = ns[q].cpu().numpy()
-        assert np.linalg.norm(x - m) <= 5e-4 * np.linalg.norm(m), (q, np.linalg.norm(x - m) / np.linalg.norm(m))
+    for t1, keep in ((2.0, lambda M: M <= 8192), (0.3, lambda M: M > 8192)):
+        specs = [(r["M"], r["a"], r["lam"]) for r in rec if keep(r["M"])]
+        Us, Vs, lams, n0s = _systems(specs)
+        b = smol.Batch(Us, Vs, lams, precision="fp32conv", tau0=1e-3)
+        ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, t1, 1e-8, scheme="rkf45")
+        for q, (U, V, lam, n0) in enumerate(zip(Us, Vs, lams, n0s)):
+            assert sts[q]["status"] == 0 and sts[q]["t"] == t1
+            osys = oracle.System(len(n0), lam, U=U, V=V, route="lowrank")
+            m, ost, _ = oracle.integrate(osys, n0, 0.0, t1, 1e-8, oracle.Options(scheme="rkf45", tau0=1e-3))
+            x = ns[q].cpu().numpy()
+            rel = np.linalg.norm(x - m) / np.linalg.norm(m)
+            assert rel <= 5e-4, (len(n0), t1, rel)
 
 
 @pytest.mark.parametrize("scheme", ["rk2", "rk4"])
