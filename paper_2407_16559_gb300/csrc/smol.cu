@@ -40,7 +40,10 @@ struct Shape {
     size_t csz, rsz;  // bytes of one complex / one real value of the compute type
 };
 
-Shape make_shape(int64_t M, int precision) {
+// `wide`: the system is part of a batch large enough to fill the GPU on its own; its
+// CTAs then take more work each (fewer, fuller CTAs: the per-CTA set-up is amortised and
+// column stores fill whole 32-byte sectors), where a lone system wants many small CTAs.
+Shape make_shape(int64_t M, int precision, bool wide = false) {
     Shape s;
     s.M = (int)M;
     s.lgMp = ilog2(M < 4 ? 4 : M);
@@ -53,9 +56,11 @@ Shape make_shape(int64_t M, int precision) {
     // CTA keeps at least 32 radix-8 butterflies per pass
     int G = 256 / s.N1;
     if (G < 1) G = 1;
+    if (wide && G < 4) G = 4;
     if (G > s.N2) G = s.N2;
     s.G = G;
-    int nf = (s.M / 2 + FIN_THREADS - 1) / FIN_THREADS;
+    const int ppt = wide ? 8 : 1;  // element pairs per thread of the finish kernels
+    int nf = (s.M / 2 + FIN_THREADS * ppt - 1) / (FIN_THREADS * ppt);
     s.nfin = std::max(1, std::min(nf, FIN_MAX_BLOCKS));
     s.csz = precision == SMOL_FP32CONV ? 8 : 16;
     s.rsz = s.csz / 2;
@@ -84,7 +89,8 @@ int threads_for(int points) {
 
 // Per-system part of the workspace.
 struct Layout {
-    size_t tw, W, Y, G2, ybuf, vec, half, stateB, mpart, fpart, sqpart, aux, log_t, log_h, log_e, log_a, total;
+    size_t tw, twc, twr, tws, W, Y, G2, ybuf, vec, half, stateB, mpart, fpart, sqpart, aux, rsc, shadow, log_t, log_h,
+        log_e, log_a, total;
     size_t vstride;  // elements between work vectors
 };
 
@@ -98,6 +104,9 @@ Layout make_layout(const Shape& s, int R, int log_cap) {
         return r;
     };
     L.tw = take((size_t)s.Mp * s.csz);
+    L.twc = take((size_t)s.Mp * s.csz);
+    L.twr = take((size_t)s.Mp * s.csz);
+    L.tws = take((size_t)s.Mp * s.csz);
     L.W = take((size_t)Tm * s.Mp * s.rsz);
     L.Y = take((size_t)Tm * s.Mp * s.csz);
     L.G2 = take((size_t)s.Mp * s.csz);
@@ -106,10 +115,12 @@ Layout make_layout(const Shape& s, int R, int log_cap) {
     L.vec = take((size_t)NVEC * L.vstride * s.rsz);
     L.half = take((size_t)s.Mp * 8);
     L.stateB = take((size_t)s.Mp * 8);
-    L.mpart = take((size_t)Tm * (s.N2 / s.G) * 2 * 8);
+    L.mpart = take((size_t)Tm * s.N2 * 2 * 8);  // sized for G = 1 (G may shrink at init)
     L.fpart = take((size_t)s.nfin * FPW * 8);
-    L.sqpart = take((size_t)(s.N2 / s.G) * 8);
+    L.sqpart = take((size_t)s.N2 * 8);
     L.aux = take((size_t)(MAXT + 1) * 8);
+    L.rsc = take((size_t)(MAXT + 2) * 8);
+    L.shadow = take(2 * align256((size_t)s.Mp * s.rsz));
     L.log_t = take((size_t)log_cap * 8);
     L.log_h = take((size_t)log_cap * 8);
     L.log_e = take((size_t)log_cap * 8);
@@ -129,7 +140,7 @@ Header make_header(const std::vector<Shape>& sh) {
     const size_t n = sh.size();
     H.nC = H.nB = H.nF = 0;
     for (const Shape& s : sh) {
-        H.nC += s.N2 / s.G;
+        H.nC += s.N2;  // room for G = 1; the launch count is set from the final maps
         H.nB += s.N1 / 2;
         H.nF += s.nfin;
     }
@@ -196,14 +207,22 @@ int64_t max_m_for(int32_t R, int32_t precision) {
     return best;
 }
 
+// A batch counts as wide when its systems together hold more than 2^20 sizes.
+bool is_wide(int count, const int64_t* M) {
+    int64_t tot = 0;
+    for (int q = 0; q < count; ++q) tot += M[q];
+    return count > 1 && tot > ((int64_t)1 << 20);
+}
+
 size_t batch_bytes(int count, const int64_t* M, int R, const smol_opts& o) {
     if (count < 1 || count > MAX_BATCH || R < 1 || R > MAXR) return 0;
     const int64_t mm = max_m_for(R, o.precision);
     std::vector<Shape> sh;
     size_t tot = 0;
+    const bool wide = is_wide(count, M);
     for (int q = 0; q < count; ++q) {
         if (M[q] < 1 || M[q] > mm) return 0;
-        sh.push_back(make_shape(M[q], o.precision));
+        sh.push_back(make_shape(M[q], o.precision, wide));
         tot += make_layout(sh.back(), R, std::max(o.log_capacity, 0)).total;
     }
     return make_header(sh).total + tot;
@@ -342,6 +361,12 @@ Comb2 comb2(const StageIn& cand, const StageIn& del) {
     };
     for (int j = 0; j < cand.nv; ++j) add(cand.slot[j], cand.c[j], 0.0);
     for (int j = 0; j < del.nv; ++j) add(del.slot[j], 0.0, del.c[j]);
+    for (int j = 0; j < c.in.nv; ++j) {
+        c.ch[j] = (float)c.in.c[j];
+        c.cl[j] = (float)(c.in.c[j] - (double)c.ch[j]);
+        c.dh[j] = (float)c.d[j];
+        c.dl[j] = (float)(c.d[j] - (double)c.dh[j]);
+    }
     return c;
 }
 
@@ -370,7 +395,10 @@ EpiOut epi_k(int slot, double hfac, int sq) {
 template <typename R>
 void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
     const LaunchArgs A = args_for(E, false);
-    auto Ev = [&](const StageIn& in, int k, double hfac, bool first) {
+    auto Ev = [&](StageIn in, int k, double hfac, bool first) {
+        if (sizeof(R) == sizeof(float))
+            for (int j = 0; j < in.nv; ++j)
+                if (in.slot[j] == SLOT_CUR) in.slot[j] = SLOT_CURF;
         launch_eval<R>(E, A, in, epi_k(k, hfac, (first && P.steady) ? 1 : 0), st, pr);
     };
     auto finish = [&](const StageIn& cand, const StageIn& del) {
@@ -514,8 +542,9 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     E->ws = (char*)d_ws;
     const int prec = o.precision;
     const int logc = std::max(o.log_capacity, 0);
+    const bool wide = is_wide(count, Ms);
     for (int q = 0; q < count; ++q) {
-        E->sh.push_back(make_shape(Ms[q], prec));
+        E->sh.push_back(make_shape(Ms[q], prec, wide));
         E->lay.push_back(make_layout(E->sh.back(), R, logc));
     }
     E->H = make_header(E->sh);
@@ -582,6 +611,8 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         }
         const int T = (int)W.size();
         E->T.push_back(T);
+        Shape& sm = E->sh[q];
+        while (smem_cols(sm, T) > SMEM_LIMIT && sm.G > 1) sm.G /= 2;  // wide shapes may not fit
         if (smem_rows(s, T) > SMEM_LIMIT || smem_cols(s, T) > SMEM_LIMIT) return SMOL_EUNSUPPORTED;
         E->smemC = std::max(E->smemC, smem_cols(s, T));
         E->smemB = std::max(E->smemB, smem_rows(s, T));
@@ -604,6 +635,9 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         d.lambda = lam[q];
         d.W = b + L.W;
         d.tw = b + L.tw;
+        d.twc = b + L.twc;
+        d.twr = b + L.twr;
+        d.tws = b + L.tws;
         d.Y = b + L.Y;
         d.G2 = b + L.G2;
         d.ybuf = b + L.ybuf;
@@ -613,6 +647,11 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         d.fpart = (double*)(b + L.fpart);
         d.sqpart = (double*)(b + L.sqpart);
         d.aux = (double*)(b + L.aux);
+        d.rsc = (double*)(b + L.rsc);
+        if (prec == SMOL_FP32CONV) {
+            d.shadow0 = b + L.shadow;
+            d.shadow1 = b + L.shadow + align256((size_t)s.Mp * s.rsz);
+        }
         d.log_t = (double*)(b + L.log_t);
         d.log_h = (double*)(b + L.log_h);
         d.log_e = (double*)(b + L.log_e);
@@ -672,16 +711,49 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
             twp = &twcache.back().second;
         }
         const std::vector<double>& tw64 = *twp;
-        std::vector<unsigned char> Wb, twb;
+        // four-step and spectral twiddles in the layouts the kernels read contiguously:
+        //   twc[n2][k1] = W_Mp^{n2 k1} = W_{2Mp}^{2 n2 k1 mod 2Mp}, twr[k1][n2] = its conjugate,
+        //   tws[k1][k2] = W_{2Mp}^{k1 + N1 k2}
+        std::vector<double> twc((size_t)2 * s.Mp), twr((size_t)2 * s.Mp), tws((size_t)2 * s.Mp);
+        auto wv = [&](uint64_t e, double* re, double* im) {  // W_{2Mp}^e, any e
+            e %= 2 * (uint64_t)s.Mp;
+            const double sgn = e >= (uint64_t)s.Mp ? -1.0 : 1.0;
+            if (e >= (uint64_t)s.Mp) e -= s.Mp;
+            *re = sgn * tw64[2 * e];
+            *im = sgn * tw64[2 * e + 1];
+        };
+        for (int n2 = 0; n2 < s.N2; ++n2)
+            for (int k1 = 0; k1 < s.N1; ++k1) {
+                double re, im;
+                wv(2 * (uint64_t)n2 * k1, &re, &im);
+                const size_t c = (size_t)n2 * s.N1 + k1, r = (size_t)k1 * s.N2 + n2;
+                twc[2 * c] = re;
+                twc[2 * c + 1] = im;
+                twr[2 * r] = re;
+                twr[2 * r + 1] = -im;
+                wv((uint64_t)k1 + (uint64_t)s.N1 * n2, &re, &im);
+                tws[2 * r] = re;
+                tws[2 * r + 1] = im;
+            }
+        std::vector<unsigned char> Wb, twb, tcb, trb, tsb;
         if (prec == SMOL_FP32CONV) {
             to_type<float>(hW, Wb);
             to_type<float>(tw64, twb);
+            to_type<float>(twc, tcb);
+            to_type<float>(twr, trb);
+            to_type<float>(tws, tsb);
         } else {
             to_type<double>(hW, Wb);
             to_type<double>(tw64, twb);
+            to_type<double>(twc, tcb);
+            to_type<double>(twr, trb);
+            to_type<double>(tws, tsb);
         }
         CK(cudaMemcpyAsync(b + L.W, Wb.data(), Wb.size(), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(b + L.tw, twb.data(), twb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b + L.twc, tcb.data(), tcb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b + L.twr, trb.data(), trb.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b + L.tws, tsb.data(), tsb.size(), cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(b + L.vec, 0, (size_t)NVEC * L.vstride * s.rsz, st));
         CK(cudaMemsetAsync(b + L.ybuf, 0, (size_t)s.Mp * s.rsz, st));
         CK(cudaMemsetAsync(b + L.half, 0, (size_t)s.Mp * 8, st));

@@ -65,6 +65,29 @@ __device__ __forceinline__ cx<R> twl(const cx<R>* __restrict__ tw, uint32_t e, u
     return (e & Mp) ? -w : w;
 }
 
+// Quotient and remainder by a runtime divisor: shifts for powers of two (the usual
+// case: FFT lengths, column groups, T = 1, 2, 4), a division otherwise.
+struct Div {
+    int d, sh;
+    bool p2;
+};
+__device__ __forceinline__ Div mkdiv(int d) {
+    Div r;
+    r.d = d;
+    r.p2 = (d & (d - 1)) == 0;
+    r.sh = __ffs(d) - 1;
+    return r;
+}
+__device__ __forceinline__ void divmod(const Div& D, int x, int& q, int& r) {
+    if (D.p2) {
+        q = x >> D.sh;
+        r = x & (D.d - 1);
+    } else {
+        q = x / D.d;
+        r = x - q * D.d;
+    }
+}
+
 // Length-4 DFT in place (forward: W_4 = -i; INV: +i).
 template <typename R, bool INV>
 __device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3) {
@@ -118,9 +141,10 @@ __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>
     const int q = P >> LGR;
     const int nb = q * G;
     const int sh = lgP - LGR - lgp;  // W_{RAD p}^{e} = W_P^{e << sh}
+    const Div DG = mkdiv(G);
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        const int g = idx % G;
-        const int i = idx / G;
+        int g, i;
+        divmod(DG, idx, i, g);
         const int k = i & (p - 1);
         cx<R> u[RAD];
 #pragma unroll

@@ -88,19 +88,25 @@ __device__ __forceinline__ void set_next_step(Ctl* c) {
     c->h = c->clamped ? c->t1 - c->t : c->tau;
 }
 
-// Last-CTA-done pattern: every CTA of a system writes its partials, then one atomic
-// per CTA; the CTA that arrives last sees all partials and returns true (all threads).
-__device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-        *flag = (prev == (unsigned)nblk - 1);
-    }
-    __syncthreads();
-    if (*flag) __threadfence();
-    return *flag;
+// Double-float (FP32 pair) accumulation of sum c_j k_j over FP32 stage vectors, used by
+// the FP32 form so that its increments and error vectors keep ~2^-44 relative accuracy
+// without the narrow FP64 path. Built on the error-free transformations of Dekker
+// (1971) and Knuth (TAOCP vol. 2): the exact product of two floats as p + e with a fused
+// multiply-add, and the exact sum of two floats as s + t. Coefficients are split on the
+// host into c = ch + cl (both floats).
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_fma(DF& acc, float ch, float cl, float k) {
+    const float p = ch * k;
+    const float e = fmaf(ch, k, -p) + cl * k;  // ch*k - p exactly, plus the low part
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float t = (acc.hi - (s - bb)) + (p - bb);  // acc.hi + p - s exactly
+    acc.hi = s;
+    acc.lo += t + e;
 }
+__device__ __forceinline__ double df_value(const DF& a) { return (double)a.hi + (double)a.lo; }
 
 // Half-step state of step doubling (FP64): half = sum c_j v_j over [0, M).
 template <typename R>
@@ -111,7 +117,7 @@ __global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv
     const int blk = load_sys(sysv, map, one, S, cv);
     if (cv.done) return;
     const int np = (S.M + 1) >> 1;
-    const Terms<R> tr = resolve_terms<R>(in, S, cv);
+    const Terms<R> tr = resolve_terms<R>(in, S, cv, false);
     for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
         double y0, y1;
         stage_pair<double, R>(in, tr, S.M, 2 * p, y0, y1);
@@ -125,6 +131,7 @@ __global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv
 struct Comb2 {
     StageIn in;  // slots and candidate coefficients c_j
     double d[MAXV];
+    float ch[MAXV], cl[MAXV], dh[MAXV], dl[MAXV];  // c and d split into float pairs
 };
 
 // Final kernel of an attempt: candidate = sum c_j v_j (FP64) written to the other state
@@ -148,7 +155,79 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     double se = 0.0, sc = 0.0, mx = 0.0, bad = 0.0, ms = 0.0;
     const int np = (S.M + 1) >> 1;
     const StageIn& in = cd.in;
-    const Terms<R> tp = resolve_terms<R>(in, S, cv);
+    const Terms<R> tp = resolve_terms<R>(in, S, cv, false);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        // FP32 form: the FP32 stage terms are combined in double-float arithmetic, the FP64
+        // terms (state, half-step state) in FP64; FP64 is used only for those terms, the
+        // candidate's final sum and the mass moment. Norms, max and the finite test work
+        // on the FP32 image of the candidate, which also becomes the next state's shadow.
+        float* shad = reinterpret_cast<float*>(cv.cur ? S.shadow0 : S.shadow1);
+        float fse = 0.f, fsc = 0.f, fmx = 0.f;
+        bool fbad = false;
+        for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
+            const int i = 2 * p;
+            const bool two = i + 1 < S.M;
+            DF c0 = {0.f, 0.f}, c1 = {0.f, 0.f}, d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
+            double b0 = 0.0, b1 = 0.0, e0 = 0.0, e1 = 0.0;
+#pragma unroll
+            for (int j = 0; j < MAXV; ++j)
+                if (j < in.nv) {
+                    if ((tp.dmask >> j) & 1u) {
+                        const double* v = reinterpret_cast<const double*>(tp.p[j]);
+                        const double v0 = __ldg(v + i), v1 = two ? __ldg(v + i + 1) : 0.0;
+                        b0 += in.c[j] * v0;
+                        b1 += in.c[j] * v1;
+                        if (cd.d[j] != 0.0) {
+                            e0 += cd.d[j] * v0;
+                            e1 += cd.d[j] * v1;
+                        }
+                    } else {
+                        const float* v = reinterpret_cast<const float*>(tp.p[j]);
+                        float v0, v1;
+                        if (two) {
+                            const float2 w = __ldg(reinterpret_cast<const float2*>(v) + p);
+                            v0 = w.x;
+                            v1 = w.y;
+                        } else {
+                            v0 = __ldg(v + i);
+                            v1 = 0.f;
+                        }
+                        df_fma(c0, cd.ch[j], cd.cl[j], v0);
+                        df_fma(c1, cd.ch[j], cd.cl[j], v1);
+                        df_fma(d0, cd.dh[j], cd.dl[j], v0);
+                        df_fma(d1, cd.dh[j], cd.dl[j], v1);
+                    }
+                }
+            const double y0 = b0 + df_value(c0), y1 = b1 + df_value(c1);
+            // error: the FP64 part only where FP64 terms enter it (step doubling)
+            float q0, q1;
+            if (e0 != 0.0 || e1 != 0.0) {
+                q0 = (float)(e0 + df_value(d0));
+                q1 = (float)(e1 + df_value(d1));
+            } else {
+                q0 = d0.hi + d0.lo;
+                q1 = d1.hi + d1.lo;
+            }
+            fse += q0 * q0 + q1 * q1;
+            const float f0 = (float)y0, f1 = (float)y1;
+            if (two) {
+                *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
+                *reinterpret_cast<float2*>(shad + i) = make_float2(f0, f1);
+                ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
+            } else {
+                outp[i] = y0;
+                shad[i] = f0;
+                ms += (double)(i + 1) * y0;
+            }
+            fsc += f0 * f0 + f1 * f1;
+            fmx = fmaxf(fmx, fmaxf(fabsf(f0), fabsf(f1)));
+            fbad = fbad || !isfinite(f0) || !isfinite(f1);
+        }
+        se = (double)fse;
+        sc = (double)fsc;
+        mx = (double)fmx;
+        bad = fbad ? 1.0 : 0.0;
+    } else {
     for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
         const int i = 2 * p;
         double y0 = 0.0, y1 = 0.0, d0 = 0.0, d1 = 0.0;
@@ -192,6 +271,7 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
         ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
         mx = fmax(mx, fmax(fabs(y0), fabs(y1)));
         if (!isfinite(y0) || !isfinite(y1)) bad = 1.0;
+    }
     }
     // one fused warp-level reduction of the five partials, then one pass over the warps
     for (int o = 16; o > 0; o >>= 1) {
@@ -317,8 +397,10 @@ __global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, 
     const int W = S.T + 3;  // mu_t..., n2, max, mass
     double acc[MAXT + 3];
     for (int q = 0; q < W; ++q) acc[q] = 0.0;
+    R* shad = S.shadow0 ? reinterpret_cast<R*>(cv.cur ? S.shadow1 : S.shadow0) : nullptr;
     for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) {
         const double y = n[i];
+        if (shad) shad[i] = (R)y;
         for (int t = 0; t < S.T; ++t) acc[t] += (double)Wr[(size_t)t * S.Mp + i] * y;
         acc[S.T] += y * y;
         acc[S.T + 1] = fmax(acc[S.T + 1], fabs(y));

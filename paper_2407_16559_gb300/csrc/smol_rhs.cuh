@@ -67,6 +67,9 @@ struct SysDev {
     double lambda;
     const void* W;   // R-typed T x Mp weights (zero beyond M)
     const void* tw;  // cx<R> twiddles W_{2Mp}^e, e < Mp
+    const void* twc; // cx<R> four-step twiddles W_Mp^{n2 k1} as [n2][k1] (column kernels)
+    const void* twr; // cx<R> their conjugates as [k1][n2] (row kernel, inverse)
+    const void* tws; // cx<R> spectral twiddles W_{2Mp}^{k1 + N1 k2} as [k1][k2] (row kernel)
     void* Y;         // cx<R> T x Mp spectra after the column pass, [t][k1][n2]
     void* G2;        // cx<R> Mp values after the row pass, [k1][n2]
     void* ybuf;      // R-typed stage input y of the current evaluation (Mp)
@@ -77,6 +80,10 @@ struct SysDev {
     double* sqpart;  // ||S||^2 partials [bx]
     double* aux;     // MAXT + 1 doubles: collision-rate coefficients of the preparation;
                      // aux[MAXT] = y_1 of the current evaluation in FP64
+    double* rsc;     // RHS scalars of the current evaluation: death coefficients delta_t
+                     // [0, MAXT), monomer source [MAXT], S_1 [MAXT + 1]
+    void* shadow0;   // FP32 form: R-typed copies of the two state buffers (stage inputs)
+    void* shadow1;
     double* log_t;   // step log ring (log_cap entries each, shared capacity)
     double* log_h;
     double* log_e;
@@ -96,7 +103,10 @@ struct SysDev {
 // Stage input y = sum_j c_j v_j. slot >= 0: work vector (type R); slot -1 / -2: the
 // current / other state buffer; -3: the caller's vector `ext` (single system); -4: the
 // half-step state. Slots < 0 are FP64 vectors.
-enum { SLOT_CUR = -1, SLOT_OTHER = -2, SLOT_EXT = -3, SLOT_HALF = -4 };
+enum { SLOT_CUR = -1, SLOT_OTHER = -2, SLOT_EXT = -3, SLOT_HALF = -4, SLOT_CURF = -5 };
+// SLOT_CURF: the current state's R-typed shadow (FP32 form), read by stage inputs of
+// the right-hand side; resolves to the FP64 state where no shadow exists or where the
+// FP64 value is needed.
 struct StageIn {
     int nv, direct;  // direct: y is the single FP64 term itself (c == 1)
     int slot[MAXV];
@@ -133,7 +143,8 @@ struct Terms {
 };
 
 template <typename R>
-__device__ __forceinline__ Terms<R> resolve_terms(const StageIn& in, const SysDev& S, const CtlView& cv) {
+__device__ __forceinline__ Terms<R> resolve_terms(const StageIn& in, const SysDev& S, const CtlView& cv,
+                                                  bool shadow_ok = true) {
     Terms<R> tr;
     const int cur = cv.cur;
     const double* s0 = cv.s0;
@@ -141,7 +152,14 @@ __device__ __forceinline__ Terms<R> resolve_terms(const StageIn& in, const SysDe
     tr.dmask = 0u;
 #pragma unroll
     for (int j = 0; j < MAXV; ++j) {
-        const int sl = in.slot[j];
+        int sl = in.slot[j];
+        if (sl == SLOT_CURF) {
+            if (shadow_ok && S.shadow0) {
+                tr.p[j] = cur ? S.shadow1 : S.shadow0;
+                continue;
+            }
+            sl = SLOT_CUR;
+        }
         if (sl >= 0) {
             tr.p[j] = reinterpret_cast<const R*>(S.vec) + (int64_t)sl * S.vstride;
         } else {
@@ -231,6 +249,65 @@ __device__ __forceinline__ R pow2(int e) {
     return (R)__longlong_as_double((long long)(1023 + e) << 52);
 }
 
+// Last-CTA-done pattern: every CTA of a system writes its partials, then one atomic
+// per CTA; the CTA that arrives last sees all partials and returns true (all threads).
+__device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
+        *flag = (prev == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (*flag) __threadfence();
+    return *flag;
+}
+
+// Scalars of one evaluation from the column-pass moment partials (one CTA, after all
+// partials are written): mu_t, nu_t summed over the columns in a fixed order, then
+//   delta_t = sum_{alpha: u=t} coef_alpha mu_{v(alpha)}   (death: D_s = sum_t delta_t W_t[s])
+//   source  = lambda/2 sum coef (rho_u sigma_v + sigma_u rho_v) + lambda y_1 sum coef W_u[1] rho_v
+//   S_1     = -y_1 D_1 + source  (FP64: its two terms nearly cancel)
+// with sigma_t = mu_t - W_t[1] y_1, rho_t = nu_t - W_t[1] y_1.
+template <typename R>
+__device__ void finalize_scalars(const SysDev& S, double y1, double* mom) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int q = warp; q < 2 * S.T; q += nw) {
+        const int t = q >> 1, which = q & 1;
+        double v = 0.0;
+        for (int c = lane; c < S.nbx; c += 32) v += __ldcg(S.mpart + 2 * ((size_t)t * S.nbx + c) + which);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) mom[q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const R* Wr = reinterpret_cast<const R*>(S.W);
+    double sig[MAXT], rho[MAXT], del[MAXT], w1s[MAXT];
+    for (int t = 0; t < S.T; ++t) {
+        const double w1 = (double)Wr[(size_t)t * S.Mp];
+        w1s[t] = w1;
+        sig[t] = mom[2 * t] - w1 * y1;
+        rho[t] = mom[2 * t + 1] - w1 * y1;
+        del[t] = 0.0;
+    }
+    double shat = 0.0, mono = 0.0;
+    for (int al = 0; al < S.R; ++al) {
+        const int u = S.au[al], v = S.av[al];
+        const double c = S.acoef[al];
+        del[u] += c * mom[2 * v];
+        shat += c * (rho[u] * sig[v] + sig[u] * rho[v]);
+        mono += c * w1s[u] * rho[v];
+    }
+    double D1 = 0.0;
+    for (int t = 0; t < S.T; ++t) {
+        S.rsc[t] = del[t];
+        D1 += del[t] * w1s[t];
+    }
+    const double src = 0.5 * S.lambda * shat + S.lambda * y1 * mono;
+    S.rsc[MAXT] = src;
+    S.rsc[MAXT + 1] = -y1 * D1 + src;
+}
+
 // Copies the descriptor of this CTA's system into shared memory and fetches the fields
 // of its control block; returns the block index within the system. A launch over a
 // single system passes map == nullptr and the descriptor itself as a kernel argument
@@ -289,6 +366,7 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ double red[2 * MAXT][8];
+    __shared__ bool lastc;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_sys(sysv, map, one, S, cv);
     if (cv.done) return;
@@ -304,15 +382,19 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
     const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
     // twiddle tables first: their loads overlap the stage-input loads below
     stage_tw(twP, S.lgN1, tw, S.lgMp);
-    for (int idx = threadIdx.x; idx < N1 * G; idx += blockDim.x) {
-        const int g = idx % G, k1 = idx / G;
-        tw4[idx] = twl(tw, (2u * (uint32_t)(n2b + g) * (uint32_t)k1) & mask2, (uint32_t)S.Mp);
+    {
+        const cx<R>* twc = reinterpret_cast<const cx<R>*>(S.twc);
+        for (int idx = threadIdx.x; idx < N1 * G; idx += blockDim.x) {
+            const int k1 = idx & (N1 - 1), g = idx >> S.lgN1;  // contiguous reads along k1
+            tw4[k1 * G + g] = ldg(twc + (size_t)(n2b + g) * N1 + k1);
+        }
     }
     const Terms<R> P = resolve_terms<R>(in, S, cv);
     R* yb = reinterpret_cast<R*>(S.ybuf);
+    const Div DG = mkdiv(G);
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-        const int g = idx % G;
-        const int n1 = idx / G;
+        int g, n1;
+        divmod(DG, idx, n1, g);
         const int i = 2 * ((n1 << S.lgN2) + n2b + g);
         R y0, y1;
         stage_pair<R, R>(in, P, S.M, i, y0, y1);
@@ -321,9 +403,11 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         if (!in.direct) *reinterpret_cast<typename vec2<R>::T*>(yb + i) = {y0, y1};
     }
     if (bx == 0 && threadIdx.x == 0 && !in.direct) {
-        // y_1 in FP64 for the monomer equation, whose two large terms nearly cancel
+        // y_1 in FP64 (from the FP64 state, not its shadow) for the monomer equation,
+        // whose two large terms nearly cancel
+        const Terms<R> P64 = resolve_terms<R>(in, S, cv, false);
         double z0, z1;
-        stage_pair<double, R>(in, P, S.M, 0, z0, z1);
+        stage_pair<double, R>(in, P64, S.M, 0, z0, z1);
         S.aux[MAXT] = z0;
     }
     for (int q = half * T + threadIdx.x; q < N1 * GT; q += blockDim.x) a[q] = mk<R>((R)0, (R)0);
@@ -335,8 +419,8 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         const R* Wt = Wall + (size_t)t * S.Mp;
         R mu = (R)0, nu = (R)0;
         for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-            const int g = idx % G;
-            const int n1 = idx / G;
+            int g, n1;
+            divmod(DG, idx, n1, g);
             const int i = 2 * ((n1 << S.lgN2) + n2b + g);
             const typename vec2<R>::T w = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wt + i));
             const R x0 = w.x * ys[2 * idx], x1 = w.y * ys[2 * idx + 1];
@@ -344,14 +428,14 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
             nu += (R)(i + 1) * x0 + (R)(i + 2) * x1;
             a[n1 * GT + t * G + g] = mk<R>(x0 * sc, x1 * sc);
         }
-        double m0 = (double)mu, m1 = (double)nu;
+        // warp sums in the compute type (FP32 in the FP32 form), then FP64 across warps
         for (int o = 16; o > 0; o >>= 1) {
-            m0 += __shfl_down_sync(0xffffffffu, m0, o);
-            m1 += __shfl_down_sync(0xffffffffu, m1, o);
+            mu += __shfl_down_sync(0xffffffffu, mu, o);
+            nu += __shfl_down_sync(0xffffffffu, nu, o);
         }
         if (lane == 0) {
-            red[2 * t][warp] = m0;
-            red[2 * t + 1][warp] = m1;
+            red[2 * t][warp] = (double)mu;
+            red[2 * t + 1][warp] = (double)nu;
         }
     }
     __syncthreads();
@@ -362,11 +446,20 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         const int t = threadIdx.x >> 1;
         S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
     }
+    // the last column CTA of the system turns the partials into the evaluation's scalars
+    if (arrive_last(S.ctl, S.nbx, &lastc)) {
+        const double y1 = in.direct ? __ldg(reinterpret_cast<const double*>(P.p[0])) : __ldcg(S.aux + MAXT);
+        finalize_scalars<R>(S, y1, &red[0][0]);
+        if (threadIdx.x == 0) S.ctl->arrive = 0;
+        __syncthreads();
+    }
     cx<R>* res = tile_fft<R, false>(a, b, S.lgN1, GT, twP);
     cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
+    const Div DGT = mkdiv(GT);
     for (int idx = threadIdx.x; idx < N1 * GT; idx += blockDim.x) {
-        const int c = idx % GT, k1 = idx / GT;
-        const int t = c / G, g = c % G;
+        int c, k1, t, g;
+        divmod(DGT, idx, k1, c);
+        divmod(DG, c, t, g);
         Yall[(size_t)t * S.Mp + (size_t)k1 * S.N2 + n2b + g] = res[idx] * tw4[k1 * G + g];
     }
 }
@@ -427,10 +520,10 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
     stage_tw(twP, S.lgN2, tw, S.lgMp);
     for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
-        const int rho = idx / N2, k2 = idx % N2;
+        const int rho = idx >> S.lgN2, k2 = idx & (N2 - 1);
         const uint32_t r = (uint32_t)(rho ? r1 : r0);
-        tws[idx] = ldg(tw + (r + (uint32_t)S.N1 * (uint32_t)k2));
-        twi[idx] = conj(twl(tw, (2u * (uint32_t)k2 * r) & mask2, (uint32_t)S.Mp));
+        tws[idx] = ldg(reinterpret_cast<const cx<R>*>(S.tws) + (size_t)r * N2 + k2);
+        twi[idx] = ldg(reinterpret_cast<const cx<R>*>(S.twr) + (size_t)r * N2 + k2);
     }
     if (threadIdx.x < S.npairs) {
         // FP32: pair p carries 2^(e_u + e_v - e_max) so that the sum stays in range.
@@ -444,8 +537,8 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     }
     const cx<R>* Yin = reinterpret_cast<const cx<R>*>(S.Y);
     for (int idx = threadIdx.x; idx < N2 * G; idx += blockDim.x) {
-        const int k2 = idx % N2;  // consecutive threads read consecutive k2 (coalesced)
-        const int col = idx / N2;
+        const int k2 = idx & (N2 - 1);  // consecutive threads read consecutive k2 (coalesced)
+        const int col = idx >> S.lgN2;
         const int t = col >> 1, rho = col & 1;
         const int r = rho ? r1 : r0;
         a[k2 * G + col] = Yin[(size_t)t * S.Mp + (size_t)r * N2 + k2];
@@ -481,8 +574,8 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     cx<R>* res = tile_fft<R, true>(Yo, Z, S.lgN2, 2, twP);
     cx<R>* G2 = reinterpret_cast<cx<R>*>(S.G2);
     for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
-        const int n2 = idx % N2;
-        const int rho = idx / N2;
+        const int n2 = idx & (N2 - 1);
+        const int rho = idx >> S.lgN2;
         const int r = rho ? r1 : r0;
         G2[(size_t)r * N2 + n2] = res[n2 * 2 + rho] * twi[idx];
     }
@@ -500,9 +593,8 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ double red[33];
-    __shared__ double mom[2 * MAXT];
     __shared__ R delta[MAXT];
-    __shared__ double src_s, bscale_s;
+    __shared__ double src_s, bscale_s, s1_s;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_sys(sysv, map, one, S, cv);
     if (cv.done) return;
@@ -513,53 +605,18 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     const int n2b = bx * G;
     stage_tw(twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
     const cx<R>* G2 = reinterpret_cast<const cx<R>*>(S.G2);
+    const Div DG = mkdiv(G);
     for (int idx = threadIdx.x; idx < S.N1 * G; idx += blockDim.x) {
-        const int g = idx % G;
-        const int k1 = idx / G;
+        int g, k1;
+        divmod(DG, idx, k1, g);
         a[idx] = G2[(size_t)k1 * S.N2 + n2b + g];
     }
-    // Moments mu_t, nu_t from the column-pass partials: one warp per quantity, fixed order.
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int q = warp; q < 2 * S.T; q += nw) {
-            const int t = q >> 1, which = q & 1;
-            double s = 0.0;
-            for (int c = lane; c < S.nbx; c += 32) s += S.mpart[2 * ((size_t)t * S.nbx + c) + which];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) mom[q] = s;
-        }
-    }
-    __syncthreads();
     const R* yr = reinterpret_cast<const R*>(S.ybuf);
     const double* yd = in.direct ? reinterpret_cast<const double*>(resolve_terms<R>(in, S, cv).p[0]) : nullptr;
-    __shared__ double s1_s;
+    if (threadIdx.x < S.T) delta[threadIdx.x] = (R)__ldcg(S.rsc + threadIdx.x);
     if (threadIdx.x == 0) {
-        const double y1 = yd ? yd[0] : __ldcg(S.aux + MAXT);
-        const R* Wr = reinterpret_cast<const R*>(S.W);
-        double sig[MAXT], rho[MAXT], del[MAXT], w1s[MAXT];
-        for (int t = 0; t < S.T; ++t) {
-            const double w1 = (double)Wr[(size_t)t * S.Mp];
-            w1s[t] = w1;
-            sig[t] = mom[2 * t] - w1 * y1;      // sum_{i>=2} W_t[i] y_i
-            rho[t] = mom[2 * t + 1] - w1 * y1;  // sum_{i>=2} i W_t[i] y_i
-            del[t] = 0.0;
-        }
-        double shat = 0.0, mono = 0.0;
-        for (int al = 0; al < S.R; ++al) {
-            const int u = S.au[al], v = S.av[al];
-            const double c = S.acoef[al];
-            del[u] += c * mom[2 * v];
-            shat += c * (rho[u] * sig[v] + sig[u] * rho[v]);
-            mono += c * w1s[u] * rho[v];
-        }
-        double D1 = 0.0;
-        for (int t = 0; t < S.T; ++t) {
-            delta[t] = (R)del[t];
-            D1 += del[t] * w1s[t];
-        }
-        src_s = 0.5 * S.lambda * shat + S.lambda * y1 * mono;
-        // S_1 = -y_1 D_1 + source, in FP64 whatever R is
-        s1_s = -y1 * D1 + src_s;
+        src_s = __ldcg(S.rsc + MAXT);
+        s1_s = __ldcg(S.rsc + MAXT + 1);
         int emax = 0;
         if (sizeof(R) == sizeof(float)) {
             emax = -100000;
@@ -577,8 +634,8 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
     double sq = 0.0;
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-        const int g = idx % G;
-        const int n1 = idx / G;
+        int g, n1;
+        divmod(DG, idx, n1, g);
         const int i = 2 * ((n1 << S.lgN2) + n2b + g);
         if (i >= S.M) continue;
         const cx<R> z = res[idx];

@@ -29,7 +29,10 @@ constexpr size_t al(size_t x) { return (x + A256 - 1) / A256 * A256; }
 // Layout of the scratch array (byte offsets); sized for M = SMAX_M, T = 2 SMAX_R.
 constexpr size_t OFF_CTL = 0;
 constexpr size_t OFF_TW = OFF_CTL + al(sizeof(Ctl));
-constexpr size_t OFF_W = OFF_TW + al((size_t)SMAX_M * 16);
+constexpr size_t OFF_TWC = OFF_TW + al((size_t)SMAX_M * 16);
+constexpr size_t OFF_TWR = OFF_TWC + al((size_t)SMAX_M * 16);
+constexpr size_t OFF_TWS = OFF_TWR + al((size_t)SMAX_M * 16);
+constexpr size_t OFF_W = OFF_TWS + al((size_t)SMAX_M * 16);
 constexpr size_t OFF_Y = OFF_W + al((size_t)SMAX_T * SMAX_M * 8);
 constexpr size_t OFF_G2 = OFF_Y + al((size_t)SMAX_T * SMAX_M * 16);
 constexpr size_t OFF_YBUF = OFF_G2 + al((size_t)SMAX_M * 16);
@@ -37,10 +40,11 @@ constexpr size_t OFF_MPART = OFF_YBUF + al((size_t)SMAX_M * 8);
 constexpr size_t OFF_SYS = OFF_MPART + al((size_t)SMAX_T * 1024 * 2 * 8);
 constexpr size_t OFF_MAPC = OFF_SYS + al(sizeof(SysDev));
 constexpr size_t OFF_MAPB = OFF_MAPC + al((size_t)1024 * sizeof(int2));
-constexpr size_t SCRATCH_BYTES = OFF_MAPB + al((size_t)1024 * sizeof(int2));
+constexpr size_t OFF_RSC = OFF_MAPB + al((size_t)1024 * sizeof(int2));
+constexpr size_t SCRATCH_BYTES = OFF_RSC + al((size_t)(MAXT + 2) * 8);
 
 // The scratch memory of smol_rhs_static.
-static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 12,174,336 bytes
+static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 15,320,320 bytes
 
 constexpr int MAX_DEVICES = 64;
 unsigned char* g_scratch_ptr[MAX_DEVICES];  // device address of g_scratch per device
@@ -58,12 +62,22 @@ __global__ void k_static_weights(const double* __restrict__ U, const double* __r
     }
 }
 
-// Twiddles exp(-i pi e / Mp), e < Mp.
-__global__ void k_static_twiddles(int Mp, double2* tw) {
+// Twiddles exp(-i pi e / Mp), e < Mp, and the four-step / spectral tables in the
+// layouts the kernels read: twc[n2][k1] = W_Mp^{n2 k1}, twr[k1][n2] = its conjugate,
+// tws[k1][k2] = W_{2Mp}^{k1 + N1 k2}.
+__global__ void k_static_twiddles(int Mp, int N1, int N2, double2* tw, double2* twc, double2* twr, double2* tws) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Mp; e += gridDim.x * blockDim.x) {
         double s, c;
         sincospi((double)e / (double)Mp, &s, &c);
         tw[e] = make_double2(c, -s);
+        const int n2 = e / N1, k1 = e % N1;
+        const long long f = (2LL * n2 * k1) % (2LL * Mp);
+        sincospi((double)f / (double)Mp, &s, &c);
+        twc[e] = make_double2(c, -s);
+        twr[(size_t)k1 * N2 + n2] = make_double2(c, s);
+        const int r = e / N2, k2 = e % N2;
+        sincospi((double)(r + (long long)N1 * k2) / (double)Mp, &s, &c);
+        tws[e] = make_double2(c, -s);
     }
 }
 
@@ -157,10 +171,14 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     }
     d.W = base + OFF_W;
     d.tw = base + OFF_TW;
+    d.twc = base + OFF_TWC;
+    d.twr = base + OFF_TWR;
+    d.tws = base + OFF_TWS;
     d.Y = base + OFF_Y;
     d.G2 = base + OFF_G2;
     d.ybuf = base + OFF_YBUF;
     d.mpart = (double*)(base + OFF_MPART);
+    d.rsc = (double*)(base + OFF_RSC);
     d.ctl = (Ctl*)(base + OFF_CTL);
     SysDev* dsys = (SysDev*)(base + OFF_SYS);
     int2* mapC = (int2*)(base + OFF_MAPC);
@@ -171,7 +189,8 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     if (cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st) != cudaSuccess) return SMOL_ECUDA;
     k_static_setup<<<1, 256, 0, st>>>(d, dsys, mapC, N2 / G, mapB, N1 / 2);
     k_static_weights<<<256, 256, 0, st>>>(d_U, d_V, (int)M, Mp, R, (double*)(base + OFF_W));
-    k_static_twiddles<<<64, 256, 0, st>>>(Mp, (double2*)(base + OFF_TW));
+    k_static_twiddles<<<64, 256, 0, st>>>(Mp, N1, N2, (double2*)(base + OFF_TW), (double2*)(base + OFF_TWC),
+                                          (double2*)(base + OFF_TWR), (double2*)(base + OFF_TWS));
 
     StageIn in;
     memset(&in, 0, sizeof(in));
