@@ -74,13 +74,15 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # Algorithmic work per launch of each kernel class (FP64 flops / compulsory bytes)
 # ---------------------------------------------------------------------------
-def algorithmic(M: int, T: int, csz: int):
+def algorithmic(M: int, T: int, csz: int, lgn1: int = 0):
     """Per launch: flops of the FFT stages a kernel performs (5 N log2 N convention for
     a complex length-N transform, the real-FFT split / merge counted as one stage) and
-    the bytes it must move (inputs read once, outputs written once)."""
+    the bytes it must move (inputs read once, outputs written once). lgn1: log2 of the
+    column length N1 of the four-step split (0: the rule, ceil(log2 Mp / 2))."""
     lg = (M - 1).bit_length()
     Mp = 1 << lg
-    lg1, lg2 = (lg + 1) // 2, lg // 2
+    lg1 = lgn1 if lgn1 > 0 else (lg + 1) // 2
+    lg2 = lg - lg1
     fl = {
         "fwd_cols": T * 5.0 * Mp * lg1,
         "rows": (T + 1) * 5.0 * Mp * (lg2 + 1),
@@ -235,7 +237,7 @@ def config_dict(precision: str):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: int):
+def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: int, tune: bool = True):
     import numpy as np
 
     from synth import kernel_factors, monodisperse
@@ -245,8 +247,14 @@ def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: 
     sysm = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=1e-3, max_attempts=20000)
     n = torch.from_numpy(monodisperse(w["M"])).cuda()
     n, st0 = sysm.integrate(n, 0.0, w["t_setup"], w["tol"], scheme="rkf45")
+    # FFT schedule and launch mode: timed candidates from this state (untimed set-up)
+    sched = {}
+    if tune:
+        sched, tune_us = smol.tune(U, V, w["lam"], n, w["tol"], precision=precision, attempts=64, stream=stream)
+        sched = dict(sched, tuned_us_per_attempt=round(tune_us, 1))
+    opts = {k: v for k, v in sched.items() if k in smol.SCHEDULE_KEYS}
     # timed run: chunk of one attempt per graph launch
-    tsys = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=st0["tau_next"], chunk=1)
+    tsys = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=st0["tau_next"], chunk=1, **opts)
     run = tsys.start(n, st0["t"], w["t1"], w["tol"], scheme="rkf45")
     for _ in range(W):
         tsys.advance()
@@ -263,7 +271,7 @@ def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: 
     prof_ms, prof_cnt = tsys.profile(reps=10)
     run, stats = tsys.finish()
     del run
-    return ms, stats, prof_ms, prof_cnt, tsys, U, V
+    return ms, stats, prof_ms, prof_cnt, tsys, U, V, sched
 
 
 def gpu_arm(args):
@@ -291,13 +299,15 @@ def gpu_arm(args):
         torch.cuda.synchronize()
 
     if args.only_batch:
-        msb, stb, Ms = time_batch(smol, torch, "fp32conv", K, W, stream, flush, args.batch)
+        msb, stb, Ms, _ = time_batch(smol, torch, "fp32conv", K, W, stream, flush, args.batch,
+                                     tune=not args.no_tune)
         if rank == 0:
             print(json.dumps({"batch_ms_per_step": msb / K, "systems": args.batch, "steps": K}))
         return 0
     barrier()
     with ClockSampler(local) as clk:
-        ms, stats, prof_ms, prof_cnt, tsys, U, V = time_form(smol, torch, precision, K, W, stream, flush, rank)
+        ms, stats, prof_ms, prof_cnt, tsys, U, V, sched = time_form(smol, torch, precision, K, W, stream, flush, rank,
+                                                                    tune=not args.no_tune)
     barrier()
     clocks = clk.summary()
     if dist is not None:
@@ -312,12 +322,13 @@ def gpu_arm(args):
     accepted_per_s = world * acc_rate * K / (ms / 1000.0)
 
     # e2e: public API with host buffers, per step H2D state -> one attempt -> D2H state + stats
-    e2e = e2e_leg(smol, torch, precision, max(10, min(K, 400)), U, V, stream)
+    sopts = {k: v for k, v in sched.items() if k in smol.SCHEDULE_KEYS}
+    e2e = e2e_leg(smol, torch, precision, max(10, min(K, 400)), U, V, stream, sopts)
 
     # roofline of the dominant kernel class
     Tn = tsys.num_transforms
     csz = 8 if precision == "fp32conv" else 16
-    fl, by = algorithmic(WORKLOAD["M"], Tn, csz)
+    fl, by = algorithmic(WORKLOAD["M"], Tn, csz, sched.get("fft_lgn1", 0))
     per_step = {k: prof_ms[k] * prof_cnt[k] / 10 for k in prof_ms}
     dom = max(("fwd_cols", "rows", "inv_cols"), key=lambda k: per_step[k])
     peaks, pk_src = measured_peaks()
@@ -348,27 +359,30 @@ def gpu_arm(args):
         "metric": "rhs_evals_per_s", "value": value, "unit": "RHS evals/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": dict(config_dict(precision), parallelism=f"replicas{world}"),
+        "config": dict(config_dict(precision), parallelism=f"replicas{world}",
+                       schedule=sched or "rule (untuned)"),
         "accepted_steps_per_s": accepted_per_s,
         "attempts": {"accepted": stats["accepted"], "rejected": stats["rejected"], "t_end": stats["t"]},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * K,
         "clocks": clocks,
     }
     if args.both and precision == "fp64":
-        ms32, st32, pm32, pc32, tsys32, _, _ = time_form(smol, torch, "fp32conv", K, W, stream, flush, rank)
+        ms32, st32, pm32, pc32, tsys32, _, _, sch32 = time_form(smol, torch, "fp32conv", K, W, stream, flush, rank,
+                                                                tune=not args.no_tune)
         v32 = world * EVALS_PER_STEP * K / (ms32 / 1000.0)
         line["fp32conv"] = {"value": v32, "ms_per_step": ms32 / K, "speedup_vs_fp64": v32 / value,
-                            "kernel_us": {k: round(v * 1000.0, 3) for k, v in pm32.items()},
+                            "kernel_us": {k: round(v * 1000.0, 3) for k, v in pm32.items()}, "schedule": sch32,
                             "rhs_rel_err_vs_fp64": rhs_accuracy(smol, torch, U, V)}
     if args.batch > 0:
         Kb = max(3, K // 10)
-        msb, stb, Ms = time_batch(smol, torch, "fp32conv", Kb, W, stream, flush, args.batch)
+        msb, stb, Ms, bflags = time_batch(smol, torch, "fp32conv", Kb, W, stream, flush, args.batch,
+                                          tune=not args.no_tune)
         att = sum(x["attempts"] for x in stb)
         acc = sum(x["accepted"] for x in stb)
         line["batch"] = {"systems": args.batch, "precision": "fp32conv", "steps": Kb, "ms_per_step": msb / Kb,
                          "rhs_evals_per_s": world * EVALS_PER_STEP * args.batch * Kb / (msb / 1000.0),
                          "accepted_steps_per_s": world * acc / max(att, 1) * args.batch * Kb / (msb / 1000.0),
-                         "elements": int(sum(Ms)),
+                         "elements": int(sum(Ms)), "launch_flags": bflags,
                          "note": "one step = one RKF45 attempt of every system; systems from seed 2407, "
                                  "M = 2^round(U(10,16)), a ~ U(0.2,0.9), lambda log-uniform [0.005, 0.1]"}
     if dist is not None:
@@ -379,7 +393,7 @@ def gpu_arm(args):
     return 0
 
 
-def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count: int = 256):
+def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count: int = 256, tune: bool = True):
     """The batched workload: `count` independent systems (M = 2^round(U(10,16)), kernel
     (i/j)^a + (j/i)^a with a ~ U(0.2, 0.9), lambda log-uniform in [0.005, 0.1],
     monodisperse starts, seed 2407), each with its own adaptive RKF45 step (tol 1e-8).
@@ -395,6 +409,7 @@ def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count
         lams.append(r["lam"])
         n0s.append(torch.from_numpy(monodisperse(r["M"])).cuda())
     b = smol.Batch(Us, Vs, lams, precision=precision, stream=stream, tau0=1e-3, chunk=1)
+    flags = b.tune(n0s, 1e-8, attempts=8)[0] if tune else 0
     b.start(n0s, 0.0, 1000.0, 1e-8, scheme="rkf45")
     for _ in range(W):
         b.advance()
@@ -410,7 +425,7 @@ def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count
     ms = sum(a.elapsed_time(c) for a, c in ev)
     _, stats = b.finish()
     Ms = [r["M"] for r in rec]
-    return ms, stats, Ms
+    return ms, stats, Ms, flags
 
 
 def rhs_accuracy(smol, torch, U, V):
@@ -424,13 +439,14 @@ def rhs_accuracy(smol, torch, U, V):
     return float((a - b).norm() / a.norm())
 
 
-def e2e_leg(smol, torch, precision, K, U, V, stream):
+def e2e_leg(smol, torch, precision, K, U, V, stream, sched=None):
     """Per step: pinned host state -> device, one RKF45 attempt through smol_integrate,
     device -> pinned host state; wall time of K steps."""
     from synth import monodisperse
     w = WORKLOAD
     M = w["M"]
-    sysm = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=1e-3, max_attempts=1, chunk=1)
+    sysm = smol.System(U, V, w["lam"], precision=precision, stream=stream, tau0=1e-3, max_attempts=1, chunk=1,
+                       **(sched or {}))
     h = torch.from_numpy(monodisperse(M)).pin_memory()
     d = torch.empty(M, dtype=torch.float64, device="cuda")
     t = 0.0
@@ -466,6 +482,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="systems of the batched workload (0: skip)")
     ap.add_argument("--only-batch", action="store_true", help="time only the batched workload (profiling aid)")
+    ap.add_argument("--no-tune", action="store_true", help="use the rule's FFT schedule and launch mode")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-max-evals", type=int, default=None)
     ap.add_argument("--cpu-worker", action="store_true")

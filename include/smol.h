@@ -85,6 +85,15 @@ extern "C" {
 #define SMOL_NORM_ABS 0
 #define SMOL_NORM_REL 1
 
+/* Option flags (smol_opts.flags). */
+#define SMOL_FLAG_NO_PDL 1  /* launch every kernel after its predecessor has ended (no
+                               programmatic dependent launch) */
+/* The same for one kernel class only (the SMOL_PROF_* kinds below, shifted): */
+#define SMOL_FLAG_NO_PDL_FWD_COLS 2
+#define SMOL_FLAG_NO_PDL_ROWS     4
+#define SMOL_FLAG_NO_PDL_INV_COLS 8
+#define SMOL_FLAG_NO_PDL_STEP     16
+
 typedef struct smol_system smol_system;   /* opaque, created by smol_init_system */
 
 typedef struct smol_opts {
@@ -101,8 +110,11 @@ typedef struct smol_opts {
     double  fac_max;
     int64_t max_attempts;   /* default 2^62 */
     int32_t chunk;          /* step attempts per CUDA-graph launch; default 32 */
-    int32_t reserved;
+    int32_t flags;          /* SMOL_FLAG_* bits; 0 = defaults */
     void*   stream;         /* cudaStream_t; NULL = legacy default stream */
+    /* FFT schedule of a single system (a batch uses the rule): 0 = the rule. */
+    int32_t fft_lgn1;       /* log2 N1 of Mp = N1 N2 (column length), 1 <= fft_lgn1 < log2 Mp */
+    int32_t fft_g;          /* columns per CTA of the column kernels, a power of two <= 64 */
 } smol_opts;
 
 typedef struct smol_stats {
@@ -198,6 +210,26 @@ int smol_integrate_finish(smol_system* sys, smol_stats* stats);
 int smol_profile_attempts(smol_system* sys, int32_t reps, double* kernel_ms, int64_t* kernel_launches,
                           int32_t nkinds);
 
+/* Schedule autotuner (the FFT schedule and the launch mode are implementation choices
+ * that the paper leaves open: it only states the O(M R log M) cost of the FFT route,
+ * Sec. 1). For one system of the given problem it times `attempts` step attempts of
+ * `scheme` at tolerance tol, after one warm-up chunk, for each candidate schedule:
+ *   - log2 N1 of the four-step split Mp = N1 N2: the rule's value and one either side;
+ *   - columns per CTA of the column kernels: the rule's value and twice it;
+ *   - launch mode: programmatic dependent launch for every kernel, for none, or for
+ *     all but the forward column kernel.
+ * Candidates whose shared memory does not fit are skipped. *opts is read as the base
+ * options and receives the fastest schedule in fft_lgn1, fft_g and flags (its other
+ * fields are unchanged); *us_per_attempt (may be NULL) that schedule's microseconds
+ * per attempt. d_n0 (device, M doubles, 16-byte aligned) is the state the attempts
+ * start from; it is not modified. Allocates and frees its own device memory and
+ * synchronises: a set-up call, not for timed regions. Returns SMOL_OK, SMOL_EINVAL,
+ * SMOL_EUNSUPPORTED, or SMOL_ECUDA when no candidate could be timed (e.g. the
+ * integration stopped with an error status during every timing). */
+int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double lambda,
+              const double* d_n0, double tol, int32_t scheme, int32_t attempts, smol_opts* opts,
+              double* us_per_attempt);
+
 /* Copies the step log of the last smol_integrate (the most recent min(count, cap)
  * attempts, oldest first) to host arrays of cap entries each (any may be NULL).
  * *count receives the number of attempts made. */
@@ -228,6 +260,13 @@ int smol_batch_integrate_start(smol_batch* batch, double* const* d_n, double t0,
                                double tol, int32_t scheme);
 int smol_batch_integrate_advance(smol_batch* batch);
 int smol_batch_integrate_finish(smol_batch* batch, smol_stats* stats);
+/* Launch-mode autotuner of a batch (its FFT schedules follow the rule): times
+ * `attempts` attempts of every system from copies of the states d_n[q] (not modified)
+ * for each launch mode that smol_tune tries, keeps the fastest for later integrations
+ * of this batch and returns its flags in *flags and its microseconds per attempt of the
+ * whole batch in *us_per_attempt (either may be NULL). Not while an integration runs. */
+int smol_batch_tune(smol_batch* batch, double* const* d_n, double tol, int32_t scheme,
+                    int32_t attempts, int32_t* flags, double* us_per_attempt);
 int smol_batch_get_log(smol_batch* batch, int32_t system, double* h_t, double* h_tau,
                        double* h_err, int32_t* h_accepted, int32_t cap, int64_t* count);
 void smol_batch_destroy(smol_batch* batch);

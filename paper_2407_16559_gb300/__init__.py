@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
         ("log_capacity", ctypes.c_int32), ("tau0", ctypes.c_double), ("euler_a", ctypes.c_double),
         ("tau_min_rel", ctypes.c_double), ("steady_rtol", ctypes.c_double), ("fixed_tau", ctypes.c_double),
         ("fac_min", ctypes.c_double), ("fac_max", ctypes.c_double), ("max_attempts", ctypes.c_int64),
-        ("chunk", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("chunk", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("fft_lgn1", ctypes.c_int32), ("fft_g", ctypes.c_int32),
     ]
 
 
@@ -86,7 +87,13 @@ SIGNATURES = {
     "smol_batch_integrate_finish": (ctypes.c_int, [_P, _P]),
     "smol_batch_get_log": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _I32, ctypes.POINTER(_I64)]),
     "smol_batch_destroy": (None, [_P]),
+    "smol_tune": (ctypes.c_int, [_I64, _I32, _P, _P, _D, _P, _D, _I32, _I32, ctypes.POINTER(Opts), ctypes.POINTER(_D)]),
+    "smol_batch_tune": (ctypes.c_int, [_P, _P, _D, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
 }
+
+# option flags (smol_opts.flags)
+FLAG_NO_PDL, FLAG_NO_PDL_FWD_COLS, FLAG_NO_PDL_ROWS, FLAG_NO_PDL_INV_COLS, FLAG_NO_PDL_STEP = 1, 2, 4, 8, 16
+SCHEDULE_KEYS = ("fft_lgn1", "fft_g", "flags")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -135,6 +142,23 @@ def rhs_static(U, V, lam: float, n, out=None, stream=None):
     _check(_lib.smol_rhs_static(M, R, U.data_ptr(), V.data_ptr(), float(lam), n.data_ptr(), out.data_ptr(),
                                 st.cuda_stream), "smol_rhs_static")
     return out
+
+
+def tune(U, V, lam: float, n0, tol: float, scheme: str = "rkf45", precision: str = "fp64", attempts: int = 64,
+         stream=None, device=None, **opts):
+    """smol_tune: times the candidate FFT schedules and launch modes of this problem
+    and returns ({fft_lgn1, fft_g, flags}, microseconds per attempt); pass the dict as
+    options to System."""
+    torch = _torch()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    M, R = U.shape
+    o, dev, _ = _make_opts(precision, stream, device, opts)
+    n0 = torch.as_tensor(n0).to(device=dev, dtype=torch.float64).contiguous()
+    us = ctypes.c_double()
+    _check(_lib.smol_tune(M, R, U.ctypes.data, V.ctypes.data, float(lam), n0.data_ptr(), float(tol), SCHEMES[scheme],
+                          int(attempts), ctypes.byref(o), ctypes.byref(us)), "smol_tune")
+    return {k: int(getattr(o, k)) for k in SCHEDULE_KEYS}, us.value
 
 
 def _check(rc: int, what: str):
@@ -218,6 +242,16 @@ class Batch:
         if rc in (EINVAL, ECUDA, ENOSPACE, EUNSUPPORTED):
             raise SmolError(rc, "smol_batch_integrate")
         return ns, [s.as_dict() for s in st]
+
+    def tune(self, n0s, tol: float, scheme: str = "rkf45", attempts: int = 16):
+        """smol_batch_tune: keeps the fastest launch mode for this batch; returns
+        (flags, microseconds per attempt of the whole batch)."""
+        ns, ptrs = self._states(n0s)
+        fl, us = ctypes.c_int32(), ctypes.c_double()
+        _check(_lib.smol_batch_tune(self._h, ptrs, float(tol), SCHEMES[scheme], int(attempts), ctypes.byref(fl),
+                                    ctypes.byref(us)), "smol_batch_tune")
+        self.opts.flags = fl.value
+        return fl.value, us.value
 
     def start(self, n0s, t0, t1, tol, scheme="rkf45"):
         ns, ptrs = self._states(n0s)

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "../../include/smol.h"
@@ -43,20 +44,24 @@ struct Shape {
 // `wide`: the system is part of a batch large enough to fill the GPU on its own; its
 // CTAs then take more work each (fewer, fuller CTAs: the per-CTA set-up is amortised and
 // column stores fill whole 32-byte sectors), where a lone system wants many small CTAs.
-Shape make_shape(int64_t M, int precision, bool wide = false) {
+// FFT schedule of one system. The rule: N1 = 2^ceil(lg Mp / 2) (column length), N2 =
+// Mp / N1; one column of N1 >= 256 points per CTA, several short columns per CTA so
+// that a CTA keeps at least 32 radix-8 butterflies per pass. lgn1 > 0 / g > 0 replace
+// the rule's log2 N1 / columns per CTA (single systems; chosen by the autotuner).
+Shape make_shape(int64_t M, int precision, bool wide = false, int lgn1 = 0, int g = 0) {
     Shape s;
     s.M = (int)M;
     s.lgMp = ilog2(M < 4 ? 4 : M);
     s.Mp = 1 << s.lgMp;
     s.lgN1 = (s.lgMp + 1) / 2;
-    s.lgN2 = s.lgMp / 2;
+    if (lgn1 > 0 && lgn1 < s.lgMp) s.lgN1 = lgn1;
+    s.lgN2 = s.lgMp - s.lgN1;
     s.N1 = 1 << s.lgN1;
     s.N2 = 1 << s.lgN2;
-    // one column of N1 >= 256 points per CTA; several short columns per CTA so that a
-    // CTA keeps at least 32 radix-8 butterflies per pass
     int G = 256 / s.N1;
     if (G < 1) G = 1;
     if (wide && G < 4) G = 4;
+    if (g > 0) G = g;
     if (G > s.N2) G = s.N2;
     s.G = G;
     const int ppt = wide ? 8 : 1;  // element pairs per thread of the finish kernels
@@ -222,7 +227,8 @@ size_t batch_bytes(int count, const int64_t* M, int R, const smol_opts& o) {
     const bool wide = is_wide(count, M);
     for (int q = 0; q < count; ++q) {
         if (M[q] < 1 || M[q] > mm) return 0;
-        sh.push_back(make_shape(M[q], o.precision, wide));
+        sh.push_back(count == 1 ? make_shape(M[q], o.precision, false, o.fft_lgn1, o.fft_g)
+                                : make_shape(M[q], o.precision, wide));
         tot += make_layout(sh.back(), R, std::max(o.log_capacity, 0)).total;
     }
     return make_header(sh).total + tot;
@@ -292,6 +298,16 @@ struct smol_batch : Engine {};
 // ---------------------------------------------------------------------------
 namespace {
 
+// Every kernel of an attempt asks for the same (largest) shared-memory carveout: with
+// programmatic dependent launch the next kernel's CTAs are placed on SMs while the
+// previous kernel still runs there, and an SM whose L1 / shared split would have to
+// change cannot take them, which crowds the early CTAs onto few SMs.
+template <typename K>
+bool carve(K k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+}
+
 template <typename R>
 int set_smem_attrs(const Engine* E) {
     if (cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemC) !=
@@ -299,6 +315,9 @@ int set_smem_attrs(const Engine* E) {
         cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemC) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemB) != cudaSuccess)
+        return SMOL_ECUDA;
+    if (!(carve(k_fwd_cols<R>) && carve(k_rows<R>) && carve(k_inv_cols<R>) && carve(k_finish<R>) &&
+          carve(k_lincomb<R>)))
         return SMOL_ECUDA;
     return SMOL_OK;
 }
@@ -326,20 +345,40 @@ LaunchArgs args_for(const Engine* E, bool rhs) {
     return a;
 }
 
+// Launches kernel k with programmatic stream serialisation (the kernel may start while
+// its predecessor in the stream runs; it waits for it in griddep_wait) unless the
+// options disable it.
+template <typename... KArgs, typename... Args>
+void launch(const Engine* E, int kind, void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+            Args&&... args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (E->o.flags & (SMOL_FLAG_NO_PDL | (SMOL_FLAG_NO_PDL_FWD_COLS << kind))) ? 0 : 1;
+    cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <typename R>
 void launch_eval(const Engine* E, const LaunchArgs& A, const StageIn& in, const EpiOut& eo, cudaStream_t st,
                  Prof* pr) {
     {
         ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
-        k_fwd_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(A.sys, A.mapC, A.one, in);
+        launch(E, SMOL_PROF_FWD_COLS, k_fwd_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, in);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_ROWS);
-        k_rows<R><<<E->H.nB, E->thrB, E->smemB, st>>>(A.sys, A.mapB, A.one);
+        launch(E, SMOL_PROF_ROWS, k_rows<R>, E->H.nB, E->thrB, E->smemB, st, A.sys, A.mapB, A.one);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
-        k_inv_cols<R><<<E->H.nC, E->thrC, E->smemC, st>>>(A.sys, A.mapC, A.one, in, eo);
+        launch(E, SMOL_PROF_INV_COLS, k_inv_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, in, eo);
     }
 }
 
@@ -403,11 +442,11 @@ void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cuda
     };
     auto finish = [&](const StageIn& cand, const StageIn& del) {
         ProfScope ps(pr, st, SMOL_PROF_STEP);
-        k_finish<R><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, comb2(cand, del), P);
+        launch(E, SMOL_PROF_STEP, k_finish<R>, E->H.nF, FIN_THREADS, 0, st, A.sys, A.mapF, A.one, comb2(cand, del), P);
     };
     auto half = [&](const StageIn& in) {
         ProfScope ps(pr, st, SMOL_PROF_STEP);
-        k_lincomb<R><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, in);
+        launch(E, SMOL_PROF_STEP, k_lincomb<R>, E->H.nF, FIN_THREADS, 0, st, A.sys, A.mapF, A.one, in);
     };
     const int N = SLOT_CUR, H = SLOT_HALF;
     if (scheme == SCHEME_RKF45) {
@@ -544,7 +583,8 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     const int logc = std::max(o.log_capacity, 0);
     const bool wide = is_wide(count, Ms);
     for (int q = 0; q < count; ++q) {
-        E->sh.push_back(make_shape(Ms[q], prec, wide));
+        E->sh.push_back(count == 1 ? make_shape(Ms[q], prec, false, o.fft_lgn1, o.fft_g)
+                                   : make_shape(Ms[q], prec, wide));
         E->lay.push_back(make_layout(E->sh.back(), R, logc));
     }
     E->H = make_header(E->sh);
@@ -789,6 +829,8 @@ void engine_free(Engine* E) {
 int check_opts(const smol_opts& o) {
     if (o.precision != SMOL_FP64 && o.precision != SMOL_FP32CONV) return SMOL_EINVAL;
     if (o.log_capacity < 0 || o.chunk < 0) return SMOL_EINVAL;
+    if (o.fft_lgn1 < 0 || o.fft_lgn1 > 30 || o.fft_g < 0 || o.fft_g > 64 || (o.fft_g & (o.fft_g - 1)))
+        return SMOL_EINVAL;
     return SMOL_OK;
 }
 
@@ -829,7 +871,8 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
     int64_t na = E->o.chunk > 0 ? E->o.chunk : 32;
     if (E->o.max_attempts < na) na = E->o.max_attempts;
     if (na < 1) na = 1;
-    const int64_t key = na * 64 + scheme * 16 + (fixed ? 8 : 0) + (E->o.steady_rtol > 0.0 ? 4 : 0);
+    const int64_t key = ((na * 64 + scheme * 16 + (fixed ? 8 : 0) + (E->o.steady_rtol > 0.0 ? 4 : 0)) << 8) +
+                        (E->o.flags & 0xff);
     if (E->gkey != key) {
         if (E->gexec) {
             cudaGraphExecDestroy(E->gexec);
@@ -1015,6 +1058,41 @@ int rhs_common(smol_system* S, const double* d_n, double* d_out, double* d_birth
     return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
 }
 
+// Schedule autotuner: mean time of one step attempt of engine E, run from copies of
+// the states d_n0 (into d_work), over `attempts` attempts after one warm-up chunk, in
+// microseconds; < 0 if a call failed or a system ended during the timing.
+double time_attempts(Engine* E, double* const* d_work, const double* const* d_n0, double tol, int scheme,
+                     int attempts) {
+    cudaStream_t st = E->stream;
+    for (int q = 0; q < E->count; ++q)
+        if (cudaMemcpyAsync(d_work[q], d_n0[q], (size_t)E->sh[q].M * 8, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+            return -1.0;
+    if (integrate_start(E, d_work, 0.0, 1e300, tol, scheme) != SMOL_OK) return -1.0;
+    const int64_t chunks = std::max<int64_t>(1, (attempts + E->run_attempts - 1) / E->run_attempts);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double us = -1.0;
+    if (integrate_advance(E) == SMOL_OK && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess) {
+        bool ok = true;
+        for (int64_t c = 0; c < chunks && ok; ++c) ok = integrate_advance(E) == SMOL_OK;
+        float ms = 0.f;
+        if (ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+            us = 1000.0 * ms / (double)(chunks * E->run_attempts);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // an error status or a steady stop ends the timing's validity
+    if (integrate_finish(E, nullptr) != SMOL_OK) return -1.0;
+    return us;
+}
+
+// Programmatic-launch masks the tuner tries.
+constexpr int TUNE_FLAGS[] = {0, SMOL_FLAG_NO_PDL, SMOL_FLAG_NO_PDL_FWD_COLS};
+constexpr int PDL_BITS = SMOL_FLAG_NO_PDL | SMOL_FLAG_NO_PDL_FWD_COLS | SMOL_FLAG_NO_PDL_ROWS |
+                         SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP;
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1146,6 +1224,64 @@ void smol_destroy(smol_system* S) {
     delete S;
 }
 
+int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double lambda, const double* d_n0,
+              double tol, int32_t scheme, int32_t attempts, smol_opts* opts, double* us_per_attempt) {
+    if (!h_U || !h_V || !d_n0 || !opts || M < 1 || R < 1 || R > MAXR || !(lambda >= 0.0) || attempts < 1 ||
+        scheme < SMOL_RK2 || scheme > SMOL_RKF45 || !(tol > 0.0) || ((uintptr_t)d_n0 & 15))
+        return SMOL_EINVAL;
+    smol_opts base = *opts;
+    int rc = check_opts(base);
+    if (rc != SMOL_OK) return rc;
+    if (M > max_m_for(R, base.precision)) return SMOL_EUNSUPPORTED;
+    base.max_attempts = (int64_t)1 << 62;
+    base.fixed_tau = 0.0;
+    double* d_work = nullptr;
+    if (cudaMalloc((void**)&d_work, (size_t)M * 8) != cudaSuccess) return SMOL_ECUDA;
+    const Shape def = make_shape(M, base.precision);
+    double best = -1.0;
+    smol_opts bo = base;
+    for (int dl : {0, -1, 1}) {
+        const int lg = def.lgN1 + dl;
+        if (lg < 1 || lg >= def.lgMp) continue;
+        const int g0 = make_shape(M, base.precision, false, lg, 0).G;
+        for (int gm : {1, 2}) {
+            const int g = g0 * gm;
+            if (g > 64 || g > (1 << (def.lgMp - lg)) || (gm > 1 && g0 * gm == g0)) continue;
+            smol_opts c = base;
+            c.fft_lgn1 = lg;
+            c.fft_g = g;
+            const size_t bytes = batch_bytes(1, &M, R, c);
+            if (bytes == 0) continue;
+            void* ws = nullptr;
+            if (cudaMalloc(&ws, bytes + 256) != cudaSuccess) continue;
+            void* wsa = (void*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+            smol_system* S = new smol_system();
+            if (engine_init(S, 1, &M, R, &h_U, &h_V, &lambda, c, wsa, bytes) == SMOL_OK &&
+                S->sh[0].G == g) {  // skip a G that the shared-memory limit reduced
+                for (int fl : TUNE_FLAGS) {
+                    S->o.flags = (base.flags & ~PDL_BITS) | fl;
+                    const double us = time_attempts(S, &d_work, &d_n0, tol, scheme, attempts);
+                    if (us > 0.0 && (best < 0.0 || us < best)) {
+                        best = us;
+                        bo = c;
+                        bo.flags = S->o.flags;
+                    }
+                }
+            }
+            engine_free(S);
+            delete S;
+            cudaFree(ws);
+        }
+    }
+    cudaFree(d_work);
+    if (best < 0.0) return SMOL_ECUDA;
+    opts->fft_lgn1 = bo.fft_lgn1;
+    opts->fft_g = bo.fft_g;
+    opts->flags = bo.flags;
+    if (us_per_attempt) *us_per_attempt = best;
+    return SMOL_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C interface: batch of independent systems
 // ---------------------------------------------------------------------------
@@ -1211,6 +1347,49 @@ int smol_batch_set_stream(smol_batch* B, void* stream) {
     if (!B) return SMOL_EINVAL;
     B->stream = (cudaStream_t)stream;
     B->o.stream = stream;
+    return SMOL_OK;
+}
+
+int smol_batch_tune(smol_batch* B, double* const* d_n, double tol, int32_t scheme, int32_t attempts,
+                    int32_t* flags, double* us_per_attempt) {
+    if (!B || !d_n || attempts < 1 || scheme < SMOL_RK2 || scheme > SMOL_RKF45 || !(tol > 0.0) || B->running)
+        return SMOL_EINVAL;
+    for (int q = 0; q < B->count; ++q)
+        if (!d_n[q] || ((uintptr_t)d_n[q] & 15)) return SMOL_EINVAL;
+    std::vector<double*> work(B->count, nullptr);
+    int rc = SMOL_OK;
+    for (int q = 0; q < B->count && rc == SMOL_OK; ++q)
+        if (cudaMalloc((void**)&work[q], (size_t)B->sh[q].M * 8) != cudaSuccess) rc = SMOL_ECUDA;
+    const int base = B->o.flags;
+    const int64_t maxa = B->o.max_attempts;
+    const double ftau = B->o.fixed_tau;
+    B->o.max_attempts = (int64_t)1 << 62;
+    B->o.fixed_tau = 0.0;
+    double best = -1.0;
+    int bf = base;
+    for (int fl : TUNE_FLAGS) {
+        if (rc != SMOL_OK) break;
+        B->o.flags = (base & ~PDL_BITS) | fl;
+        const double us = time_attempts(B, work.data(), d_n, tol, scheme, attempts);
+        if (us > 0.0 && (best < 0.0 || us < best)) {
+            best = us;
+            bf = B->o.flags;
+        }
+    }
+    B->o.max_attempts = maxa;
+    B->o.fixed_tau = ftau;
+    B->o.flags = bf;
+    B->gkey = -1;  // recapture with the chosen launch mask
+    if (B->gexec) {
+        cudaGraphExecDestroy(B->gexec);
+        B->gexec = nullptr;
+    }
+    for (double* w : work)
+        if (w) cudaFree(w);
+    if (rc == SMOL_OK && best < 0.0) rc = SMOL_ECUDA;
+    if (rc != SMOL_OK) return rc;
+    if (flags) *flags = bf;
+    if (us_per_attempt) *us_per_attempt = best;
     return SMOL_OK;
 }
 

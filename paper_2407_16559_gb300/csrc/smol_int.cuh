@@ -126,6 +126,72 @@ __global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv
     }
 }
 
+// Controller of one system after an attempt (one thread, on a shared-memory copy c of
+// the control block). E = ||error||^2, C = ||candidate||^2, X = max|candidate|, B != 0
+// if the candidate is not finite, MS = sum_s s candidate_s, Q = ||S(n)||^2 partial sum.
+__device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, Ctl& cref, double E, double C,
+                                           double X, double B, double MS, double Q) {
+    Ctl* c = &cref;
+    c->arrive = 0;
+    c->rhs_evals += 1;  // S(n^k) of the first stage
+    if (P.steady) {
+        c->steady = Q;
+        // ||S|| / ||n|| < rtol  <=>  Q < rtol^2 nrm2 (both sides non-negative)
+        if (c->nrm2 > 0.0 && Q < P.steady_rtol * P.steady_rtol * c->nrm2) {
+            c->status = ST_STEADY;
+            c->done = 1;
+            return;
+        }
+    }
+    c->rhs_evals += P.evals - 1;
+    c->rhs_paper += P.evals_paper;
+    c->attempts += 1;
+    double err = (P.fixed && P.scheme != SCHEME_RKF45) ? 0.0 : sqrt_d(E);
+    if (P.rel_norm) {
+        const double nn = sqrt_d(c->nrm2);
+        if (nn > 0.0) err /= nn;
+    }
+    c->err_last = err;
+    if (!isfinite(err) || B != 0.0) {
+        c->status = ST_ENONFINITE;
+        c->done = 1;
+        return;
+    }
+    int acc;
+    const double h = c->h;
+    const double tau_new = propose(P, h, c->tau, err, c->tol, &acc);
+    if (P.log_cap > 0) {
+        const int64_t slot = (c->attempts - 1) % P.log_cap;
+        S.log_t[slot] = c->t;
+        S.log_h[slot] = h;
+        S.log_e[slot] = err;
+        S.log_a[slot] = acc;
+    }
+    if (acc) {
+        c->cur ^= 1;
+        c->t = c->clamped ? c->t1 : c->t + h;
+        c->accepted += 1;
+        c->nrm2 = C;
+        c->ymax = X;
+        c->mass = MS;
+        set_xe(c, S, X);
+        if (!c->clamped) c->tau = tau_new;
+    } else {
+        c->rejected += 1;
+        c->tau = tau_new;
+    }
+    if (c->t < c->t1 && c->tau < P.tau_min_rel * fmax(1.0, fabs(c->t))) {
+        c->status = ST_EUNDERFLOW;
+        c->done = 1;
+    } else if (c->t >= c->t1) {
+        c->done = 1;
+    } else if (c->attempts >= P.max_attempts) {
+        c->status = ST_EMAXATT;
+        c->done = 1;
+    }
+    if (!c->done) set_next_step(c);
+}
+
 // Candidate and error combinations of the final kernel over one set of terms: each
 // term is loaded once; cand = sum c_j v_j and err = sum d_j v_j.
 struct Comb2 {
@@ -297,8 +363,15 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
         S.fpart[FPW * blk + q] = v;
     }
     if (!arrive_last(ctl, S.nfin, &last)) return;
-    // The last CTA reduces the per-CTA partials with all its threads (fixed order:
-    // thread j takes partials j, j + blockDim, ...; then the block-wide tree).
+    // The last CTA copies the control block into shared memory (one word per thread),
+    // reduces the per-CTA partials with all its threads (thread j takes partials j,
+    // j + blockDim, ...; then one fused tree over the block), runs the controller on
+    // the shared copy and writes the block back: no dependent global round trips in
+    // the serial part.
+    constexpr int CW = (int)(sizeof(Ctl) / 4);
+    __shared__ __align__(16) Ctl cs;
+    for (int q = threadIdx.x; q < CW; q += blockDim.x)
+        reinterpret_cast<int*>(&cs)[q] = __ldcg(reinterpret_cast<const int*>(ctl) + q);
     double E = 0.0, C = 0.0, X = 0.0, B = 0.0, Q = 0.0, MS = 0.0;
     for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) {
         const double* q = S.fpart + FPW * b;
@@ -310,72 +383,39 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     }
     if (P.steady)
         for (int b = threadIdx.x; b < S.nbx; b += blockDim.x) Q += __ldcg(S.sqpart + b);
-    E = block_sum(E, red);
-    C = block_sum(C, red);
-    Q = block_sum(Q, red);
-    MS = block_sum(MS, red);
-    X = block_max(X, red);
-    B = block_max(B, red);
-    if (threadIdx.x != 0) return;
-    Ctl* c = ctl;
-    c->arrive = 0;
-    c->rhs_evals += 1;  // S(n^k) of the first stage
-    if (P.steady) {
-        c->steady = Q;
-        // ||S|| / ||n|| < rtol  <=>  Q < rtol^2 nrm2 (both sides non-negative)
-        if (c->nrm2 > 0.0 && Q < P.steady_rtol * P.steady_rtol * c->nrm2) {
-            c->status = ST_STEADY;
-            c->done = 1;
-            return;
+    for (int o = 16; o > 0; o >>= 1) {
+        E += __shfl_down_sync(0xffffffffu, E, o);
+        C += __shfl_down_sync(0xffffffffu, C, o);
+        Q += __shfl_down_sync(0xffffffffu, Q, o);
+        MS += __shfl_down_sync(0xffffffffu, MS, o);
+        X = fmax(X, __shfl_down_sync(0xffffffffu, X, o));
+        B = fmax(B, __shfl_down_sync(0xffffffffu, B, o));
+    }
+    __syncthreads();  // wred reuse and the shared control block
+    if (lane == 0) {
+        wred[0][warp] = E;
+        wred[1][warp] = C;
+        wred[2][warp] = X;
+        wred[3][warp] = B;
+        wred[4][warp] = MS;
+        red[warp] = Q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        E = wred[0][0], C = wred[1][0], X = wred[2][0], B = wred[3][0], MS = wred[4][0], Q = red[0];
+        for (int w = 1; w < nw; ++w) {
+            E += wred[0][w];
+            C += wred[1][w];
+            X = fmax(X, wred[2][w]);
+            B = fmax(B, wred[3][w]);
+            MS += wred[4][w];
+            Q += red[w];
         }
+        controller(P, S, cs, E, C, X, B, MS, Q);
     }
-    c->rhs_evals += P.evals - 1;
-    c->rhs_paper += P.evals_paper;
-    c->attempts += 1;
-    double err = (P.fixed && P.scheme != SCHEME_RKF45) ? 0.0 : sqrt_d(E);
-    if (P.rel_norm) {
-        const double nn = sqrt_d(c->nrm2);
-        if (nn > 0.0) err /= nn;
-    }
-    c->err_last = err;
-    if (!isfinite(err) || B != 0.0) {
-        c->status = ST_ENONFINITE;
-        c->done = 1;
-        return;
-    }
-    int acc;
-    const double h = c->h;
-    const double tau_new = propose(P, h, c->tau, err, c->tol, &acc);
-    if (P.log_cap > 0) {
-        const int64_t slot = (c->attempts - 1) % P.log_cap;
-        S.log_t[slot] = c->t;
-        S.log_h[slot] = h;
-        S.log_e[slot] = err;
-        S.log_a[slot] = acc;
-    }
-    if (acc) {
-        c->cur ^= 1;
-        c->t = c->clamped ? c->t1 : c->t + h;
-        c->accepted += 1;
-        c->nrm2 = C;
-        c->ymax = X;
-        c->mass = MS;
-        set_xe(c, S, X);
-        if (!c->clamped) c->tau = tau_new;
-    } else {
-        c->rejected += 1;
-        c->tau = tau_new;
-    }
-    if (c->t < c->t1 && c->tau < P.tau_min_rel * fmax(1.0, fabs(c->t))) {
-        c->status = ST_EUNDERFLOW;
-        c->done = 1;
-    } else if (c->t >= c->t1) {
-        c->done = 1;
-    } else if (c->attempts >= P.max_attempts) {
-        c->status = ST_EMAXATT;
-        c->done = 1;
-    }
-    if (!c->done) set_next_step(c);
+    __syncthreads();
+    for (int q = threadIdx.x; q < CW; q += blockDim.x)
+        reinterpret_cast<int*>(ctl)[q] = reinterpret_cast<const int*>(&cs)[q];
 }
 
 // Preparation of an integration, pass 1: moments mu_t of n0, ||n0||^2, max|n0| and

@@ -308,27 +308,28 @@ __device__ void finalize_scalars(const SysDev& S, double y1, double* mom) {
     S.rsc[MAXT + 1] = -y1 * D1 + src;
 }
 
-// Copies the descriptor of this CTA's system into shared memory and fetches the fields
-// of its control block; returns the block index within the system. A launch over a
-// single system passes map == nullptr and the descriptor itself as a kernel argument
-// (no global round trip); a batch passes the device array and the block map.
-__device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                        const SysDev& one, SysDev& sh, CtlView& cv) {
+// Programmatic dependent launch. The kernels of an evaluation sequence are launched
+// with programmatic stream serialisation, so that a kernel's CTAs may be scheduled
+// while its predecessor in the stream is still running. griddep_wait() returns once
+// every predecessor grid has completed and its writes are visible (at once for a
+// kernel launched without the attribute); griddep_release() then lets the next kernel
+// of the stream start its own prologue. Before griddep_wait() a kernel reads only what
+// no kernel of the sequence writes (descriptors, block maps, weights, twiddle tables)
+// and writes only its own shared memory.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Copies the descriptor of this CTA's system into shared memory and returns the block
+// index within the system. A launch over a single system passes map == nullptr and the
+// descriptor itself as a kernel argument (no global round trip); a batch passes the
+// device array and the block map. Ends with a barrier.
+__device__ __forceinline__ int load_desc(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                         const SysDev& one, SysDev& sh) {
     int blk;
     const int* src;
     if (map == nullptr) {
         blk = blockIdx.x;
         src = reinterpret_cast<const int*>(&one);
-        if (threadIdx.x < MAXT) cv.xe[threadIdx.x] = one.ctl->xe[threadIdx.x];
-        if (threadIdx.x == 0) {
-            const Ctl* c = one.ctl;
-            cv.done = c->done;
-            cv.cur = c->cur;
-            cv.s0 = c->state[0];
-            cv.s1 = c->state[1];
-            cv.h = c->h;
-            cv.ymax = c->ymax;
-        }
     } else {
         const int2 m = map[blockIdx.x];
         blk = m.y;
@@ -337,19 +338,32 @@ __device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const i
     int* dst = reinterpret_cast<int*>(&sh);
     for (int q = threadIdx.x; q < (int)(sizeof(SysDev) / 4); q += blockDim.x) dst[q] = src[q];
     __syncthreads();
-    if (map != nullptr) {
-        if (threadIdx.x < MAXT) cv.xe[threadIdx.x] = sh.ctl->xe[threadIdx.x];
-        if (threadIdx.x == 0) {
-            const Ctl* c = sh.ctl;
-            cv.done = c->done;
-            cv.cur = c->cur;
-            cv.s0 = c->state[0];
-            cv.s1 = c->state[1];
-            cv.h = c->h;
-            cv.ymax = c->ymax;
-        }
-        __syncthreads();
+    return blk;
+}
+
+// Waits for the predecessor kernels (griddep_wait), releases the next one, and fetches
+// the fields of the system's control block that every kernel reads. Ends with a barrier.
+__device__ __forceinline__ void load_ctl(const SysDev& sh, CtlView& cv) {
+    griddep_wait();
+    griddep_release();
+    const Ctl* c = sh.ctl;
+    if (threadIdx.x < MAXT) cv.xe[threadIdx.x] = c->xe[threadIdx.x];
+    if (threadIdx.x == 0) {
+        cv.done = c->done;
+        cv.cur = c->cur;
+        cv.s0 = c->state[0];
+        cv.s1 = c->state[1];
+        cv.h = c->h;
+        cv.ymax = c->ymax;
     }
+    __syncthreads();
+}
+
+// Both steps, for kernels with no prologue of their own.
+__device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                        const SysDev& one, SysDev& sh, CtlView& cv) {
+    const int blk = load_desc(sysv, map, one, sh);
+    load_ctl(sh, cv);
     return blk;
 }
 
@@ -368,8 +382,7 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
     __shared__ double red[2 * MAXT][8];
     __shared__ bool lastc;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int bx = load_sys(sysv, map, one, S, cv);
-    if (cv.done) return;
+    const int bx = load_desc(sysv, map, one, S);
     const int G = S.G, T = S.T, GT = G * T, N1 = S.N1;
     const int half = (N1 >> 1) * G;
     const int n2b = bx * G;
@@ -389,6 +402,8 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
             tw4[k1 * G + g] = ldg(twc + (size_t)(n2b + g) * N1 + k1);
         }
     }
+    load_ctl(S, cv);
+    if (cv.done) return;
     const Terms<R> P = resolve_terms<R>(in, S, cv);
     R* yb = reinterpret_cast<R*>(S.ybuf);
     const Div DG = mkdiv(G);
@@ -505,8 +520,7 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     __shared__ CtlView cv;
     __shared__ R pc[MAXR];
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int blk = load_sys(sysv, map, one, S, cv);
-    if (cv.done) return;
+    const int blk = load_desc(sysv, map, one, S);
     const int G = 2 * S.T;
     const int N2 = S.N2;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
@@ -525,6 +539,8 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
         tws[idx] = ldg(reinterpret_cast<const cx<R>*>(S.tws) + (size_t)r * N2 + k2);
         twi[idx] = ldg(reinterpret_cast<const cx<R>*>(S.twr) + (size_t)r * N2 + k2);
     }
+    load_ctl(S, cv);
+    if (cv.done) return;
     if (threadIdx.x < S.npairs) {
         // FP32: pair p carries 2^(e_u + e_v - e_max) so that the sum stays in range.
         R c = (R)S.pcoef[threadIdx.x];
@@ -596,14 +612,15 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     __shared__ R delta[MAXT];
     __shared__ double src_s, bscale_s, s1_s;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int bx = load_sys(sysv, map, one, S, cv);
-    if (cv.done) return;
+    const int bx = load_desc(sysv, map, one, S);
     const int G = S.G;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
     cx<R>* b = a + (S.N1 * G);
     cx<R>* twP = b + (S.N1 * G);
     const int n2b = bx * G;
     stage_tw(twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
+    load_ctl(S, cv);
+    if (cv.done) return;
     const cx<R>* G2 = reinterpret_cast<const cx<R>*>(S.G2);
     const Div DG = mkdiv(G);
     for (int idx = threadIdx.x; idx < S.N1 * G; idx += blockDim.x) {

@@ -121,3 +121,19 @@ def test_batch_systems_stop_independently(smol):
     ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 1.0, 1e-8, scheme="rkf45")
     assert sts[1]["status"] == smol.ENONFINITE
     assert sts[0]["status"] == 0 and sts[2]["status"] == 0 and sts[0]["t"] == 1.0
+
+
+def test_batch_tune_keeps_results(smol):
+    """smol_batch_tune keeps the fastest launch mode; the batch's trajectories do not
+    depend on it (bit-identical)."""
+    import torch
+    Us, Vs, lams, n0s = _systems(SPECS)
+    st0 = [torch.from_numpy(n) for n in n0s]
+    a = smol.Batch(Us, Vs, lams, tau0=1e-3)
+    ra, sa = a.integrate(st0, 0.0, 0.3, 1e-8)
+    b = smol.Batch(Us, Vs, lams, tau0=1e-3)
+    fl, us = b.tune(st0, 1e-8, attempts=4)
+    assert fl in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS) and us > 0.0
+    rb, sb = b.integrate(st0, 0.0, 0.3, 1e-8)
+    for x, y, p, q in zip(ra, rb, sa, sb):
+        assert torch.equal(x, y) and p["accepted"] == q["accepted"]

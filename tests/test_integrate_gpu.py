@@ -160,3 +160,36 @@ def test_fp32conv_integrate_accuracy(smol):
                                    precision="fp32conv", tau0=0.01)
     assert st["status"] == 0 and ost["status"] == 0
     assert np.linalg.norm(n - m) <= 1e-4 * np.linalg.norm(m)
+
+
+def test_launch_modes_do_not_change_results(smol):
+    """Programmatic dependent launch only changes when CTAs are scheduled: every launch
+    mode gives bit-identical trajectories."""
+    import torch
+    M = 8192
+    U, V = kernel_factors("brownian", M, a=0.6)
+    n0 = torch.from_numpy(monodisperse(M)).cuda()
+    ref = None
+    for flags in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS, smol.FLAG_NO_PDL_ROWS | smol.FLAG_NO_PDL_STEP):
+        n, st = smol.System(U, V, 0.01, tau0=1e-3, flags=flags).integrate(n0, 0.0, 2.0, 1e-8)
+        got = (n.cpu().numpy(), st["accepted"], st["rejected"])
+        if ref is None:
+            ref = got
+        assert np.array_equal(got[0], ref[0]) and got[1:] == ref[1:]
+
+
+def test_tune_picks_a_valid_schedule(smol):
+    """smol_tune returns one of its candidates, and the tuned system follows the
+    default one's constant-step trajectory to rounding."""
+    import torch
+    M = 4096
+    U, V = kernel_factors("brownian", M, a=0.5)
+    n0 = torch.from_numpy(sample_state(M, 0.01)).cuda()
+    sched, us = smol.tune(U, V, 0.01, n0, 1e-8, attempts=8)
+    assert us > 0.0
+    assert sched["fft_lgn1"] in (5, 6, 7) and sched["fft_g"] in (2, 4, 8, 16)
+    assert sched["flags"] in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS)
+    a, _ = smol.System(U, V, 0.01, fixed_tau=0.01, **sched).integrate(n0, 0.0, 1.0, 1e-8)
+    b, _ = smol.System(U, V, 0.01, fixed_tau=0.01).integrate(n0, 0.0, 1.0, 1e-8)
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)

@@ -50,12 +50,12 @@ def _close(x, ref, rtol, scale=None, what=""):
     assert ei <= rtol * si + 1e-300, f"{what}: linf {ei:.3e} > {rtol:.0e} * {si:.3e}"
 
 
-def check_rhs(smol, n, U, V, lam, precision="fp64", route=None):
+def check_rhs(smol, n, U, V, lam, precision="fp64", route=None, **opts):
     import torch
     M = n.size
     if route is None:
         route = "direct" if M <= 2048 else "lowrank"
-    sysm = smol.System(U, V, lam, precision=precision)
+    sysm = smol.System(U, V, lam, precision=precision, **opts)
     dn = torch.from_numpy(n).cuda()
     S = sysm.rhs(dn).cpu().numpy()
     b, l, src = (t.cpu().numpy() for t in sysm.rhs_terms(dn))
@@ -161,3 +161,44 @@ def test_rhs_zero_state_and_repeat(smol):
     a1 = sysm.rhs(n).cpu().numpy()
     a2 = sysm.rhs(n).cpu().numpy()
     assert np.array_equal(a1, a2)  # deterministic reductions
+
+
+def _rule(M):
+    """The FFT schedule rule: log2 Mp, log2 N1 (column length) and columns per CTA."""
+    lgmp = max(2, int(M - 1).bit_length())
+    lg1 = (lgmp + 1) // 2
+    return lgmp, lg1, max(1, 256 >> lg1)
+
+
+@pytest.mark.parametrize("M", [9, 1000, 4096, 65537])
+@pytest.mark.parametrize("dl,gm", [(-1, 1), (1, 1), (0, 2), (1, 2), (-2, 4)])
+def test_rhs_fft_schedules(smol, M, dl, gm):
+    """Every schedule the autotuner may pick (another split Mp = N1 N2, more columns per
+    CTA) computes the same S: the split changes only the rounding order."""
+    lgmp, lg1, _ = _rule(M)
+    lg = lg1 + dl
+    if not 1 <= lg < lgmp:
+        pytest.skip("split outside the valid range for this size")
+    g = min(max(1, 256 >> lg) * gm, 1 << (lgmp - lg), 64)
+    U, V = kernel_factors("brownian_const", M, a=0.45)
+    try:
+        check_rhs(smol, sample_state(M, 0.02, seed=M + 7), U, V, 0.02, fft_lgn1=lg, fft_g=g)
+    except smol.SmolError as e:
+        # long rows whose T transforms exceed the shared memory of a CTA (the tuner
+        # skips these candidates too)
+        assert e.code == smol.EUNSUPPORTED and (1 << (lgmp - lg)) >= 1024
+        pytest.skip("shape beyond the shared-memory limit")
+
+
+@pytest.mark.parametrize("dl", [-1, 1])
+def test_rhs_fft_schedules_fp32conv(smol, dl):
+    M = 65536
+    lgmp, lg1, g = _rule(M)
+    U, V = kernel_factors("brownian", M, a=0.8)
+    check_rhs(smol, sample_state(M, 0.02, seed=3), U, V, 0.02, precision="fp32conv", fft_lgn1=lg1 + dl, fft_g=g)
+
+
+def test_rhs_bad_schedule_rejected(smol):
+    U, V = kernel_factors("brownian", 64, a=0.5)
+    with pytest.raises(smol.SmolError):
+        smol.System(U, V, 0.0, fft_g=3)
