@@ -146,7 +146,7 @@ Header make_header(const std::vector<Shape>& sh) {
     H.nC = H.nB = H.nF = 0;
     for (const Shape& s : sh) {
         H.nC += s.N2;  // room for G = 1; the launch count is set from the final maps
-        H.nB += s.N1 / 2;
+        H.nB += s.N1 / 2 + 1;  // row pairs and the scalar CTA
         H.nF += s.nfin;
     }
     size_t o = 0;
@@ -374,7 +374,7 @@ void launch_eval(const Engine* E, const LaunchArgs& A, const StageIn& in, const 
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_ROWS);
-        launch(E, SMOL_PROF_ROWS, k_rows<R>, E->H.nB, E->thrB, E->smemB, st, A.sys, A.mapB, A.one);
+        launch(E, SMOL_PROF_ROWS, k_rows<R>, E->H.nB, E->thrB, E->smemB, st, A.sys, A.mapB, A.one, in);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
@@ -656,7 +656,9 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         if (smem_rows(s, T) > SMEM_LIMIT || smem_cols(s, T) > SMEM_LIMIT) return SMOL_EUNSUPPORTED;
         E->smemC = std::max(E->smemC, smem_cols(s, T));
         E->smemB = std::max(E->smemB, smem_rows(s, T));
-        E->thrC = std::max(E->thrC, threads_for(s.N1 * s.G * T));
+        // one thread per radix-8 butterfly of the column tiles, and at least one per
+        // stage-input pair (so that all stage-input loads of a CTA are in flight at once)
+        E->thrC = std::max(E->thrC, std::max(threads_for(s.N1 * s.G * T), std::min(256, (s.N1 * s.G / 2 + 31) & ~31)));
         E->thrB = std::max(E->thrB, threads_for(s.N2 * 2 * T));
         char* b = ws + E->base[q];
         SysDev& d = hs[q];
@@ -729,7 +731,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         hsr[q] = d;
         hsr[q].ctl = E->d_rctl + q;
         for (int c = 0; c < s.N2 / s.G; ++c) mC.push_back(make_int2(q, c));
-        for (int c = 0; c < s.N1 / 2; ++c) mB.push_back(make_int2(q, c));
+        for (int c = 0; c <= s.N1 / 2; ++c) mB.push_back(make_int2(q, c));  // 0: scalar CTA
         for (int c = 0; c < s.nfin; ++c) mF.push_back(make_int2(q, c));
 
         // Host images of the tables: weights (zero beyond M) and twiddles
@@ -851,6 +853,7 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
         h.t = t0;
         h.t1 = t1;
         h.tol = tol;
+        h.itol2 = tol > 0.0 ? 1.0 / (tol * tol) : 0.0;
         h.tau = E->o.tau0 > 0.0 ? E->o.tau0 : (fixed ? E->o.fixed_tau : 0.0);
         h.state[0] = d_n[q];
         h.state[1] = (double*)(E->ws + E->base[q] + E->lay[q].stateB);

@@ -201,13 +201,39 @@ __device__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __re
     return a;
 }
 
+// Asynchronous global -> shared copies of one element (4, 8 or 16 bytes; both addresses
+// aligned to the size): every copy a thread issues is in flight at once, and
+// cp_async_wait() waits for all of the calling thread's copies (a barrier then makes
+// them visible to the CTA).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* smem, const T* gmem) {
+    cp_async<(int)sizeof(T)>(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Stages the table W_P^e (e < P) of a length-P tile transform into shared memory from
-// the global table of W_{2Mp}^e.
+// the global table of W_{2Mp}^e (e < Mp; W^{e + Mp} = -W^e): stage_tw issues the
+// copies, stage_tw_fix (after cp_async_wait, by the same threads) negates the entries
+// taken from the second half-period.
 template <typename R>
 __device__ __forceinline__ void stage_tw(cx<R>* twP, int lgP, const cx<R>* __restrict__ tw, int lgMp) {
     const int P = 1 << lgP;
     const int sh = lgMp + 1 - lgP;
-    for (int e = threadIdx.x; e < P; e += blockDim.x) twP[e] = twl(tw, (uint32_t)e << sh, 1u << lgMp);
+    const uint32_t Mp = 1u << lgMp;
+    for (int e = threadIdx.x; e < P; e += blockDim.x) cp_async_el(twP + e, tw + (((uint32_t)e << sh) & (Mp - 1)));
+}
+template <typename R>
+__device__ __forceinline__ void stage_tw_fix(cx<R>* twP, int lgP, int lgMp) {
+    const int P = 1 << lgP;
+    const int sh = lgMp + 1 - lgP;
+    const uint32_t Mp = 1u << lgMp;
+    for (int e = threadIdx.x; e < P; e += blockDim.x)
+        if (((uint32_t)e << sh) & Mp) twP[e] = -twP[e];
 }
 
 // Deterministic block-wide sum (fixed reduction order). sh: >= 32 doubles of shared

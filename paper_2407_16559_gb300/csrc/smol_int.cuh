@@ -40,47 +40,38 @@ __device__ __forceinline__ double sqrt_d(double x) {
     if (x < 1e-30 || x > 1e30 || !isfinite(x)) return sqrt(x);
     return x * rsqrt_d(x);
 }
-// x^(1/n) for x in [1e-30, 1e30], n in {2, 4, 5}.
-__device__ __forceinline__ double root_d(double x, int n) {
-    double z = (double)powf((float)x, -1.0f / (float)n);
-    const double inv_n = 1.0 / (double)n;
-    for (int it = 0; it < 2; ++it) {
-        double zn = z * z;
-        if (n == 4) zn = zn * zn;
-        else if (n == 5) zn = zn * zn * z;
-        z = z * (1.0 + (1.0 - x * zn) * inv_n);
-    }
-    double zm = 1.0;  // z^(n-1)
-    for (int k = 1; k < n; ++k) zm *= z;
-    return x * zm;
+// Step factor of Sec. 2 from a = (err / tol)^2: s (tol / err)^(1/p) = s a^(-1/q), q = 2p,
+// clamped to [fac_min, fac_max]. y = a^(-1/q) from an FP32 estimate refined by one
+// Newton step in FP64 on y^-q - a = 0, y <- y (1 + (1 - a y^q) / q), which takes the
+// ~1e-7 estimate below 1e-13; a is first clamped to [1e-36, 1e36] (the factor sits at
+// a clamp bound well inside that range). err = 0 gives fac_max.
+__device__ __forceinline__ double step_factor(const CtlParams& P, double a, double s, int q) {
+    if (!(a > 0.0)) return P.fac_max;
+    a = fmin(fmax(a, 1e-36), 1e36);
+    double y = (double)exp2f(-log2f((float)a) / (float)q);
+    const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    const double yq = q == 10 ? y8 * y2 : (q == 8 ? y8 : (q == 4 ? y4 : y2));
+    y = y * (1.0 + (1.0 - a * yq) * (1.0 / (double)q));
+    return fmin(fmax(s * y, P.fac_min), P.fac_max);
 }
 
-// Step-size rules of Sec. 2. Returns the proposed step; *acc the decision.
-__device__ __forceinline__ double propose(const CtlParams& P, double h, double tau, double err, double tol, int* acc) {
+// Step-size rules of Sec. 2 from a = (err / tol)^2. Returns the proposed step; *acc the
+// decision (err <= tol, i.e. a <= 1).
+__device__ __forceinline__ double propose(const CtlParams& P, double h, double tau, double a, int* acc) {
     if (P.fixed) {
         *acc = 1;
         return tau;
     }
-    *acc = err <= tol;
-    if (P.scheme == SCHEME_RKF45 || P.ctrl == CTRL_FORMULA) {
-        // RKF45: tau <- 0.9 tau (tol/err)^(1/5); Eq. (6): tau <- 1/4 tau (tol/err)^(1/p).
-        const double s = (P.scheme == SCHEME_RKF45) ? 0.9 : 0.25;
-        const double ex = (P.scheme == SCHEME_RKF45) ? 0.2 : 1.0 / (double)P.order;
-        (void)ex;
-        const int n = (P.scheme == SCHEME_RKF45) ? 5 : P.order;
-        double fac;
-        if (err == 0.0) {
-            fac = P.fac_max;
-        } else {
-            double x = tol / err;
-            // outside [1e-30, 1e30] the factor is clamped anyway
-            x = fmin(fmax(x, 1e-30), 1e30);
-            fac = fmin(fmax(s * root_d(x, n), P.fac_min), P.fac_max);
-        }
-        return h * fac;
-    }
+    *acc = a <= 1.0;
+    if (P.scheme == SCHEME_RKF45) return h * step_factor(P, a, 0.9, 10);      // 0.9 tau (tol/err)^(1/5)
+    if (P.ctrl == CTRL_FORMULA) return h * step_factor(P, a, 0.25, 2 * P.order);  // Eq. (6)
     // halve on reject, double on accept
     return *acc ? 2.0 * h : 0.5 * h;
+}
+
+// The steady stop: ||S(n)|| / ||n|| < rtol, i.e. Q < rtol^2 nrm2 (both non-negative).
+__device__ __forceinline__ bool steady_stop(const CtlParams& P, double nrm2, double Q) {
+    return P.steady && nrm2 > 0.0 && Q < P.steady_rtol * P.steady_rtol * nrm2;
 }
 
 __device__ __forceinline__ void set_next_step(Ctl* c) {
@@ -127,17 +118,19 @@ __global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv
 }
 
 // Controller of one system after an attempt (one thread, on a shared-memory copy c of
-// the control block). E = ||error||^2, C = ||candidate||^2, X = max|candidate|, B != 0
-// if the candidate is not finite, MS = sum_s s candidate_s, Q = ||S(n)||^2 partial sum.
+// the control block). E = ||error||^2, C = ||candidate||^2, X = max|candidate|, bad:
+// the candidate is not finite, MS = sum_s s candidate_s, Q = ||S(n)||^2. The accept
+// decision and the step factor use a = E / tol^2 (divided by nrm2 for the relative
+// norm) and need no square root; err itself (stats and log) is formed by another
+// thread at the same time (error_norm).
 __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, Ctl& cref, double E, double C,
-                                           double X, double B, double MS, double Q) {
+                                           double X, bool bad, double MS, double Q) {
     Ctl* c = &cref;
     c->arrive = 0;
     c->rhs_evals += 1;  // S(n^k) of the first stage
     if (P.steady) {
         c->steady = Q;
-        // ||S|| / ||n|| < rtol  <=>  Q < rtol^2 nrm2 (both sides non-negative)
-        if (c->nrm2 > 0.0 && Q < P.steady_rtol * P.steady_rtol * c->nrm2) {
+        if (steady_stop(P, c->nrm2, Q)) {
             c->status = ST_STEADY;
             c->done = 1;
             return;
@@ -146,25 +139,20 @@ __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, 
     c->rhs_evals += P.evals - 1;
     c->rhs_paper += P.evals_paper;
     c->attempts += 1;
-    double err = (P.fixed && P.scheme != SCHEME_RKF45) ? 0.0 : sqrt_d(E);
-    if (P.rel_norm) {
-        const double nn = sqrt_d(c->nrm2);
-        if (nn > 0.0) err /= nn;
-    }
-    c->err_last = err;
-    if (!isfinite(err) || B != 0.0) {
+    double a = (P.fixed && P.scheme != SCHEME_RKF45) ? 0.0 : E * c->itol2;
+    if (P.rel_norm && c->nrm2 > 0.0) a /= c->nrm2;
+    if (bad || !(E <= 1.7e308)) {
         c->status = ST_ENONFINITE;
         c->done = 1;
         return;
     }
     int acc;
     const double h = c->h;
-    const double tau_new = propose(P, h, c->tau, err, c->tol, &acc);
+    const double tau_new = propose(P, h, c->tau, a, &acc);
     if (P.log_cap > 0) {
         const int64_t slot = (c->attempts - 1) % P.log_cap;
         S.log_t[slot] = c->t;
         S.log_h[slot] = h;
-        S.log_e[slot] = err;
         S.log_a[slot] = acc;
     }
     if (acc) {
@@ -192,6 +180,29 @@ __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, 
     if (!c->done) set_next_step(c);
 }
 
+// err of an attempt for the stats and the step log (beside the controller, on another
+// warp): sqrt(E), over ||n|| for the relative norm. nrm2_0 and att0 are ||n||^2 and
+// the attempt count read before the controller runs; of c only err_last is written.
+__device__ __forceinline__ void error_norm(const CtlParams& P, const SysDev& S, Ctl& c, double nrm2_0, int64_t att0,
+                                           double E, bool bad, double Q) {
+    if (steady_stop(P, nrm2_0, Q)) return;
+    double err = (P.fixed && P.scheme != SCHEME_RKF45) ? 0.0 : sqrt_d(E);
+    if (P.rel_norm) {
+        const double nn = sqrt_d(nrm2_0);
+        if (nn > 0.0) err /= nn;
+    }
+    c.err_last = err;
+    if (bad || !(E <= 1.7e308)) return;
+    if (P.log_cap > 0) S.log_e[att0 % P.log_cap] = err;
+}
+
+// |x| as the bit pattern of a double (an unsigned integer order that agrees with the
+// order of the non-negative doubles; NaN and infinity patterns are >= INF_BITS).
+constexpr unsigned long long INF_BITS = 0x7ff0000000000000ull;
+__device__ __forceinline__ unsigned long long absbits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
 // Candidate and error combinations of the final kernel over one set of terms: each
 // term is loaded once; cand = sum c_j v_j and err = sum d_j v_j.
 struct Comb2 {
@@ -211,14 +222,24 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
                                                    const CtlParams P) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
-    __shared__ double red[33];
-    __shared__ double wred[5][8];
+    __shared__ double wred[4][8];
+    __shared__ unsigned long long xred[8];
     __shared__ bool last;
+    __shared__ __align__(16) Ctl cs;
+    constexpr int CW = (int)(sizeof(Ctl) / 4);
     const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
     if (cv.done) return;
+    // The control block is copied into shared memory now (no kernel writes it while this
+    // one runs): the last CTA runs the controller on that copy, off global memory.
+    for (int q = threadIdx.x; q < CW; q += blockDim.x)
+        reinterpret_cast<int*>(&cs)[q] = __ldcg(reinterpret_cast<const int*>(ctl) + q);
     double* outp = const_cast<double*>(cv.cur ? cv.s0 : cv.s1);
-    double se = 0.0, sc = 0.0, mx = 0.0, bad = 0.0, ms = 0.0;
+    // max |candidate| as the bit pattern of a non-negative double (integer max is
+    // monotone on those, and a NaN or infinity pattern is at least INF_BITS, which marks
+    // a non-finite candidate)
+    double se = 0.0, sc = 0.0, ms = 0.0;
+    unsigned long long mxb = 0ull;
     const int np = (S.M + 1) >> 1;
     const StageIn& in = cd.in;
     const Terms<R> tp = resolve_terms<R>(in, S, cv, false);
@@ -291,8 +312,7 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
         }
         se = (double)fse;
         sc = (double)fsc;
-        mx = (double)fmx;
-        bad = fbad ? 1.0 : 0.0;
+        mxb = fbad ? INF_BITS : absbits((double)fmx);
     } else {
     for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
         const int i = 2 * p;
@@ -335,50 +355,53 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
         se += d0 * d0 + d1 * d1;
         sc += y0 * y0 + y1 * y1;
         ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
-        mx = fmax(mx, fmax(fabs(y0), fabs(y1)));
-        if (!isfinite(y0) || !isfinite(y1)) bad = 1.0;
+        mxb = max(mxb, max(absbits(y0), absbits(y1)));
     }
     }
-    // one fused warp-level reduction of the five partials, then one pass over the warps
+    // one fused warp-level reduction of the partials, then one pass over the warps
     for (int o = 16; o > 0; o >>= 1) {
         se += __shfl_down_sync(0xffffffffu, se, o);
         sc += __shfl_down_sync(0xffffffffu, sc, o);
         ms += __shfl_down_sync(0xffffffffu, ms, o);
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        bad = fmax(bad, __shfl_down_sync(0xffffffffu, bad, o));
+        mxb = max(mxb, __shfl_down_sync(0xffffffffu, mxb, o));
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) {
         wred[0][warp] = se;
         wred[1][warp] = sc;
-        wred[2][warp] = mx;
-        wred[3][warp] = bad;
-        wred[4][warp] = ms;
+        wred[2][warp] = ms;
+        xred[warp] = mxb;
     }
     __syncthreads();
-    if (threadIdx.x < 5) {
+    if (threadIdx.x < 4) {
         const int q = threadIdx.x;
-        double v = wred[q][0];
-        for (int w = 1; w < nw; ++w) v = (q == 2 || q == 3) ? fmax(v, wred[q][w]) : v + wred[q][w];
-        S.fpart[FPW * blk + q] = v;
+        double v = 0.0;
+        if (q == 2) {
+            unsigned long long x = xred[0];
+            for (int w = 1; w < nw; ++w) x = max(x, xred[w]);
+            v = __longlong_as_double((long long)x);
+        } else if (q < 2) {
+            v = wred[q][0];
+            for (int w = 1; w < nw; ++w) v += wred[q][w];
+        } else {
+            v = wred[2][0];
+            for (int w = 1; w < nw; ++w) v += wred[2][w];
+        }
+        S.fpart[FPW * blk + (q == 3 ? 4 : q)] = v;  // E, C, max bits, -, mass moment
     }
     if (!arrive_last(ctl, S.nfin, &last)) return;
-    // The last CTA copies the control block into shared memory (one word per thread),
-    // reduces the per-CTA partials with all its threads (thread j takes partials j,
-    // j + blockDim, ...; then one fused tree over the block), runs the controller on
-    // the shared copy and writes the block back: no dependent global round trips in
-    // the serial part.
-    constexpr int CW = (int)(sizeof(Ctl) / 4);
-    __shared__ __align__(16) Ctl cs;
-    for (int q = threadIdx.x; q < CW; q += blockDim.x)
-        reinterpret_cast<int*>(&cs)[q] = __ldcg(reinterpret_cast<const int*>(ctl) + q);
-    double E = 0.0, C = 0.0, X = 0.0, B = 0.0, Q = 0.0, MS = 0.0;
+    // The last CTA reduces the per-CTA partials with all its threads (thread j takes
+    // partials j, j + blockDim, ...; then one fused tree over the block) and runs the
+    // controller (thread 0) and the error norm (thread 32) on the shared copy of the
+    // control block, which it then writes back.
+    double E = 0.0, C = 0.0, Q = 0.0, MS = 0.0;
+    unsigned long long XB = 0ull;
+#pragma unroll 4
     for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) {
         const double* q = S.fpart + FPW * b;
         E += __ldcg(q);
         C += __ldcg(q + 1);
-        X = fmax(X, __ldcg(q + 2));
-        B = fmax(B, __ldcg(q + 3));
+        XB = max(XB, (unsigned long long)__double_as_longlong(__ldcg(q + 2)));
         MS += __ldcg(q + 4);
     }
     if (P.steady)
@@ -388,30 +411,32 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
         C += __shfl_down_sync(0xffffffffu, C, o);
         Q += __shfl_down_sync(0xffffffffu, Q, o);
         MS += __shfl_down_sync(0xffffffffu, MS, o);
-        X = fmax(X, __shfl_down_sync(0xffffffffu, X, o));
-        B = fmax(B, __shfl_down_sync(0xffffffffu, B, o));
+        XB = max(XB, __shfl_down_sync(0xffffffffu, XB, o));
     }
-    __syncthreads();  // wred reuse and the shared control block
+    const double nrm2_0 = cs.nrm2;  // read before the controller may overwrite them
+    const int64_t att0 = cs.attempts;
+    __syncthreads();  // wred / xred reuse
     if (lane == 0) {
         wred[0][warp] = E;
         wred[1][warp] = C;
-        wred[2][warp] = X;
-        wred[3][warp] = B;
-        wred[4][warp] = MS;
-        red[warp] = Q;
+        wred[2][warp] = MS;
+        wred[3][warp] = Q;
+        xred[warp] = XB;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        E = wred[0][0], C = wred[1][0], X = wred[2][0], B = wred[3][0], MS = wred[4][0], Q = red[0];
+    const int t2 = blockDim.x > 32 ? 32 : 0;
+    if (threadIdx.x == 0 || threadIdx.x == t2) {
+        E = wred[0][0], C = wred[1][0], MS = wred[2][0], Q = wred[3][0], XB = xred[0];
         for (int w = 1; w < nw; ++w) {
             E += wred[0][w];
             C += wred[1][w];
-            X = fmax(X, wred[2][w]);
-            B = fmax(B, wred[3][w]);
-            MS += wred[4][w];
-            Q += red[w];
+            MS += wred[2][w];
+            Q += wred[3][w];
+            XB = max(XB, xred[w]);
         }
-        controller(P, S, cs, E, C, X, B, MS, Q);
+        const bool bad = XB >= INF_BITS;
+        if (threadIdx.x == t2) error_norm(P, S, cs, nrm2_0, att0, E, bad, Q);
+        if (threadIdx.x == 0) controller(P, S, cs, E, C, __longlong_as_double((long long)XB), bad, MS, Q);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < CW; q += blockDim.x)

@@ -53,6 +53,7 @@ struct Ctl {
     double ymax;                // max_i |n_i| of the current state (FP32 input scaling)
     double steady;              // ||S(n)||_2^2 of the last attempt's first stage (unscaled)
     double mass;                // sum_s s n_s of the current state
+    double itol2;               // 1 / tol^2 (0 for constant steps without a tolerance)
     int32_t done, status, cur, clamped;
     int64_t attempts, accepted, rejected, rhs_evals, rhs_paper;
     double* state[2];           // double-buffered state; state[cur] is n^k
@@ -78,8 +79,7 @@ struct SysDev {
     double* mpart;   // moment partials [t][bx][2]
     double* fpart;   // partials of the finish / preparation kernels [block][FPW]
     double* sqpart;  // ||S||^2 partials [bx]
-    double* aux;     // MAXT + 1 doubles: collision-rate coefficients of the preparation;
-                     // aux[MAXT] = y_1 of the current evaluation in FP64
+    double* aux;     // MAXT + 1 doubles: collision-rate coefficients of the preparation
     double* rsc;     // RHS scalars of the current evaluation: death coefficients delta_t
                      // [0, MAXT), monomer source [MAXT], S_1 [MAXT + 1]
     void* shadow0;   // FP32 form: R-typed copies of the two state buffers (stage inputs)
@@ -224,6 +224,14 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
     }
 }
 
+// Transforms whose weights a column CTA loads ahead of the wait for the previous
+// kernel (all of them for T <= WPRE), and a register-array lookup by a runtime index.
+constexpr int WPRE = 4;
+template <typename V>
+__device__ __forceinline__ V pick(const V (&v)[WPRE], int t) {
+    return t == 0 ? v[0] : (t == 1 ? v[1] : (t == 2 ? v[2] : v[3]));
+}
+
 // Exponent of the input scaling of transform t: FP64 runs unscaled; FP32 divides
 // x_t by 2^(ilogb(max|W_t|) + ilogb(max|y|)) so that its largest entry is near 1.
 template <typename R>
@@ -264,13 +272,14 @@ __device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
 }
 
 // Scalars of one evaluation from the column-pass moment partials (one CTA, after all
-// partials are written): mu_t, nu_t summed over the columns in a fixed order, then
+// partials are written; *y1p = y_1 in FP64, read after the first barrier): mu_t, nu_t
+// summed over the columns in a fixed order, then
 //   delta_t = sum_{alpha: u=t} coef_alpha mu_{v(alpha)}   (death: D_s = sum_t delta_t W_t[s])
 //   source  = lambda/2 sum coef (rho_u sigma_v + sigma_u rho_v) + lambda y_1 sum coef W_u[1] rho_v
 //   S_1     = -y_1 D_1 + source  (FP64: its two terms nearly cancel)
 // with sigma_t = mu_t - W_t[1] y_1, rho_t = nu_t - W_t[1] y_1.
 template <typename R>
-__device__ void finalize_scalars(const SysDev& S, double y1, double* mom) {
+__device__ void finalize_scalars(const SysDev& S, const double* y1p, double* mom) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     for (int q = warp; q < 2 * S.T; q += nw) {
         const int t = q >> 1, which = q & 1;
@@ -281,6 +290,7 @@ __device__ void finalize_scalars(const SysDev& S, double y1, double* mom) {
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    const double y1 = *y1p;
     const R* Wr = reinterpret_cast<const R*>(S.W);
     double sig[MAXT], rho[MAXT], del[MAXT], w1s[MAXT];
     for (int t = 0; t < S.T; ++t) {
@@ -380,7 +390,6 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ double red[2 * MAXT][8];
-    __shared__ bool lastc;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_desc(sysv, map, one, S);
     const int G = S.G, T = S.T, GT = G * T, N1 = S.N1;
@@ -399,14 +408,29 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         const cx<R>* twc = reinterpret_cast<const cx<R>*>(S.twc);
         for (int idx = threadIdx.x; idx < N1 * G; idx += blockDim.x) {
             const int k1 = idx & (N1 - 1), g = idx >> S.lgN1;  // contiguous reads along k1
-            tw4[k1 * G + g] = ldg(twc + (size_t)(n2b + g) * N1 + k1);
+            cp_async_el(tw4 + k1 * G + g, twc + (size_t)(n2b + g) * N1 + k1);
         }
     }
+    // weights of this thread's first element pair for the first WPRE transforms: constant
+    // data, loaded before the wait for the previous kernel
+    const R* Wall = reinterpret_cast<const R*>(S.W);
+    const Div DG = mkdiv(G);
+    typename vec2<R>::T wpre[WPRE];
+    if ((int)threadIdx.x < half) {
+        int g, n1;
+        divmod(DG, threadIdx.x, n1, g);
+        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
+#pragma unroll
+        for (int t = 0; t < WPRE; ++t)
+            if (t < T) wpre[t] = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wall + (size_t)t * S.Mp + i));
+    }
     load_ctl(S, cv);
-    if (cv.done) return;
+    if (cv.done) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
     const Terms<R> P = resolve_terms<R>(in, S, cv);
     R* yb = reinterpret_cast<R*>(S.ybuf);
-    const Div DG = mkdiv(G);
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
         int g, n1;
         divmod(DG, idx, n1, g);
@@ -417,18 +441,17 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         ys[2 * idx + 1] = y1;
         if (!in.direct) *reinterpret_cast<typename vec2<R>::T*>(yb + i) = {y0, y1};
     }
-    if (bx == 0 && threadIdx.x == 0 && !in.direct) {
-        // y_1 in FP64 (from the FP64 state, not its shadow) for the monomer equation,
-        // whose two large terms nearly cancel
-        const Terms<R> P64 = resolve_terms<R>(in, S, cv, false);
-        double z0, z1;
-        stage_pair<double, R>(in, P64, S.M, 0, z0, z1);
-        S.aux[MAXT] = z0;
-    }
     for (int q = half * T + threadIdx.x; q < N1 * GT; q += blockDim.x) a[q] = mk<R>((R)0, (R)0);
+    cp_async_wait();
+    stage_tw_fix(twP, S.lgN1, S.lgMp);
     __syncthreads();
-    const R* Wall = reinterpret_cast<const R*>(S.W);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    // FP64 form: the per-thread moments go through shared memory (the second tile
+    // buffer, unused until the transform) and each is summed by one warp, which takes
+    // far fewer FP64 instructions than a shuffle tree in every warp; the FP32 form sums
+    // in FP32 shuffles and then in FP64 across warps.
+    const bool viasm = sizeof(R) == sizeof(double) && N1 * G >= (int)blockDim.x;
+    double* rb = reinterpret_cast<double*>(b);
     for (int t = 0; t < T; ++t) {
         const R sc = pow2<R>(-xexp<R>(S, cv, t));
         const R* Wt = Wall + (size_t)t * S.Mp;
@@ -437,13 +460,19 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
             int g, n1;
             divmod(DG, idx, n1, g);
             const int i = 2 * ((n1 << S.lgN2) + n2b + g);
-            const typename vec2<R>::T w = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wt + i));
+            const typename vec2<R>::T w = (idx == (int)threadIdx.x && t < WPRE)
+                                              ? pick(wpre, t)
+                                              : __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wt + i));
             const R x0 = w.x * ys[2 * idx], x1 = w.y * ys[2 * idx + 1];
             mu += x0 + x1;
             nu += (R)(i + 1) * x0 + (R)(i + 2) * x1;
             a[n1 * GT + t * G + g] = mk<R>(x0 * sc, x1 * sc);
         }
-        // warp sums in the compute type (FP32 in the FP32 form), then FP64 across warps
+        if (viasm) {
+            rb[(2 * t) * blockDim.x + threadIdx.x] = (double)mu;
+            rb[(2 * t + 1) * blockDim.x + threadIdx.x] = (double)nu;
+            continue;
+        }
         for (int o = 16; o > 0; o >>= 1) {
             mu += __shfl_down_sync(0xffffffffu, mu, o);
             nu += __shfl_down_sync(0xffffffffu, nu, o);
@@ -454,19 +483,19 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         }
     }
     __syncthreads();
-    if (threadIdx.x < 2 * T) {
-        const int nw = (blockDim.x + 31) >> 5;
+    if (viasm) {
+        for (int q = warp; q < 2 * T; q += nw) {
+            double v = 0.0;
+            for (int k = lane; k < (int)blockDim.x; k += 32) v += rb[q * blockDim.x + k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) S.mpart[2 * ((size_t)(q >> 1) * S.nbx + bx) + (q & 1)] = v;
+        }
+        __syncthreads();  // the transform overwrites the second tile buffer
+    } else if (threadIdx.x < 2 * T) {
         double v = 0.0;
         for (int w = 0; w < nw; ++w) v += red[threadIdx.x][w];
         const int t = threadIdx.x >> 1;
         S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
-    }
-    // the last column CTA of the system turns the partials into the evaluation's scalars
-    if (arrive_last(S.ctl, S.nbx, &lastc)) {
-        const double y1 = in.direct ? __ldg(reinterpret_cast<const double*>(P.p[0])) : __ldcg(S.aux + MAXT);
-        finalize_scalars<R>(S, y1, &red[0][0]);
-        if (threadIdx.x == 0) S.ctl->arrive = 0;
-        __syncthreads();
     }
     cx<R>* res = tile_fft<R, false>(a, b, S.lgN1, GT, twP);
     cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
@@ -482,14 +511,20 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
 // ---------------------------------------------------------------------------
 // Kernel B: row transforms of length N2 for a pair of rows (k1, N1 - k1), the
 // real-FFT split, the product sum over kernel terms, the packed inverse spectrum,
-// inverse row transforms and the inverse twiddle. CTA b of a system owns rows
-// (b, N1 - b); CTA 0 owns rows (0, N1 / 2).
+// inverse row transforms and the inverse twiddle. CTA 0 of a system is its scalar CTA;
+// CTA b + 1 owns rows (b, N1 - b), CTA 1 rows (0, N1 / 2).
 // ---------------------------------------------------------------------------
+// FP64 form (FOLD): the factors 1/2 of E, O and of the packed inverse and the first
+// pair's coefficient are taken out of the per-frequency arithmetic (it then forms 2 X,
+// sums pc[p] / pc[0] (2X_u)(2X_v) and returns 2 Y / pc[0] * 4) and applied once in the
+// birth scale of the inverse column kernel (fold_scale); the FP64 pipe is what bounds
+// this kernel. The FP32 form keeps them in place, where they keep the values in range.
 template <typename R>
 __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, int G, int ia, int ib, cx<R> w,
                                               const R* pc, cx<R>& Ya, cx<R>& Yb) {
     // Z holds the row spectra as Z[k2 * G + col], col = 2 t + rho; ia / ib are the
     // offsets k2 * G + rho of the pair's two frequencies ka and Mp - ka; w = W_L^ka.
+    constexpr bool FOLD = sizeof(R) == sizeof(double);
     cx<R> Ca = mk<R>((R)0, (R)0), Cb = Ca;
     for (int p = 0; p < S.npairs; ++p) {
         const int u = S.pu[p], v = S.pv[p];
@@ -499,28 +534,61 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
         for (int q = 0; q < 2; ++q) {
             const cx<R> za = Z[ia + 2 * tt[q]];
             const cx<R> zb = conj(Z[ib + 2 * tt[q]]);
-            const cx<R> E = scl(za + zb, (R)0.5);
-            const cx<R> O = scl(mul_mi(za - zb), (R)0.5);
+            cx<R> E = za + zb, O = mul_mi(za - zb);
+            if (!FOLD) {
+                E = scl(E, (R)0.5);
+                O = scl(O, (R)0.5);
+            }
             const cx<R> wO = w * O;
             Xa[q] = E + wO;
             Xb[q] = conj(E - wO);
         }
-        Ca = Ca + scl(Xa[0] * Xa[1], pc[p]);
-        Cb = Cb + scl(Xb[0] * Xb[1], pc[p]);
+        cx<R> pa = Xa[0] * Xa[1], pb = Xb[0] * Xb[1];
+        if (!FOLD || pc[p] != (R)1) {
+            pa = scl(pa, pc[p]);
+            pb = scl(pb, pc[p]);
+        }
+        Ca = Ca + pa;
+        Cb = Cb + pb;
     }
     const cx<R> wb = -conj(w);  // W_L^(Mp - ka)
-    Ya = scl(w * (Ca - conj(Cb)) + mul_pi(Ca + conj(Cb)), (R)0.5);
-    Yb = scl(wb * (Cb - conj(Ca)) + mul_pi(Cb + conj(Ca)), (R)0.5);
+    Ya = w * (Ca - conj(Cb)) + mul_pi(Ca + conj(Cb));
+    Yb = wb * (Cb - conj(Ca)) + mul_pi(Cb + conj(Ca));
+    if (!FOLD) {
+        Ya = scl(Ya, (R)0.5);
+        Yb = scl(Yb, (R)0.5);
+    }
 }
+
+// First pair coefficient taken out of the FP64 spectral product (1 if it is zero).
+__device__ __forceinline__ double fold_coef(const SysDev& S) { return S.pcoef[0] != 0.0 ? S.pcoef[0] : 1.0; }
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                              const __grid_constant__ SysDev one) {
+                                              const __grid_constant__ SysDev one, const StageIn in) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ R pc[MAXR];
+    __shared__ double y1s;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int blk = load_desc(sysv, map, one, S);
+    const int cta = load_desc(sysv, map, one, S);
+    if (cta == 0) {
+        // The scalar CTA of the system, beside the row CTAs: y_1 in FP64 (from the FP64
+        // state, not its FP32 shadow: the two large terms of the monomer equation nearly
+        // cancel), then the moment partials of the column pass turned into the
+        // evaluation's scalars, which only the inverse column kernel reads.
+        load_ctl(S, cv);
+        if (cv.done) return;
+        if (threadIdx.x == 0) {
+            const Terms<R> P64 = resolve_terms<R>(in, S, cv, false);
+            double z0, z1;
+            stage_pair<double, R>(in, P64, S.M, 0, z0, z1);
+            y1s = z0;
+        }
+        finalize_scalars<R>(S, &y1s, reinterpret_cast<double*>(smraw));
+        return;
+    }
+    const int blk = cta - 1;  // row pair
     const int G = 2 * S.T;
     const int N2 = S.N2;
     cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
@@ -536,14 +604,19 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
         const int rho = idx >> S.lgN2, k2 = idx & (N2 - 1);
         const uint32_t r = (uint32_t)(rho ? r1 : r0);
-        tws[idx] = ldg(reinterpret_cast<const cx<R>*>(S.tws) + (size_t)r * N2 + k2);
-        twi[idx] = ldg(reinterpret_cast<const cx<R>*>(S.twr) + (size_t)r * N2 + k2);
+        cp_async_el(tws + idx, reinterpret_cast<const cx<R>*>(S.tws) + (size_t)r * N2 + k2);
+        cp_async_el(twi + idx, reinterpret_cast<const cx<R>*>(S.twr) + (size_t)r * N2 + k2);
     }
     load_ctl(S, cv);
-    if (cv.done) return;
+    if (cv.done) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
     if (threadIdx.x < S.npairs) {
         // FP32: pair p carries 2^(e_u + e_v - e_max) so that the sum stays in range.
+        // FP64: pc[0] is folded into the birth scale (spectral_pair).
         R c = (R)S.pcoef[threadIdx.x];
+        if (sizeof(R) == sizeof(double)) c = (R)(S.pcoef[threadIdx.x] / fold_coef(S));
         if (sizeof(R) == sizeof(float)) {
             int emax = -100000;
             for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, cv, S.pu[p]) + xexp<R>(S, cv, S.pv[p]));
@@ -557,8 +630,10 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
         const int col = idx >> S.lgN2;
         const int t = col >> 1, rho = col & 1;
         const int r = rho ? r1 : r0;
-        a[k2 * G + col] = Yin[(size_t)t * S.Mp + (size_t)r * N2 + k2];
+        cp_async_el(a + k2 * G + col, Yin + (size_t)t * S.Mp + (size_t)r * N2 + k2);
     }
+    cp_async_wait();
+    stage_tw_fix(twP, S.lgN2, S.lgMp);
     __syncthreads();
     cx<R>* Z = tile_fft<R, false>(a, b, S.lgN2, G, twP);
     cx<R>* Yo = (Z == a) ? b : a;  // packed inverse spectrum, [k2 * 2 + rho]
@@ -597,6 +672,29 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     }
 }
 
+// Epilogue inputs of the element pair (i, i + 1): the collision rates D_s = sum_t
+// delta_t W_t[s] (delta_t from the evaluation's scalars) and the stage input y_s.
+template <typename R>
+__device__ __forceinline__ void epi_inputs(const SysDev& S, const R* Wr, const R* yr, const double* yd, int i, R& D0,
+                                           R& D1, R& y0, R& y1) {
+    D0 = (R)0;
+    D1 = (R)0;
+    for (int t = 0; t < S.T; ++t) {
+        const R d = (R)__ldcg(S.rsc + t);
+        const typename vec2<R>::T w = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wr + (size_t)t * S.Mp + i));
+        D0 += d * w.x;
+        D1 += d * w.y;
+    }
+    if (yd) {
+        y0 = (R)yd[i];
+        y1 = (i + 1 < S.M) ? (R)yd[i + 1] : (R)0;
+    } else {
+        const typename vec2<R>::T yy = *reinterpret_cast<const typename vec2<R>::T*>(yr + i);
+        y0 = yy.x;
+        y1 = yy.y;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Kernel C: inverse column transforms of length N1 (only the first half of the
 // outputs is needed), then the epilogue: birth, death, shattering, monomer source,
@@ -609,7 +707,6 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ double red[33];
-    __shared__ R delta[MAXT];
     __shared__ double src_s, bscale_s, s1_s;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_desc(sysv, map, one, S);
@@ -620,17 +717,30 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     const int n2b = bx * G;
     stage_tw(twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
     load_ctl(S, cv);
-    if (cv.done) return;
+    if (cv.done) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
     const cx<R>* G2 = reinterpret_cast<const cx<R>*>(S.G2);
     const Div DG = mkdiv(G);
     for (int idx = threadIdx.x; idx < S.N1 * G; idx += blockDim.x) {
         int g, k1;
         divmod(DG, idx, k1, g);
-        a[idx] = G2[(size_t)k1 * S.N2 + n2b + g];
+        cp_async_el(a + idx, G2 + (size_t)k1 * S.N2 + n2b + g);
     }
     const R* yr = reinterpret_cast<const R*>(S.ybuf);
     const double* yd = in.direct ? reinterpret_cast<const double*>(resolve_terms<R>(in, S, cv).p[0]) : nullptr;
-    if (threadIdx.x < S.T) delta[threadIdx.x] = (R)__ldcg(S.rsc + threadIdx.x);
+    const R* Wr = reinterpret_cast<const R*>(S.W);
+    const int half = (S.N1 >> 1) * G;
+    // The epilogue inputs of this thread's first element pair (idx = threadIdx.x) are
+    // loaded before the transform, so that their latency overlaps it.
+    R pD0 = (R)0, pD1 = (R)0, py0 = (R)0, py1 = (R)0;
+    if (threadIdx.x < half) {
+        int g, n1;
+        divmod(DG, threadIdx.x, n1, g);
+        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
+        if (i < S.M) epi_inputs<R>(S, Wr, yr, yd, i, pD0, pD1, py0, py1);
+    }
     if (threadIdx.x == 0) {
         src_s = __ldcg(S.rsc + MAXT);
         s1_s = __ldcg(S.rsc + MAXT + 1);
@@ -640,14 +750,16 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
             for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, cv, S.pu[p]) + xexp<R>(S, cv, S.pv[p]));
         }
         bscale_s = S.bnorm * (double)pow2<float>(emax);
+        // FP64: the factors the spectral product left out, (1/2)^3 pc[0]
+        if (sizeof(R) == sizeof(double)) bscale_s *= 0.125 * fold_coef(S);
     }
+    cp_async_wait();
+    stage_tw_fix(twP, S.lgN1, S.lgMp);
     __syncthreads();
     cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, twP);
     const double hsc = eo.out_slot >= 0 ? cv.h * eo.hfac : 1.0;
     const R scale = (R)hsc, bscale = (R)bscale_s, lam1 = (R)(1.0 + S.lambda);
     const double src = src_s;
-    const int half = (S.N1 >> 1) * G;
-    const R* Wr = reinterpret_cast<const R*>(S.W);
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
     double sq = 0.0;
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
@@ -656,22 +768,8 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
         const int i = 2 * ((n1 << S.lgN2) + n2b + g);
         if (i >= S.M) continue;
         const cx<R> z = res[idx];
-        R D0 = (R)0, D1 = (R)0;
-        for (int t = 0; t < S.T; ++t) {
-            const typename vec2<R>::T w =
-                __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wr + (size_t)t * S.Mp + i));
-            D0 += delta[t] * w.x;
-            D1 += delta[t] * w.y;
-        }
-        R y0, y1;
-        if (yd) {
-            y0 = (R)yd[i];
-            y1 = (i + 1 < S.M) ? (R)yd[i + 1] : (R)0;
-        } else {
-            const typename vec2<R>::T yy = *reinterpret_cast<const typename vec2<R>::T*>(yr + i);
-            y0 = yy.x;
-            y1 = yy.y;
-        }
+        R D0 = pD0, D1 = pD1, y0 = py0, y1 = py1;
+        if (idx != (int)threadIdx.x) epi_inputs<R>(S, Wr, yr, yd, i, D0, D1, y0, y1);
         const R b0 = (i == 0) ? (R)0 : z.x * bscale;
         const R b1 = z.y * bscale;
         const R l0 = (i == 0) ? (R)(-(s1_s - src)) : lam1 * y0 * D0;

@@ -187,7 +187,7 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     // The control block must read "not done" and the weights must be zero beyond M:
     // both are rewritten on every call, since the array keeps the previous call's data.
     if (cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), st) != cudaSuccess) return SMOL_ECUDA;
-    k_static_setup<<<1, 256, 0, st>>>(d, dsys, mapC, N2 / G, mapB, N1 / 2);
+    k_static_setup<<<1, 256, 0, st>>>(d, dsys, mapC, N2 / G, mapB, N1 / 2 + 1);
     k_static_weights<<<256, 256, 0, st>>>(d_U, d_V, (int)M, Mp, R, (double*)(base + OFF_W));
     k_static_twiddles<<<64, 256, 0, st>>>(Mp, N1, N2, (double2*)(base + OFF_TW), (double2*)(base + OFF_TWC),
                                           (double2*)(base + OFF_TWR), (double2*)(base + OFF_TWS));
@@ -210,7 +210,7 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     SysDev none;
     memset(&none, 0, sizeof(none));
     k_fwd_cols<double><<<N2 / G, threads_for_s(N1 * G * T), sc, st>>>(dsys, mapC, none, in);
-    k_rows<double><<<N1 / 2, threads_for_s(N2 * 2 * T), sr, st>>>(dsys, mapB, none);
+    k_rows<double><<<N1 / 2 + 1, threads_for_s(N2 * 2 * T), sr, st>>>(dsys, mapB, none, in);
     k_inv_cols<double><<<N2 / G, threads_for_s(N1 * G), sc, st>>>(dsys, mapC, none, in, eo);
     return cudaGetLastError() == cudaSuccess ? SMOL_OK : SMOL_ECUDA;
 }
