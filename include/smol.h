@@ -93,6 +93,10 @@ extern "C" {
 #define SMOL_FLAG_NO_PDL_ROWS     4
 #define SMOL_FLAG_NO_PDL_INV_COLS 8
 #define SMOL_FLAG_NO_PDL_STEP     16
+/* Launch every evaluation's inverse column pass as its own kernel (by default it runs
+   in one kernel with the next evaluation's forward column pass, or with the attempt's
+   final combination). */
+#define SMOL_FLAG_NO_FUSE         32
 
 typedef struct smol_system smol_system;   /* opaque, created by smol_init_system */
 
@@ -200,7 +204,9 @@ int smol_integrate_finish(smol_system* sys, smol_stats* stats);
 #define SMOL_PROF_ROWS     1   /* row FFTs, spectral product sum, inverse row FFTs */
 #define SMOL_PROF_INV_COLS 2   /* inverse column FFTs and the right-hand-side epilogue */
 #define SMOL_PROF_STEP     3   /* RK combination, error norm and step control */
-#define SMOL_PROF_KINDS    4
+#define SMOL_PROF_INV_FWD  4   /* fused: inverse columns of one evaluation + forward columns of the next */
+#define SMOL_PROF_INV_STEP 5   /* fused: inverse columns of the last evaluation + combination and control */
+#define SMOL_PROF_KINDS    6
 
 /* Measurement aid: runs `reps` further attempts of the current run (between
  * smol_integrate_start and smol_integrate_finish) launched one kernel at a time with
@@ -217,7 +223,7 @@ int smol_profile_attempts(smol_system* sys, int32_t reps, double* kernel_ms, int
  *   - log2 N1 of the four-step split Mp = N1 N2: the rule's value and one either side;
  *   - columns per CTA of the column kernels: the rule's value and twice it;
  *   - launch mode: programmatic dependent launch for every kernel, for none, or for
- *     all but the forward column kernel.
+ *     all but the forward column kernel; fused column passes (default) or not.
  * Candidates whose shared memory does not fit are skipped. *opts is read as the base
  * options and receives the fastest schedule in fft_lgn1, fft_g and flags (its other
  * fields are unchanged); *us_per_attempt (may be NULL) that schedule's microseconds

@@ -93,6 +93,7 @@ SIGNATURES = {
 
 # option flags (smol_opts.flags)
 FLAG_NO_PDL, FLAG_NO_PDL_FWD_COLS, FLAG_NO_PDL_ROWS, FLAG_NO_PDL_INV_COLS, FLAG_NO_PDL_STEP = 1, 2, 4, 8, 16
+FLAG_NO_FUSE = 32
 SCHEDULE_KEYS = ("fft_lgn1", "fft_g", "flags")
 
 
@@ -397,7 +398,7 @@ class System:
         n, self._run = self._run, None
         return n, st.as_dict()
 
-    PROF_KINDS = ("fwd_cols", "rows", "inv_cols", "step")
+    PROF_KINDS = ("fwd_cols", "rows", "inv_cols", "step", "inv_fwd", "inv_step")
 
     def profile(self, reps: int = 20):
         """Per-kernel-class average durations (ms) and launch counts over `reps` attempts

@@ -81,7 +81,10 @@ size_t smem_cols(const Shape& s, int T) {
     const size_t inv = 2 * n * s.csz + (size_t)s.N1 * s.csz;
     return std::max(fwd, inv);
 }
-size_t smem_rows(const Shape& s, int T) { return 2 * (size_t)s.N2 * 2 * T * s.csz + 5 * (size_t)s.N2 * s.csz; }
+// (at least the scalar CTA's 4 MAXT + 1 doubles)
+size_t smem_rows(const Shape& s, int T) {
+    return std::max<size_t>(2 * (size_t)s.N2 * 2 * T * s.csz + 5 * (size_t)s.N2 * s.csz, (4 * MAXT + 1) * 8);
+}
 
 // Threads of a CTA whose passes cover `points` points: one per radix-8 butterfly,
 // between 32 and 256.
@@ -121,7 +124,7 @@ Layout make_layout(const Shape& s, int R, int log_cap) {
     L.half = take((size_t)s.Mp * 8);
     L.stateB = take((size_t)s.Mp * 8);
     L.mpart = take((size_t)Tm * s.N2 * 2 * 8);  // sized for G = 1 (G may shrink at init)
-    L.fpart = take((size_t)s.nfin * FPW * 8);
+    L.fpart = take((size_t)std::max(s.nfin, s.N2) * FPW * 8);  // finish CTAs or column CTAs
     L.sqpart = take((size_t)s.N2 * 8);
     L.aux = take((size_t)(MAXT + 1) * 8);
     L.rsc = take((size_t)(MAXT + 2) * 8);
@@ -310,14 +313,16 @@ bool carve(K k) {
 
 template <typename R>
 int set_smem_attrs(const Engine* E) {
-    if (cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemC) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemC) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smemB) != cudaSuccess)
+    const int sc = (int)E->smemC, sb = (int)E->smemB;
+    const auto dyn = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(k_fwd_cols<R>, dyn, sc) != cudaSuccess ||
+        cudaFuncSetAttribute(k_inv_cols<R>, dyn, sc) != cudaSuccess ||
+        cudaFuncSetAttribute(k_inv_fwd<R>, dyn, sc) != cudaSuccess ||
+        cudaFuncSetAttribute(k_inv_finish<R>, dyn, sc) != cudaSuccess ||
+        cudaFuncSetAttribute(k_rows<R>, dyn, sb) != cudaSuccess)
         return SMOL_ECUDA;
-    if (!(carve(k_fwd_cols<R>) && carve(k_rows<R>) && carve(k_inv_cols<R>) && carve(k_finish<R>) &&
-          carve(k_lincomb<R>)))
+    if (!(carve(k_fwd_cols<R>) && carve(k_rows<R>) && carve(k_inv_cols<R>) && carve(k_inv_fwd<R>) &&
+          carve(k_inv_finish<R>) && carve(k_finish<R>) && carve(k_lincomb<R>)))
         return SMOL_ECUDA;
     return SMOL_OK;
 }
@@ -382,6 +387,65 @@ void launch_eval(const Engine* E, const LaunchArgs& A, const StageIn& in, const 
     }
 }
 
+// Emits the kernels of an attempt. Consecutive evaluations share a column kernel: the
+// inverse pass of one and the forward pass of the next run in k_inv_fwd, and the last
+// inverse pass runs with the final combination in k_inv_finish (unless the options
+// disable fusion). A half-step combination (k_lincomb) between two evaluations ends a
+// fused chain.
+template <typename R>
+struct Seq {
+    const Engine* E;
+    LaunchArgs A;
+    cudaStream_t st;
+    Prof* pr;
+    bool fuse;
+    bool pending = false;  // an evaluation whose inverse pass is not yet launched
+    StageIn pin;
+    EpiOut peo;
+
+    void eval(const StageIn& in, const EpiOut& eo) {
+        if (pending && fuse) {
+            ProfScope ps(pr, st, SMOL_PROF_INV_FWD);
+            launch(E, SMOL_PROF_INV_COLS, k_inv_fwd<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, pin, peo,
+                   in);
+        } else {
+            flush();
+            ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
+            launch(E, SMOL_PROF_FWD_COLS, k_fwd_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, in);
+        }
+        {
+            ProfScope ps(pr, st, SMOL_PROF_ROWS);
+            launch(E, SMOL_PROF_ROWS, k_rows<R>, E->H.nB, E->thrB, E->smemB, st, A.sys, A.mapB, A.one, in);
+        }
+        pending = true;
+        pin = in;
+        peo = eo;
+    }
+    void finish(const Comb2& c, const CtlParams& P) {
+        if (pending && fuse) {
+            ProfScope ps(pr, st, SMOL_PROF_INV_STEP);
+            launch(E, SMOL_PROF_STEP, k_inv_finish<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, pin, peo,
+                   c, P);
+            pending = false;
+            return;
+        }
+        flush();
+        ProfScope ps(pr, st, SMOL_PROF_STEP);
+        launch(E, SMOL_PROF_STEP, k_finish<R>, E->H.nF, FIN_THREADS, 0, st, A.sys, A.mapF, A.one, c, P);
+    }
+    void lincomb(const StageIn& in) {
+        flush();
+        ProfScope ps(pr, st, SMOL_PROF_STEP);
+        launch(E, SMOL_PROF_STEP, k_lincomb<R>, E->H.nF, FIN_THREADS, 0, st, A.sys, A.mapF, A.one, in);
+    }
+    void flush() {
+        if (!pending) return;
+        ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
+        launch(E, SMOL_PROF_INV_COLS, k_inv_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, pin, peo);
+        pending = false;
+    }
+};
+
 // Union of the candidate and error combinations of the final kernel.
 Comb2 comb2(const StageIn& cand, const StageIn& del) {
     Comb2 c;
@@ -433,21 +497,20 @@ EpiOut epi_k(int slot, double hfac, int sq) {
 // Enqueues one step attempt of every system of the batch on stream st.
 template <typename R>
 void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
-    const LaunchArgs A = args_for(E, false);
+    Seq<R> q;
+    q.E = E;
+    q.A = args_for(E, false);
+    q.st = st;
+    q.pr = pr;
+    q.fuse = !(E->o.flags & SMOL_FLAG_NO_FUSE);
     auto Ev = [&](StageIn in, int k, double hfac, bool first) {
         if (sizeof(R) == sizeof(float))
             for (int j = 0; j < in.nv; ++j)
                 if (in.slot[j] == SLOT_CUR) in.slot[j] = SLOT_CURF;
-        launch_eval<R>(E, A, in, epi_k(k, hfac, (first && P.steady) ? 1 : 0), st, pr);
+        q.eval(in, epi_k(k, hfac, (first && P.steady) ? 1 : 0));
     };
-    auto finish = [&](const StageIn& cand, const StageIn& del) {
-        ProfScope ps(pr, st, SMOL_PROF_STEP);
-        launch(E, SMOL_PROF_STEP, k_finish<R>, E->H.nF, FIN_THREADS, 0, st, A.sys, A.mapF, A.one, comb2(cand, del), P);
-    };
-    auto half = [&](const StageIn& in) {
-        ProfScope ps(pr, st, SMOL_PROF_STEP);
-        launch(E, SMOL_PROF_STEP, k_lincomb<R>, E->H.nF, FIN_THREADS, 0, st, A.sys, A.mapF, A.one, in);
-    };
+    auto finish = [&](const StageIn& cand, const StageIn& del) { q.finish(comb2(cand, del), P); };
+    auto half = [&](const StageIn& in) { q.lincomb(in); };
     const int N = SLOT_CUR, H = SLOT_HALF;
     if (scheme == SCHEME_RKF45) {
         Ev(stage({{N, 1.0}}), 0, 1.0, true);
@@ -1091,10 +1154,11 @@ double time_attempts(Engine* E, double* const* d_work, const double* const* d_n0
     return us;
 }
 
-// Programmatic-launch masks the tuner tries.
-constexpr int TUNE_FLAGS[] = {0, SMOL_FLAG_NO_PDL, SMOL_FLAG_NO_PDL_FWD_COLS};
+// Launch modes the tuner tries (programmatic launch, fusion of the column passes).
+constexpr int TUNE_FLAGS[] = {0, SMOL_FLAG_NO_PDL, SMOL_FLAG_NO_PDL_FWD_COLS, SMOL_FLAG_NO_FUSE,
+                              SMOL_FLAG_NO_FUSE | SMOL_FLAG_NO_PDL};
 constexpr int PDL_BITS = SMOL_FLAG_NO_PDL | SMOL_FLAG_NO_PDL_FWD_COLS | SMOL_FLAG_NO_PDL_ROWS |
-                         SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP;
+                         SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP | SMOL_FLAG_NO_FUSE;
 
 }  // namespace
 

@@ -211,123 +211,117 @@ struct Comb2 {
     float ch[MAXV], cl[MAXV], dh[MAXV], dl[MAXV];  // c and d split into float pairs
 };
 
-// Final kernel of an attempt: candidate = sum c_j v_j (FP64) written to the other state
-// buffer, error vector sum d_j v_j (FP64) reduced to ||.||_2^2, and ||candidate||^2,
-// max|candidate|, sum_s s candidate_s; the last CTA of each system reduces the partials
-// in a fixed order and runs that system's controller (accept / reject, t, tau,
-// counters, log, termination).
+// Per-thread accumulators of the final combination: ||error||^2, ||candidate||^2 and
+// sum_s s candidate_s (FP64), max |candidate| as the bit pattern of a non-negative
+// double (integer max is monotone on those, and a NaN or infinity pattern is at least
+// INF_BITS, which marks a non-finite candidate); the FP32 form keeps its norms, max and
+// finite test in FP32 until fin_acc_close.
+struct FinAcc {
+    double se, sc, ms;
+    unsigned long long mxb;
+    float fse, fsc, fmx;
+    bool fbad;
+};
+__device__ __forceinline__ FinAcc fin_acc() {
+    FinAcc a;
+    a.se = a.sc = a.ms = 0.0;
+    a.mxb = 0ull;
+    a.fse = a.fsc = a.fmx = 0.f;
+    a.fbad = false;
+    return a;
+}
 template <typename R>
-__global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                   const __grid_constant__ SysDev one, const Comb2 cd,
-                                                   const CtlParams P) {
-    __shared__ __align__(16) SysDev S;
-    __shared__ CtlView cv;
-    __shared__ double wred[4][8];
-    __shared__ unsigned long long xred[8];
-    __shared__ bool last;
-    __shared__ __align__(16) Ctl cs;
-    constexpr int CW = (int)(sizeof(Ctl) / 4);
-    const int blk = load_sys(sysv, map, one, S, cv);
-    Ctl* ctl = S.ctl;
-    if (cv.done) return;
-    // The control block is copied into shared memory now (no kernel writes it while this
-    // one runs): the last CTA runs the controller on that copy, off global memory.
-    for (int q = threadIdx.x; q < CW; q += blockDim.x)
-        reinterpret_cast<int*>(&cs)[q] = __ldcg(reinterpret_cast<const int*>(ctl) + q);
-    double* outp = const_cast<double*>(cv.cur ? cv.s0 : cv.s1);
-    // max |candidate| as the bit pattern of a non-negative double (integer max is
-    // monotone on those, and a NaN or infinity pattern is at least INF_BITS, which marks
-    // a non-finite candidate)
-    double se = 0.0, sc = 0.0, ms = 0.0;
-    unsigned long long mxb = 0ull;
-    const int np = (S.M + 1) >> 1;
+__device__ __forceinline__ void fin_acc_close(FinAcc& a) {
+    if (sizeof(R) == sizeof(float)) {
+        a.se = (double)a.fse;
+        a.sc = (double)a.fsc;
+        a.mxb = a.fbad ? INF_BITS : absbits((double)a.fmx);
+    }
+}
+
+// Final combination at the element pair (i, i + 1) (i even): candidate = sum c_j v_j
+// (FP64) written to the other state buffer (and, FP32 form, its FP32 shadow), error
+// vector sum d_j v_j reduced into the accumulators. Terms are read from L2 (a fused
+// kernel reads the stage vector it has just written).
+template <typename R>
+__device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const Terms<R>& tp, double* outp,
+                                         float* shad, int i, FinAcc& a) {
     const StageIn& in = cd.in;
-    const Terms<R> tp = resolve_terms<R>(in, S, cv, false);
+    const int p = i >> 1;
+    const bool two = i + 1 < S.M;
     if constexpr (sizeof(R) == sizeof(float)) {
         // FP32 form: the FP32 stage terms are combined in double-float arithmetic, the FP64
         // terms (state, half-step state) in FP64; FP64 is used only for those terms, the
         // candidate's final sum and the mass moment. Norms, max and the finite test work
         // on the FP32 image of the candidate, which also becomes the next state's shadow.
-        float* shad = reinterpret_cast<float*>(cv.cur ? S.shadow0 : S.shadow1);
-        float fse = 0.f, fsc = 0.f, fmx = 0.f;
-        bool fbad = false;
-        for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
-            const int i = 2 * p;
-            const bool two = i + 1 < S.M;
-            DF c0 = {0.f, 0.f}, c1 = {0.f, 0.f}, d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
-            double b0 = 0.0, b1 = 0.0, e0 = 0.0, e1 = 0.0;
+        DF c0 = {0.f, 0.f}, c1 = {0.f, 0.f}, d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
+        double b0 = 0.0, b1 = 0.0, e0 = 0.0, e1 = 0.0;
 #pragma unroll
-            for (int j = 0; j < MAXV; ++j)
-                if (j < in.nv) {
-                    if ((tp.dmask >> j) & 1u) {
-                        const double* v = reinterpret_cast<const double*>(tp.p[j]);
-                        const double v0 = __ldg(v + i), v1 = two ? __ldg(v + i + 1) : 0.0;
-                        b0 += in.c[j] * v0;
-                        b1 += in.c[j] * v1;
-                        if (cd.d[j] != 0.0) {
-                            e0 += cd.d[j] * v0;
-                            e1 += cd.d[j] * v1;
-                        }
-                    } else {
-                        const float* v = reinterpret_cast<const float*>(tp.p[j]);
-                        float v0, v1;
-                        if (two) {
-                            const float2 w = __ldg(reinterpret_cast<const float2*>(v) + p);
-                            v0 = w.x;
-                            v1 = w.y;
-                        } else {
-                            v0 = __ldg(v + i);
-                            v1 = 0.f;
-                        }
-                        df_fma(c0, cd.ch[j], cd.cl[j], v0);
-                        df_fma(c1, cd.ch[j], cd.cl[j], v1);
-                        df_fma(d0, cd.dh[j], cd.dl[j], v0);
-                        df_fma(d1, cd.dh[j], cd.dl[j], v1);
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) {
+                if ((tp.dmask >> j) & 1u) {
+                    const double* v = reinterpret_cast<const double*>(tp.p[j]);
+                    const double v0 = __ldcg(v + i), v1 = two ? __ldcg(v + i + 1) : 0.0;
+                    b0 += in.c[j] * v0;
+                    b1 += in.c[j] * v1;
+                    if (cd.d[j] != 0.0) {
+                        e0 += cd.d[j] * v0;
+                        e1 += cd.d[j] * v1;
                     }
+                } else {
+                    const float* v = reinterpret_cast<const float*>(tp.p[j]);
+                    float v0, v1;
+                    if (two) {
+                        const float2 w = __ldcg(reinterpret_cast<const float2*>(v) + p);
+                        v0 = w.x;
+                        v1 = w.y;
+                    } else {
+                        v0 = __ldcg(v + i);
+                        v1 = 0.f;
+                    }
+                    df_fma(c0, cd.ch[j], cd.cl[j], v0);
+                    df_fma(c1, cd.ch[j], cd.cl[j], v1);
+                    df_fma(d0, cd.dh[j], cd.dl[j], v0);
+                    df_fma(d1, cd.dh[j], cd.dl[j], v1);
                 }
-            const double y0 = b0 + df_value(c0), y1 = b1 + df_value(c1);
-            // error: the FP64 part only where FP64 terms enter it (step doubling)
-            float q0, q1;
-            if (e0 != 0.0 || e1 != 0.0) {
-                q0 = (float)(e0 + df_value(d0));
-                q1 = (float)(e1 + df_value(d1));
-            } else {
-                q0 = d0.hi + d0.lo;
-                q1 = d1.hi + d1.lo;
             }
-            fse += q0 * q0 + q1 * q1;
-            const float f0 = (float)y0, f1 = (float)y1;
-            if (two) {
-                *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
-                *reinterpret_cast<float2*>(shad + i) = make_float2(f0, f1);
-                ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
-            } else {
-                outp[i] = y0;
-                shad[i] = f0;
-                ms += (double)(i + 1) * y0;
-            }
-            fsc += f0 * f0 + f1 * f1;
-            fmx = fmaxf(fmx, fmaxf(fabsf(f0), fabsf(f1)));
-            fbad = fbad || !isfinite(f0) || !isfinite(f1);
+        const double y0 = b0 + df_value(c0), y1 = b1 + df_value(c1);
+        // error: the FP64 part only where FP64 terms enter it (step doubling)
+        float q0, q1;
+        if (e0 != 0.0 || e1 != 0.0) {
+            q0 = (float)(e0 + df_value(d0));
+            q1 = (float)(e1 + df_value(d1));
+        } else {
+            q0 = d0.hi + d0.lo;
+            q1 = d1.hi + d1.lo;
         }
-        se = (double)fse;
-        sc = (double)fsc;
-        mxb = fbad ? INF_BITS : absbits((double)fmx);
+        a.fse += q0 * q0 + q1 * q1;
+        const float f0 = (float)y0, f1 = (float)y1;
+        if (two) {
+            *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
+            *reinterpret_cast<float2*>(shad + i) = make_float2(f0, f1);
+            a.ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
+        } else {
+            outp[i] = y0;
+            shad[i] = f0;
+            a.ms += (double)(i + 1) * y0;
+        }
+        a.fsc += f0 * f0 + f1 * f1;
+        a.fmx = fmaxf(a.fmx, fmaxf(fabsf(f0), fabsf(f1)));
+        a.fbad = a.fbad || !isfinite(f0) || !isfinite(f1);
     } else {
-    for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x) {
-        const int i = 2 * p;
         double y0 = 0.0, y1 = 0.0, d0 = 0.0, d1 = 0.0;
-        if (i + 1 < S.M) {
+        if (two) {
             double v0[MAXV], v1[MAXV];
 #pragma unroll
             for (int j = 0; j < MAXV; ++j)
                 if (j < in.nv) {
                     if ((tp.dmask >> j) & 1u) {
-                        const double2 v = __ldg(reinterpret_cast<const double2*>(tp.p[j]) + p);
+                        const double2 v = __ldcg(reinterpret_cast<const double2*>(tp.p[j]) + p);
                         v0[j] = v.x;
                         v1[j] = v.y;
                     } else {
-                        const typename vec2<R>::T v = __ldg(reinterpret_cast<const typename vec2<R>::T*>(tp.p[j]) + p);
+                        const typename vec2<R>::T v = __ldcg(reinterpret_cast<const typename vec2<R>::T*>(tp.p[j]) + p);
                         v0[j] = (double)v.x;
                         v1[j] = (double)v.y;
                     }
@@ -345,20 +339,39 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
 #pragma unroll
             for (int j = 0; j < MAXV; ++j)
                 if (j < in.nv) {
-                    const double v = ((tp.dmask >> j) & 1u) ? __ldg(reinterpret_cast<const double*>(tp.p[j]) + i)
-                                                            : (double)__ldg(reinterpret_cast<const R*>(tp.p[j]) + i);
+                    const double v = ((tp.dmask >> j) & 1u) ? __ldcg(reinterpret_cast<const double*>(tp.p[j]) + i)
+                                                            : (double)__ldcg(reinterpret_cast<const R*>(tp.p[j]) + i);
                     y0 += in.c[j] * v;
                     d0 += cd.d[j] * v;
                 }
             outp[i] = y0;
         }
-        se += d0 * d0 + d1 * d1;
-        sc += y0 * y0 + y1 * y1;
-        ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
-        mxb = max(mxb, max(absbits(y0), absbits(y1)));
+        a.se += d0 * d0 + d1 * d1;
+        a.sc += y0 * y0 + y1 * y1;
+        a.ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
+        a.mxb = max(a.mxb, max(absbits(y0), absbits(y1)));
     }
-    }
-    // one fused warp-level reduction of the partials, then one pass over the warps
+}
+
+// Shared memory of fin_tail.
+struct FinSm {
+    double wred[4][8];
+    unsigned long long xred[8];
+    bool last;
+};
+
+// End of an attempt, after every thread of the CTA has accumulated its elements: the
+// CTA's partials are written to slot blk of nblk; the last CTA of the system reduces
+// them in a fixed order (thread j takes partials j, j + blockDim, ...; then one fused
+// tree over the block) and runs the controller (thread 0) and the error norm (thread
+// 32) on the shared copy cs of the control block, which it then writes back.
+template <typename R>
+__device__ __forceinline__ void fin_tail(const SysDev& S, const CtlParams& P, Ctl* ctl, Ctl& cs, int blk, int nblk,
+                                         FinAcc acc, FinSm& f) {
+    constexpr int CW = (int)(sizeof(Ctl) / 4);
+    fin_acc_close<R>(acc);
+    double se = acc.se, sc = acc.sc, ms = acc.ms;
+    unsigned long long mxb = acc.mxb;
     for (int o = 16; o > 0; o >>= 1) {
         se += __shfl_down_sync(0xffffffffu, se, o);
         sc += __shfl_down_sync(0xffffffffu, sc, o);
@@ -367,37 +380,31 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) {
-        wred[0][warp] = se;
-        wred[1][warp] = sc;
-        wred[2][warp] = ms;
-        xred[warp] = mxb;
+        f.wred[0][warp] = se;
+        f.wred[1][warp] = sc;
+        f.wred[2][warp] = ms;
+        f.xred[warp] = mxb;
     }
     __syncthreads();
     if (threadIdx.x < 4) {
         const int q = threadIdx.x;
         double v = 0.0;
         if (q == 2) {
-            unsigned long long x = xred[0];
-            for (int w = 1; w < nw; ++w) x = max(x, xred[w]);
+            unsigned long long x = f.xred[0];
+            for (int w = 1; w < nw; ++w) x = max(x, f.xred[w]);
             v = __longlong_as_double((long long)x);
-        } else if (q < 2) {
-            v = wred[q][0];
-            for (int w = 1; w < nw; ++w) v += wred[q][w];
         } else {
-            v = wred[2][0];
-            for (int w = 1; w < nw; ++w) v += wred[2][w];
+            const int r = q < 2 ? q : 2;
+            v = f.wred[r][0];
+            for (int w = 1; w < nw; ++w) v += f.wred[r][w];
         }
         S.fpart[FPW * blk + (q == 3 ? 4 : q)] = v;  // E, C, max bits, -, mass moment
     }
-    if (!arrive_last(ctl, S.nfin, &last)) return;
-    // The last CTA reduces the per-CTA partials with all its threads (thread j takes
-    // partials j, j + blockDim, ...; then one fused tree over the block) and runs the
-    // controller (thread 0) and the error norm (thread 32) on the shared copy of the
-    // control block, which it then writes back.
+    if (!arrive_last(ctl, nblk, &f.last)) return;
     double E = 0.0, C = 0.0, Q = 0.0, MS = 0.0;
     unsigned long long XB = 0ull;
 #pragma unroll 4
-    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         const double* q = S.fpart + FPW * b;
         E += __ldcg(q);
         C += __ldcg(q + 1);
@@ -417,22 +424,22 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     const int64_t att0 = cs.attempts;
     __syncthreads();  // wred / xred reuse
     if (lane == 0) {
-        wred[0][warp] = E;
-        wred[1][warp] = C;
-        wred[2][warp] = MS;
-        wred[3][warp] = Q;
-        xred[warp] = XB;
+        f.wred[0][warp] = E;
+        f.wred[1][warp] = C;
+        f.wred[2][warp] = MS;
+        f.wred[3][warp] = Q;
+        f.xred[warp] = XB;
     }
     __syncthreads();
     const int t2 = blockDim.x > 32 ? 32 : 0;
     if (threadIdx.x == 0 || threadIdx.x == t2) {
-        E = wred[0][0], C = wred[1][0], MS = wred[2][0], Q = wred[3][0], XB = xred[0];
+        E = f.wred[0][0], C = f.wred[1][0], MS = f.wred[2][0], Q = f.wred[3][0], XB = f.xred[0];
         for (int w = 1; w < nw; ++w) {
-            E += wred[0][w];
-            C += wred[1][w];
-            MS += wred[2][w];
-            Q += wred[3][w];
-            XB = max(XB, xred[w]);
+            E += f.wred[0][w];
+            C += f.wred[1][w];
+            MS += f.wred[2][w];
+            Q += f.wred[3][w];
+            XB = max(XB, f.xred[w]);
         }
         const bool bad = XB >= INF_BITS;
         if (threadIdx.x == t2) error_norm(P, S, cs, nrm2_0, att0, E, bad, Q);
@@ -441,6 +448,74 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     __syncthreads();
     for (int q = threadIdx.x; q < CW; q += blockDim.x)
         reinterpret_cast<int*>(ctl)[q] = reinterpret_cast<const int*>(&cs)[q];
+}
+
+// Copies the control block into shared memory (no kernel writes it while an attempt's
+// final kernel runs): the last CTA runs the controller on that copy, off global memory.
+__device__ __forceinline__ void copy_ctl(const Ctl* ctl, Ctl& cs) {
+    constexpr int CW = (int)(sizeof(Ctl) / 4);
+    for (int q = threadIdx.x; q < CW; q += blockDim.x)
+        reinterpret_cast<int*>(&cs)[q] = __ldcg(reinterpret_cast<const int*>(ctl) + q);
+}
+
+// Final kernel of an attempt: the combination over all element pairs of each system
+// (CTA blk of nfin takes pairs blk * blockDim + tid, + nfin * blockDim, ...), then
+// fin_tail (error norm, candidate norms, controller).
+template <typename R>
+__global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                   const __grid_constant__ SysDev one, const Comb2 cd,
+                                                   const CtlParams P) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ FinSm f;
+    __shared__ __align__(16) Ctl cs;
+    const int blk = load_sys(sysv, map, one, S, cv);
+    if (cv.done) return;
+    copy_ctl(S.ctl, cs);
+    double* outp = const_cast<double*>(cv.cur ? cv.s0 : cv.s1);
+    float* shad = reinterpret_cast<float*>(cv.cur ? S.shadow0 : S.shadow1);
+    const Terms<R> tp = resolve_terms<R>(cd.in, S, cv, false);
+    FinAcc acc = fin_acc();
+    const int np = (S.M + 1) >> 1;
+    for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x)
+        fin_pair<R>(S, cd, tp, outp, shad, 2 * p, acc);
+    fin_tail<R>(S, P, S.ctl, cs, blk, S.nfin, acc, f);
+}
+
+// The last inverse pass of an attempt fused with the final combination: each column
+// CTA combines the element pairs whose stage vector it has just formed, then fin_tail
+// over the nbx column CTAs of the system.
+template <typename R>
+__global__ void __launch_bounds__(256) k_inv_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                    const __grid_constant__ SysDev one, const StageIn in,
+                                                    const EpiOut eo, const Comb2 cd, const CtlParams P) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ double sm[36];
+    __shared__ FinSm f;
+    __shared__ __align__(16) Ctl cs;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int bx = load_desc(sysv, map, one, S);
+    const ColSm<R> m = col_sm<R>(S, smraw);
+    stage_tw(m.twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
+    load_ctl(S, cv);
+    if (cv.done) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
+    copy_ctl(S.ctl, cs);
+    inv_body<R>(S, cv, in, eo, bx, m, sm);
+    double* outp = const_cast<double*>(cv.cur ? cv.s0 : cv.s1);
+    float* shad = reinterpret_cast<float*>(cv.cur ? S.shadow0 : S.shadow1);
+    const Terms<R> tp = resolve_terms<R>(cd.in, S, cv, false);
+    FinAcc acc = fin_acc();
+    const Div DG = mkdiv(S.G);
+    const int half = (S.N1 >> 1) * S.G;
+    for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
+        const int i = col_elem(S, DG, bx, idx);
+        if (i < S.M) fin_pair<R>(S, cd, tp, outp, shad, i, acc);
+    }
+    fin_tail<R>(S, P, S.ctl, cs, bx, S.nbx, acc, f);
 }
 
 // Preparation of an integration, pass 1: moments mu_t of n0, ||n0||^2, max|n0| and

@@ -186,7 +186,8 @@ struct vec2<float> {
 
 // Stage input at indices i, i+1 (i even), accumulated in type A: zero at and beyond M.
 // All term loads are issued before the first multiply-add so that their latencies
-// overlap.
+// overlap. The loads go to L2 (coherent): a fused kernel reads stage vectors that it
+// wrote itself.
 template <typename A, typename R>
 __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P, int M, int i, A& y0, A& y1) {
     y0 = (A)0;
@@ -197,11 +198,11 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
         for (int j = 0; j < MAXV; ++j)
             if (j < in.nv) {
                 if ((P.dmask >> j) & 1u) {
-                    const double2 v = __ldg(reinterpret_cast<const double2*>(P.p[j]) + (i >> 1));
+                    const double2 v = __ldcg(reinterpret_cast<const double2*>(P.p[j]) + (i >> 1));
                     v0[j] = (A)v.x;
                     v1[j] = (A)v.y;
                 } else {
-                    const typename vec2<R>::T v = __ldg(reinterpret_cast<const typename vec2<R>::T*>(P.p[j]) + (i >> 1));
+                    const typename vec2<R>::T v = __ldcg(reinterpret_cast<const typename vec2<R>::T*>(P.p[j]) + (i >> 1));
                     v0[j] = (A)v.x;
                     v1[j] = (A)v.y;
                 }
@@ -217,8 +218,8 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
 #pragma unroll
         for (int j = 0; j < MAXV; ++j)
             if (j < in.nv) {
-                const A v = ((P.dmask >> j) & 1u) ? (A)__ldg(reinterpret_cast<const double*>(P.p[j]) + i)
-                                                  : (A)__ldg(reinterpret_cast<const R*>(P.p[j]) + i);
+                const A v = ((P.dmask >> j) & 1u) ? (A)__ldcg(reinterpret_cast<const double*>(P.p[j]) + i)
+                                                  : (A)__ldcg(reinterpret_cast<const R*>(P.p[j]) + i);
                 y0 += (A)in.c[j] * v;
             }
     }
@@ -271,16 +272,31 @@ __device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
     return *flag;
 }
 
-// Scalars of one evaluation from the column-pass moment partials (one CTA, after all
-// partials are written; *y1p = y_1 in FP64, read after the first barrier): mu_t, nu_t
-// summed over the columns in a fixed order, then
+// Scalars of one evaluation (the scalar CTA of the row kernel): y_1 in FP64, the
+// moments mu_t, nu_t summed over the column CTAs' partials in a fixed order, then
 //   delta_t = sum_{alpha: u=t} coef_alpha mu_{v(alpha)}   (death: D_s = sum_t delta_t W_t[s])
 //   source  = lambda/2 sum coef (rho_u sigma_v + sigma_u rho_v) + lambda y_1 sum coef W_u[1] rho_v
 //   S_1     = -y_1 D_1 + source  (FP64: its two terms nearly cancel)
-// with sigma_t = mu_t - W_t[1] y_1, rho_t = nu_t - W_t[1] y_1.
+// with sigma_t = mu_t - W_t[1] y_1, rho_t = nu_t - W_t[1] y_1. All loads (partials and
+// the stage-input terms at s = 1) are issued together; sh: >= 4 MAXT + 1 doubles of
+// shared memory, sh[3 MAXT + t] = W_t[1] staged by the caller before its wait.
 template <typename R>
-__device__ void finalize_scalars(const SysDev& S, const double* y1p, double* mom) {
+__device__ void finalize_scalars(const SysDev& S, const CtlView& cv, const StageIn& in, double* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double* mom = sh;                  // [2 MAXT]
+    double* w1s = sh + 3 * MAXT;       // [MAXT]
+    double* y1p = sh + 4 * MAXT;       // [1]
+    // y_1 in FP64 (from the FP64 state, not an FP32 shadow): lane j of warp 0 loads term j
+    if (warp == 0) {
+        const Terms<R> P = resolve_terms<R>(in, S, cv, false);
+        double v = 0.0;
+        if (lane < in.nv)
+            v = ((P.dmask >> lane) & 1u) ? __ldg(reinterpret_cast<const double*>(P.p[lane]))
+                                         : (double)__ldg(reinterpret_cast<const R*>(P.p[lane]));
+        double y1 = 0.0;
+        for (int j = 0; j < in.nv; ++j) y1 += in.c[j] * __shfl_sync(0xffffffffu, v, j);
+        if (lane == 0) *y1p = y1;
+    }
     for (int q = warp; q < 2 * S.T; q += nw) {
         const int t = q >> 1, which = q & 1;
         double v = 0.0;
@@ -291,27 +307,22 @@ __device__ void finalize_scalars(const SysDev& S, const double* y1p, double* mom
     __syncthreads();
     if (threadIdx.x != 0) return;
     const double y1 = *y1p;
-    const R* Wr = reinterpret_cast<const R*>(S.W);
-    double sig[MAXT], rho[MAXT], del[MAXT], w1s[MAXT];
-    for (int t = 0; t < S.T; ++t) {
-        const double w1 = (double)Wr[(size_t)t * S.Mp];
-        w1s[t] = w1;
-        sig[t] = mom[2 * t] - w1 * y1;
-        rho[t] = mom[2 * t + 1] - w1 * y1;
-        del[t] = 0.0;
-    }
     double shat = 0.0, mono = 0.0;
     for (int al = 0; al < S.R; ++al) {
         const int u = S.au[al], v = S.av[al];
         const double c = S.acoef[al];
-        del[u] += c * mom[2 * v];
-        shat += c * (rho[u] * sig[v] + sig[u] * rho[v]);
-        mono += c * w1s[u] * rho[v];
+        const double su = mom[2 * u] - w1s[u] * y1, ru = mom[2 * u + 1] - w1s[u] * y1;
+        const double sv = mom[2 * v] - w1s[v] * y1, rv = mom[2 * v + 1] - w1s[v] * y1;
+        shat += c * (ru * sv + su * rv);
+        mono += c * w1s[u] * rv;
     }
     double D1 = 0.0;
     for (int t = 0; t < S.T; ++t) {
-        S.rsc[t] = del[t];
-        D1 += del[t] * w1s[t];
+        double del = 0.0;
+        for (int al = 0; al < S.R; ++al)
+            if (S.au[al] == t) del += S.acoef[al] * mom[2 * S.av[al]];
+        S.rsc[t] = del;
+        D1 += del * w1s[t];
     }
     const double src = 0.5 * S.lambda * shat + S.lambda * y1 * mono;
     S.rsc[MAXT] = src;
@@ -378,63 +389,83 @@ __device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const i
 }
 
 // ---------------------------------------------------------------------------
-// Kernel A: stage input y (computed once per element), moments, and the column
-// transforms of length N1 of all T inputs x_t = W_t . y, interleaved in one tile
-// transform over T*G sequences. One CTA per G adjacent columns n2 of one system.
-// Shared memory: a, b (N1*G*T complex each), the tile twiddles W_N1^e (N1), the
-// four-step twiddles W_Mp^{n2 k1} of the CTA's columns (N1*G), y (N1*G reals).
+// Column CTAs. One CTA per G adjacent columns n2 of one system; the forward pass
+// (stage input, moments, column transforms of length N1) and the inverse pass (inverse
+// column transforms and the right-hand-side epilogue) touch the same elements
+// i = 2 (n1 N2 + n2), n1 < N1 / 2, with the same thread per element pair, so the
+// inverse pass of one stage and the forward pass of the next can run in one kernel.
+// Shared memory (forward layout; the inverse pass uses the first N1 G entries of a and
+// b): a, b (N1 G T complex each), the tile twiddles W_N1^e (N1), the four-step
+// twiddles W_Mp^{n2 k1} of the CTA's columns (N1 G), y (N1 G reals).
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                  const __grid_constant__ SysDev one, const StageIn in) {
-    __shared__ __align__(16) SysDev S;
-    __shared__ CtlView cv;
-    __shared__ double red[2 * MAXT][8];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int bx = load_desc(sysv, map, one, S);
+struct ColSm {
+    cx<R>* a;
+    cx<R>* b;
+    cx<R>* twP;
+    cx<R>* tw4;
+    R* ys;
+};
+template <typename R>
+__device__ __forceinline__ ColSm<R> col_sm(const SysDev& S, unsigned char* raw) {
+    ColSm<R> m;
+    const int n = S.N1 * S.G * S.T;
+    m.a = reinterpret_cast<cx<R>*>(raw);
+    m.b = m.a + n;
+    m.twP = m.b + n;
+    m.tw4 = m.twP + S.N1;
+    m.ys = reinterpret_cast<R*>(m.tw4 + S.N1 * S.G);
+    return m;
+}
+
+// Element index of pair idx of column CTA bx.
+__device__ __forceinline__ int col_elem(const SysDev& S, const Div& DG, int bx, int idx) {
+    int g, n1;
+    divmod(DG, idx, n1, g);
+    return 2 * ((n1 << S.lgN2) + bx * S.G + g);
+}
+
+// Forward prologue (constant data, before the wait for the previous kernel): the
+// four-step twiddles of the CTA's columns (asynchronous copies) and the weights of
+// the thread's first element pair for the first WPRE transforms.
+template <typename R>
+__device__ __forceinline__ void fwd_prologue(const SysDev& S, int bx, const ColSm<R>& m,
+                                             typename vec2<R>::T (&wpre)[WPRE]) {
+    const int G = S.G, N1 = S.N1;
+    const cx<R>* twc = reinterpret_cast<const cx<R>*>(S.twc);
+    for (int idx = threadIdx.x; idx < N1 * G; idx += blockDim.x) {
+        const int k1 = idx & (N1 - 1), g = idx >> S.lgN1;  // contiguous reads along k1
+        cp_async_el(m.tw4 + k1 * G + g, twc + (size_t)(bx * G + g) * N1 + k1);
+    }
+    const R* Wall = reinterpret_cast<const R*>(S.W);
+    if ((int)threadIdx.x < (N1 >> 1) * G) {
+        const int i = col_elem(S, mkdiv(G), bx, threadIdx.x);
+#pragma unroll
+        for (int t = 0; t < WPRE; ++t)
+            if (t < S.T) wpre[t] = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wall + (size_t)t * S.Mp + i));
+    }
+}
+
+// Forward pass after the wait: stage input y (computed once per element), moments, and
+// the column transforms of all T inputs x_t = W_t . y, interleaved in one tile
+// transform over T G sequences. fix_tw: the tile twiddles still need stage_tw_fix.
+// red: 2 MAXT x 8 doubles of shared memory.
+template <typename R>
+__device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, const StageIn& in, int bx,
+                                         const ColSm<R>& m, const typename vec2<R>::T (&wpre)[WPRE], bool fix_tw,
+                                         double (*red)[8]) {
     const int G = S.G, T = S.T, GT = G * T, N1 = S.N1;
     const int half = (N1 >> 1) * G;
     const int n2b = bx * G;
-    cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
-    cx<R>* b = a + N1 * GT;
-    cx<R>* twP = b + N1 * GT;
-    cx<R>* tw4 = twP + N1;
-    R* ys = reinterpret_cast<R*>(tw4 + N1 * G);  // this CTA's y values, [idx][2]
-    const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
-    const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
-    // twiddle tables first: their loads overlap the stage-input loads below
-    stage_tw(twP, S.lgN1, tw, S.lgMp);
-    {
-        const cx<R>* twc = reinterpret_cast<const cx<R>*>(S.twc);
-        for (int idx = threadIdx.x; idx < N1 * G; idx += blockDim.x) {
-            const int k1 = idx & (N1 - 1), g = idx >> S.lgN1;  // contiguous reads along k1
-            cp_async_el(tw4 + k1 * G + g, twc + (size_t)(n2b + g) * N1 + k1);
-        }
-    }
-    // weights of this thread's first element pair for the first WPRE transforms: constant
-    // data, loaded before the wait for the previous kernel
-    const R* Wall = reinterpret_cast<const R*>(S.W);
+    cx<R>* a = m.a;
+    cx<R>* b = m.b;
+    R* ys = m.ys;
     const Div DG = mkdiv(G);
-    typename vec2<R>::T wpre[WPRE];
-    if ((int)threadIdx.x < half) {
-        int g, n1;
-        divmod(DG, threadIdx.x, n1, g);
-        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
-#pragma unroll
-        for (int t = 0; t < WPRE; ++t)
-            if (t < T) wpre[t] = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wall + (size_t)t * S.Mp + i));
-    }
-    load_ctl(S, cv);
-    if (cv.done) {
-        cp_async_wait();  // no copy into this CTA's shared memory outlives it
-        return;
-    }
+    const R* Wall = reinterpret_cast<const R*>(S.W);
     const Terms<R> P = resolve_terms<R>(in, S, cv);
     R* yb = reinterpret_cast<R*>(S.ybuf);
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-        int g, n1;
-        divmod(DG, idx, n1, g);
-        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
+        const int i = col_elem(S, DG, bx, idx);
         R y0, y1;
         stage_pair<R, R>(in, P, S.M, i, y0, y1);
         ys[2 * idx] = y0;
@@ -443,7 +474,7 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
     }
     for (int q = half * T + threadIdx.x; q < N1 * GT; q += blockDim.x) a[q] = mk<R>((R)0, (R)0);
     cp_async_wait();
-    stage_tw_fix(twP, S.lgN1, S.lgMp);
+    if (fix_tw) stage_tw_fix(m.twP, S.lgN1, S.lgMp);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     // FP64 form: the per-thread moments go through shared memory (the second tile
@@ -497,15 +528,37 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
         const int t = threadIdx.x >> 1;
         S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
     }
-    cx<R>* res = tile_fft<R, false>(a, b, S.lgN1, GT, twP);
+    cx<R>* res = tile_fft<R, false>(a, b, S.lgN1, GT, m.twP);
     cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
     const Div DGT = mkdiv(GT);
     for (int idx = threadIdx.x; idx < N1 * GT; idx += blockDim.x) {
         int c, k1, t, g;
         divmod(DGT, idx, k1, c);
         divmod(DG, c, t, g);
-        Yall[(size_t)t * S.Mp + (size_t)k1 * S.N2 + n2b + g] = res[idx] * tw4[k1 * G + g];
+        Yall[(size_t)t * S.Mp + (size_t)k1 * S.N2 + n2b + g] = res[idx] * m.tw4[k1 * G + g];
     }
+}
+
+// Kernel A: the forward pass of one evaluation.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                  const __grid_constant__ SysDev one, const StageIn in) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ double red[2 * MAXT][8];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int bx = load_desc(sysv, map, one, S);
+    const ColSm<R> m = col_sm<R>(S, smraw);
+    // twiddle tables and weights first (constant): their loads overlap the wait
+    stage_tw(m.twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
+    typename vec2<R>::T wpre[WPRE];
+    fwd_prologue<R>(S, bx, m, wpre);
+    load_ctl(S, cv);
+    if (cv.done) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
+    fwd_body<R>(S, cv, in, bx, m, wpre, true, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -569,23 +622,17 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ R pc[MAXR];
-    __shared__ double y1s;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int cta = load_desc(sysv, map, one, S);
     if (cta == 0) {
-        // The scalar CTA of the system, beside the row CTAs: y_1 in FP64 (from the FP64
-        // state, not its FP32 shadow: the two large terms of the monomer equation nearly
-        // cancel), then the moment partials of the column pass turned into the
-        // evaluation's scalars, which only the inverse column kernel reads.
+        // The scalar CTA of the system, beside the row CTAs: the evaluation's scalars,
+        // which only the inverse column kernel reads (y_1 from the FP64 state, not its
+        // FP32 shadow: the two large terms of the monomer equation nearly cancel).
+        double* sh = reinterpret_cast<double*>(smraw);
+        if ((int)threadIdx.x < S.T) sh[3 * MAXT + threadIdx.x] = (double)reinterpret_cast<const R*>(S.W)[(size_t)threadIdx.x * S.Mp];
         load_ctl(S, cv);
         if (cv.done) return;
-        if (threadIdx.x == 0) {
-            const Terms<R> P64 = resolve_terms<R>(in, S, cv, false);
-            double z0, z1;
-            stage_pair<double, R>(in, P64, S.M, 0, z0, z1);
-            y1s = z0;
-        }
-        finalize_scalars<R>(S, &y1s, reinterpret_cast<double*>(smraw));
+        finalize_scalars<R>(S, cv, in, sh);
         return;
     }
     const int blk = cta - 1;  // row pair
@@ -695,32 +742,21 @@ __device__ __forceinline__ void epi_inputs(const SysDev& S, const R* Wr, const R
     }
 }
 
-// ---------------------------------------------------------------------------
-// Kernel C: inverse column transforms of length N1 (only the first half of the
-// outputs is needed), then the epilogue: birth, death, shattering, monomer source,
-// scaled output. One CTA per G adjacent columns of one system.
-// ---------------------------------------------------------------------------
+// Inverse pass after the wait: inverse column transforms of length N1 (only the first
+// half of the outputs is needed), then the epilogue: birth, death, shattering, monomer
+// source, the scaled output k = h S(y) (or S(y) to a caller vector). The tile twiddles
+// were issued by stage_tw and are fixed here. sm: shared scalars (>= 36 doubles).
 template <typename R>
-__global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                  const __grid_constant__ SysDev one, const StageIn in,
-                                                  const EpiOut eo) {
-    __shared__ __align__(16) SysDev S;
-    __shared__ CtlView cv;
-    __shared__ double red[33];
-    __shared__ double src_s, bscale_s, s1_s;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int bx = load_desc(sysv, map, one, S);
+__device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, const StageIn& in, const EpiOut& eo,
+                                         int bx, const ColSm<R>& m, double* sm) {
     const int G = S.G;
-    cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
+    cx<R>* a = m.a;
     cx<R>* b = a + (S.N1 * G);
-    cx<R>* twP = b + (S.N1 * G);
+    double* red = sm;  // 33
+    double& src_s = sm[33];
+    double& bscale_s = sm[34];
+    double& s1_s = sm[35];
     const int n2b = bx * G;
-    stage_tw(twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
-    load_ctl(S, cv);
-    if (cv.done) {
-        cp_async_wait();  // no copy into this CTA's shared memory outlives it
-        return;
-    }
     const cx<R>* G2 = reinterpret_cast<const cx<R>*>(S.G2);
     const Div DG = mkdiv(G);
     for (int idx = threadIdx.x; idx < S.N1 * G; idx += blockDim.x) {
@@ -736,9 +772,7 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     // loaded before the transform, so that their latency overlaps it.
     R pD0 = (R)0, pD1 = (R)0, py0 = (R)0, py1 = (R)0;
     if (threadIdx.x < half) {
-        int g, n1;
-        divmod(DG, threadIdx.x, n1, g);
-        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
+        const int i = col_elem(S, DG, bx, threadIdx.x);
         if (i < S.M) epi_inputs<R>(S, Wr, yr, yd, i, pD0, pD1, py0, py1);
     }
     if (threadIdx.x == 0) {
@@ -754,18 +788,16 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
         if (sizeof(R) == sizeof(double)) bscale_s *= 0.125 * fold_coef(S);
     }
     cp_async_wait();
-    stage_tw_fix(twP, S.lgN1, S.lgMp);
+    stage_tw_fix(m.twP, S.lgN1, S.lgMp);
     __syncthreads();
-    cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, twP);
+    cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, m.twP);
     const double hsc = eo.out_slot >= 0 ? cv.h * eo.hfac : 1.0;
     const R scale = (R)hsc, bscale = (R)bscale_s, lam1 = (R)(1.0 + S.lambda);
     const double src = src_s;
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
     double sq = 0.0;
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-        int g, n1;
-        divmod(DG, idx, n1, g);
-        const int i = 2 * ((n1 << S.lgN2) + n2b + g);
+        const int i = col_elem(S, DG, bx, idx);
         if (i >= S.M) continue;
         const cx<R> z = res[idx];
         R D0 = pD0, D1 = pD1, y0 = py0, y1 = py1;
@@ -801,6 +833,57 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
         sq = block_sum(sq, red);
         if (threadIdx.x == 0) S.sqpart[bx] = sq;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel C: the inverse pass of one evaluation.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                  const __grid_constant__ SysDev one, const StageIn in,
+                                                  const EpiOut eo) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ double sm[36];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int bx = load_desc(sysv, map, one, S);
+    const ColSm<R> m = col_sm<R>(S, smraw);
+    stage_tw(m.twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
+    load_ctl(S, cv);
+    if (cv.done) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
+    inv_body<R>(S, cv, in, eo, bx, m, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel C+A: the inverse pass of one evaluation (stage input `in`, output eo) and the
+// forward pass of the next (stage input nx) in one kernel: the column CTA that forms
+// k of this stage at its elements goes on to form the next stage input there.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_inv_fwd(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                 const __grid_constant__ SysDev one, const StageIn in,
+                                                 const EpiOut eo, const StageIn nx) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ double sm[36];
+    __shared__ double red[2 * MAXT][8];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int bx = load_desc(sysv, map, one, S);
+    const ColSm<R> m = col_sm<R>(S, smraw);
+    stage_tw(m.twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
+    typename vec2<R>::T wpre[WPRE];
+    fwd_prologue<R>(S, bx, m, wpre);
+    load_ctl(S, cv);
+    if (cv.done) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
+    inv_body<R>(S, cv, in, eo, bx, m, sm);
+    __syncthreads();  // the forward pass reuses the tile buffers
+    fwd_body<R>(S, cv, nx, bx, m, wpre, false, red);
 }
 
 }  // namespace smol

@@ -13,6 +13,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "../../include/smol.h"
 #include "smol_rhs.cuh"
 
@@ -206,7 +208,7 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     eo.hfac = 1.0;
     const size_t n = (size_t)N1 * G;
     const size_t sc = 2 * n * T * 16 + (size_t)N1 * 16 + n * 16 + n * 8;  // >= the inverse pass's need
-    const size_t sr = 2 * (size_t)N2 * 2 * T * 16 + 5 * (size_t)N2 * 16;
+    const size_t sr = std::max<size_t>(2 * (size_t)N2 * 2 * T * 16 + 5 * (size_t)N2 * 16, (4 * MAXT + 1) * 8);
     SysDev none;
     memset(&none, 0, sizeof(none));
     k_fwd_cols<double><<<N2 / G, threads_for_s(N1 * G * T), sc, st>>>(dsys, mapC, none, in);

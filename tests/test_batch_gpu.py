@@ -125,7 +125,7 @@ def test_batch_systems_stop_independently(smol):
 
 def test_batch_tune_keeps_results(smol):
     """smol_batch_tune keeps the fastest launch mode; the batch's trajectories do not
-    depend on it (bit-identical)."""
+    depend on it (bit-identical, or equal to rounding if it unfused the column passes)."""
     import torch
     Us, Vs, lams, n0s = _systems(SPECS)
     st0 = [torch.from_numpy(n) for n in n0s]
@@ -133,7 +133,12 @@ def test_batch_tune_keeps_results(smol):
     ra, sa = a.integrate(st0, 0.0, 0.3, 1e-8)
     b = smol.Batch(Us, Vs, lams, tau0=1e-3)
     fl, us = b.tune(st0, 1e-8, attempts=4)
-    assert fl in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS) and us > 0.0
+    assert fl in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS, smol.FLAG_NO_FUSE,
+                  smol.FLAG_NO_FUSE | smol.FLAG_NO_PDL) and us > 0.0
     rb, sb = b.integrate(st0, 0.0, 0.3, 1e-8)
     for x, y, p, q in zip(ra, rb, sa, sb):
-        assert torch.equal(x, y) and p["accepted"] == q["accepted"]
+        assert p["accepted"] == q["accepted"]
+        if fl & smol.FLAG_NO_FUSE:  # another order of the final block sums: equal to rounding
+            assert torch.linalg.norm(x - y) <= 1e-12 * torch.linalg.norm(x)
+        else:
+            assert torch.equal(x, y)

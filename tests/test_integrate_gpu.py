@@ -162,20 +162,31 @@ def test_fp32conv_integrate_accuracy(smol):
     assert np.linalg.norm(n - m) <= 1e-4 * np.linalg.norm(m)
 
 
-def test_launch_modes_do_not_change_results(smol):
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv"])
+@pytest.mark.parametrize("scheme", ["rkf45", "rk4", "rk2"])
+def test_launch_modes_do_not_change_results(smol, precision, scheme):
     """Programmatic dependent launch only changes when CTAs are scheduled: every launch
-    mode gives bit-identical trajectories."""
+    mode gives bit-identical trajectories. Fusing the column passes changes only the
+    order of the final kernel's block sums (column CTAs instead of finish CTAs): the
+    fused and unfused trajectories agree to rounding, with the same decisions."""
     import torch
     M = 8192
     U, V = kernel_factors("brownian", M, a=0.6)
     n0 = torch.from_numpy(monodisperse(M)).cuda()
-    ref = None
-    for flags in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS, smol.FLAG_NO_PDL_ROWS | smol.FLAG_NO_PDL_STEP):
-        n, st = smol.System(U, V, 0.01, tau0=1e-3, flags=flags).integrate(n0, 0.0, 2.0, 1e-8)
-        got = (n.cpu().numpy(), st["accepted"], st["rejected"])
-        if ref is None:
-            ref = got
-        assert np.array_equal(got[0], ref[0]) and got[1:] == ref[1:]
+    runs = {}
+    for flags in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS, smol.FLAG_NO_PDL_ROWS | smol.FLAG_NO_PDL_STEP,
+                  smol.FLAG_NO_FUSE, smol.FLAG_NO_FUSE | smol.FLAG_NO_PDL):
+        n, st = smol.System(U, V, 0.01, precision=precision, tau0=1e-3, flags=flags).integrate(
+            n0, 0.0, 2.0, 1e-8, scheme=scheme)
+        assert st["status"] == 0
+        runs[flags] = (n.cpu().numpy(), st["accepted"], st["rejected"])
+    for flags, got in runs.items():
+        ref = runs[flags & smol.FLAG_NO_FUSE]
+        assert np.array_equal(got[0], ref[0]) and got[1:] == ref[1:], flags
+    a, b = runs[0], runs[smol.FLAG_NO_FUSE]
+    assert a[1:] == b[1:]
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert np.linalg.norm(a[0] - b[0]) <= tol * np.linalg.norm(b[0])
 
 
 def test_tune_picks_a_valid_schedule(smol):
@@ -188,8 +199,33 @@ def test_tune_picks_a_valid_schedule(smol):
     sched, us = smol.tune(U, V, 0.01, n0, 1e-8, attempts=8)
     assert us > 0.0
     assert sched["fft_lgn1"] in (5, 6, 7) and sched["fft_g"] in (2, 4, 8, 16)
-    assert sched["flags"] in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS)
+    assert sched["flags"] in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS, smol.FLAG_NO_FUSE,
+                              smol.FLAG_NO_FUSE | smol.FLAG_NO_PDL)
     a, _ = smol.System(U, V, 0.01, fixed_tau=0.01, **sched).integrate(n0, 0.0, 1.0, 1e-8)
     b, _ = smol.System(U, V, 0.01, fixed_tau=0.01).integrate(n0, 0.0, 1.0, 1e-8)
     a, b = a.cpu().numpy(), b.cpu().numpy()
     assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv"])
+def test_fused_kernels_at_full_size(smol, precision):
+    """M = 2^17 (the bench size: column tiles beyond the default 48 KB of dynamic shared
+    memory): fused and unfused column passes give the same RKF45 trajectory to rounding
+    over constant steps; adaptive runs from the stiff monodisperse start both reach t1
+    (their thousands of accept / reject decisions near err = tol may differ in a few
+    places, since the two sum the error norm in different orders)."""
+    import torch
+    M = 131072
+    U, V = kernel_factors("brownian", M, a=0.9)
+    n0 = torch.from_numpy(monodisperse(M)).cuda()
+    out = []
+    for flags in (0, smol.FLAG_NO_FUSE):
+        # 2e-6 is below the Euler bound 0.1 / max_s D_s(n0) = 0.1 / (M^0.9 + M^-0.9)
+        n, st = smol.System(U, V, 0.005, precision=precision, fixed_tau=2e-6, flags=flags).integrate(
+            n0, 0.0, 1e-4, 1e-8)
+        assert st["status"] == 0 and st["accepted"] in (50, 51)
+        out.append(n.cpu().numpy())
+        n, st = smol.System(U, V, 0.005, precision=precision, tau0=1e-3, flags=flags).integrate(n0, 0.0, 0.05, 1e-8)
+        assert st["status"] == 0 and abs(st["t"] - 0.05) < 1e-12
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert np.linalg.norm(out[0] - out[1]) <= tol * np.linalg.norm(out[1])
