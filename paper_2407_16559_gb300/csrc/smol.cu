@@ -127,7 +127,7 @@ Layout make_layout(const Shape& s, int R, int log_cap) {
     L.fpart = take((size_t)std::max(s.nfin, s.N2) * FPW * 8);  // finish CTAs or column CTAs
     L.sqpart = take((size_t)s.N2 * 8);
     L.aux = take((size_t)(MAXT + 1) * 8);
-    L.rsc = take((size_t)(MAXT + 2) * 8);
+    L.rsc = take((size_t)(MAXT + 2) * 8 + MAXT * 4);
     L.shadow = take(2 * align256((size_t)s.Mp * s.rsz));
     L.log_t = take((size_t)log_cap * 8);
     L.log_h = take((size_t)log_cap * 8);
@@ -481,6 +481,7 @@ StageIn stage(std::initializer_list<std::pair<int, double>> terms) {
         const int j = in.nv++;
         in.slot[j] = tc.first;
         in.c[j] = tc.second;
+        in.cf[j] = (float)tc.second;
     }
     return in;
 }
@@ -1105,6 +1106,7 @@ int rhs_common(smol_system* S, const double* d_n, double* d_out, double* d_birth
     in.direct = 1;
     in.slot[0] = SLOT_EXT;
     in.c[0] = 1.0;
+    in.cf[0] = 1.0f;
     in.ext = d_n;
     EpiOut eo;
     memset(&eo, 0, sizeof(eo));

@@ -81,7 +81,8 @@ struct SysDev {
     double* sqpart;  // ||S||^2 partials [bx]
     double* aux;     // MAXT + 1 doubles: collision-rate coefficients of the preparation
     double* rsc;     // RHS scalars of the current evaluation: death coefficients delta_t
-                     // [0, MAXT), monomer source [MAXT], S_1 [MAXT + 1]
+                     // [0, MAXT), monomer source [MAXT], S_1 [MAXT + 1]; then delta_t
+                     // rounded to FP32 (MAXT floats, rsc_f)
     void* shadow0;   // FP32 form: R-typed copies of the two state buffers (stage inputs)
     void* shadow1;
     double* log_t;   // step log ring (log_cap entries each, shared capacity)
@@ -111,6 +112,7 @@ struct StageIn {
     int nv, direct;  // direct: y is the single FP64 term itself (c == 1)
     int slot[MAXV];
     double c[MAXV];
+    float cf[MAXV];  // c rounded to FP32 (set on the host; the FP32 form's stage inputs)
     const double* ext;
 };
 
@@ -210,7 +212,7 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
 #pragma unroll
         for (int j = 0; j < MAXV; ++j)
             if (j < in.nv) {
-                const A c = (A)in.c[j];
+                const A c = sizeof(A) == sizeof(float) ? (A)in.cf[j] : (A)in.c[j];
                 y0 += c * v0[j];
                 y1 += c * v1[j];
             }
@@ -220,7 +222,7 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
             if (j < in.nv) {
                 const A v = ((P.dmask >> j) & 1u) ? (A)__ldcg(reinterpret_cast<const double*>(P.p[j]) + i)
                                                   : (A)__ldcg(reinterpret_cast<const R*>(P.p[j]) + i);
-                y0 += (A)in.c[j] * v;
+                y0 += (sizeof(A) == sizeof(float) ? (A)in.cf[j] : (A)in.c[j]) * v;
             }
     }
 }
@@ -272,6 +274,9 @@ __device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
     return *flag;
 }
 
+// The FP32 copies of delta_t behind the FP64 scalars.
+__device__ __forceinline__ float* rsc_f(const SysDev& S) { return reinterpret_cast<float*>(S.rsc + MAXT + 2); }
+
 // Scalars of one evaluation (the scalar CTA of the row kernel): y_1 in FP64, the
 // moments mu_t, nu_t summed over the column CTAs' partials in a fixed order, then
 //   delta_t = sum_{alpha: u=t} coef_alpha mu_{v(alpha)}   (death: D_s = sum_t delta_t W_t[s])
@@ -322,6 +327,7 @@ __device__ void finalize_scalars(const SysDev& S, const CtlView& cv, const Stage
         for (int al = 0; al < S.R; ++al)
             if (S.au[al] == t) del += S.acoef[al] * mom[2 * S.av[al]];
         S.rsc[t] = del;
+        rsc_f(S)[t] = (float)del;
         D1 += del * w1s[t];
     }
     const double src = 0.5 * S.lambda * shat + S.lambda * y1 * mono;
@@ -727,7 +733,7 @@ __device__ __forceinline__ void epi_inputs(const SysDev& S, const R* Wr, const R
     D0 = (R)0;
     D1 = (R)0;
     for (int t = 0; t < S.T; ++t) {
-        const R d = (R)__ldcg(S.rsc + t);
+        const R d = sizeof(R) == sizeof(float) ? (R)__ldcg(rsc_f(S) + t) : (R)__ldcg(S.rsc + t);
         const typename vec2<R>::T w = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wr + (size_t)t * S.Mp + i));
         D0 += d * w.x;
         D1 += d * w.y;
@@ -745,7 +751,7 @@ __device__ __forceinline__ void epi_inputs(const SysDev& S, const R* Wr, const R
 // Inverse pass after the wait: inverse column transforms of length N1 (only the first
 // half of the outputs is needed), then the epilogue: birth, death, shattering, monomer
 // source, the scaled output k = h S(y) (or S(y) to a caller vector). The tile twiddles
-// were issued by stage_tw and are fixed here. sm: shared scalars (>= 36 doubles).
+// were issued by stage_tw and are fixed here. sm: shared scalars (>= 40 doubles).
 template <typename R>
 __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, const StageIn& in, const EpiOut& eo,
                                          int bx, const ColSm<R>& m, double* sm) {
@@ -756,6 +762,7 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
     double& src_s = sm[33];
     double& bscale_s = sm[34];
     double& s1_s = sm[35];
+    R* rs = reinterpret_cast<R*>(sm + 36);  // scale, birth scale, 1 + lambda, S_1, loss_1 in type R
     const int n2b = bx * G;
     const cx<R>* G2 = reinterpret_cast<const cx<R>*>(S.G2);
     const Div DG = mkdiv(G);
@@ -786,13 +793,18 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
         bscale_s = S.bnorm * (double)pow2<float>(emax);
         // FP64: the factors the spectral product left out, (1/2)^3 pc[0]
         if (sizeof(R) == sizeof(double)) bscale_s *= 0.125 * fold_coef(S);
+        // the epilogue's scalars, converted once per CTA
+        rs[0] = (R)(eo.out_slot >= 0 ? cv.h * eo.hfac : 1.0);
+        rs[1] = (R)bscale_s;
+        rs[2] = (R)(1.0 + S.lambda);
+        rs[3] = (R)s1_s;
+        rs[4] = (R)(-(s1_s - src_s));
     }
     cp_async_wait();
     stage_tw_fix(m.twP, S.lgN1, S.lgMp);
     __syncthreads();
     cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, m.twP);
-    const double hsc = eo.out_slot >= 0 ? cv.h * eo.hfac : 1.0;
-    const R scale = (R)hsc, bscale = (R)bscale_s, lam1 = (R)(1.0 + S.lambda);
+    const R scale = rs[0], bscale = rs[1], lam1 = rs[2], s1r = rs[3], l1r = rs[4];
     const double src = src_s;
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
     double sq = 0.0;
@@ -804,11 +816,11 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
         if (idx != (int)threadIdx.x) epi_inputs<R>(S, Wr, yr, yd, i, D0, D1, y0, y1);
         const R b0 = (i == 0) ? (R)0 : z.x * bscale;
         const R b1 = z.y * bscale;
-        const R l0 = (i == 0) ? (R)(-(s1_s - src)) : lam1 * y0 * D0;
+        const R l0 = (i == 0) ? l1r : lam1 * y0 * D0;
         const R l1 = lam1 * y1 * D1;
         R s0 = b0 - l0;
         const R s1 = b1 - l1;
-        if (i == 0) s0 = (R)s1_s;
+        if (i == 0) s0 = s1r;
         const bool two = i + 1 < S.M;
         if (kout) {
             if (two) *reinterpret_cast<typename vec2<R>::T*>(kout + i) = {scale * s0, scale * s1};
@@ -844,7 +856,7 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
                                                   const EpiOut eo) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
-    __shared__ double sm[36];
+    __shared__ double sm[40];
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_desc(sysv, map, one, S);
     const ColSm<R> m = col_sm<R>(S, smraw);
@@ -868,7 +880,7 @@ __global__ void __launch_bounds__(256) k_inv_fwd(const SysDev* __restrict__ sysv
                                                  const EpiOut eo, const StageIn nx) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
-    __shared__ double sm[36];
+    __shared__ double sm[40];
     __shared__ double red[2 * MAXT][8];
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_desc(sysv, map, one, S);

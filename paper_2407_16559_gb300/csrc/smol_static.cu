@@ -43,7 +43,7 @@ constexpr size_t OFF_SYS = OFF_MPART + al((size_t)SMAX_T * 1024 * 2 * 8);
 constexpr size_t OFF_MAPC = OFF_SYS + al(sizeof(SysDev));
 constexpr size_t OFF_MAPB = OFF_MAPC + al((size_t)1024 * sizeof(int2));
 constexpr size_t OFF_RSC = OFF_MAPB + al((size_t)1024 * sizeof(int2));
-constexpr size_t SCRATCH_BYTES = OFF_RSC + al((size_t)(MAXT + 2) * 8);
+constexpr size_t SCRATCH_BYTES = OFF_RSC + al((size_t)(MAXT + 2) * 8 + MAXT * 4);
 
 // The scratch memory of smol_rhs_static.
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 15,320,320 bytes
@@ -200,6 +200,7 @@ extern "C" int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const do
     in.direct = 1;
     in.slot[0] = SLOT_EXT;
     in.c[0] = 1.0;
+    in.cf[0] = 1.0f;
     in.ext = d_n;
     EpiOut eo;
     memset(&eo, 0, sizeof(eo));
