@@ -381,17 +381,30 @@ def gpu_arm(args):
                             "kernel_us": {k: round(v * 1000.0, 3) for k, v in pm32.items()}, "schedule": sch32,
                             "rhs_rel_err_vs_fp64": rhs_accuracy(smol, torch, U, V)}
     if args.batch > 0:
+        # the batch shards across ranks by cost (smol_partition, no exchange while it
+        # runs); one gather of the stats at the end
+        from synth import batch_recipe
+        rank_of, _ = smol.partition([r["M"] for r in batch_recipe(args.batch)], world)
+        shard = smol.shard_indices(rank_of, rank) if world > 1 else None
         Kb = max(3, K // 10)
+        barrier()
         msb, stb, Ms, bflags = time_batch(smol, torch, "fp32conv", Kb, W, stream, flush, args.batch,
-                                          tune=not args.no_tune)
-        att = sum(x["attempts"] for x in stb)
-        acc = sum(x["accepted"] for x in stb)
+                                          tune=not args.no_tune, shard=shard)
+        if dist is not None:
+            t = torch.tensor([msb], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            msb = float(t.item())
+        stb = smol.gather_shards(stb, rank_of, dist) if world > 1 else stb
+        att = sum(x["attempts"] for x in stb) if stb else 0
+        acc = sum(x["accepted"] for x in stb) if stb else 0
         line["batch"] = {"systems": args.batch, "precision": "fp32conv", "steps": Kb, "ms_per_step": msb / Kb,
-                         "rhs_evals_per_s": world * EVALS_PER_STEP * args.batch * Kb / (msb / 1000.0),
-                         "accepted_steps_per_s": world * acc / max(att, 1) * args.batch * Kb / (msb / 1000.0),
-                         "elements": int(sum(Ms)), "launch_flags": bflags,
+                         "rhs_evals_per_s": EVALS_PER_STEP * args.batch * Kb / (msb / 1000.0),
+                         "accepted_steps_per_s": acc / max(att, 1) * args.batch * Kb / (msb / 1000.0),
+                         "scaling": "strong" if world > 1 else "n/a",
+                         "elements": int(sum(r["M"] for r in batch_recipe(args.batch))), "launch_flags": bflags,
                          "note": "one step = one RKF45 attempt of every system; systems from seed 2407, "
-                                 "M = 2^round(U(10,16)), a ~ U(0.2,0.9), lambda log-uniform [0.005, 0.1]"}
+                                 "M = 2^round(U(10,16)), a ~ U(0.2,0.9), lambda log-uniform [0.005, 0.1]; "
+                                 "with N ranks the systems are split by cost, time = slowest rank"}
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -400,7 +413,8 @@ def gpu_arm(args):
     return 0
 
 
-def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count: int = 256, tune: bool = True):
+def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count: int = 256, tune: bool = True,
+               shard=None):
     """The batched workload: `count` independent systems (M = 2^round(U(10,16)), kernel
     (i/j)^a + (j/i)^a with a ~ U(0.2, 0.9), lambda log-uniform in [0.005, 0.1],
     monodisperse starts, seed 2407), each with its own adaptive RKF45 step (tol 1e-8).
@@ -408,6 +422,8 @@ def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count
     systems). Returns device ms over K steps and the systems' stats."""
     from synth import batch_recipe, kernel_factors, monodisperse
     rec = batch_recipe(count)
+    if shard is not None:  # this rank's systems (smol_partition)
+        rec = [rec[q] for q in shard]
     Us, Vs, lams, n0s = [], [], [], []
     for r in rec:
         U, V = kernel_factors("brownian", r["M"], a=r["a"])

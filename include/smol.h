@@ -271,6 +271,18 @@ int smol_batch_integrate_finish(smol_batch* batch, smol_stats* stats);
  * for each launch mode that smol_tune tries, keeps the fastest for later integrations
  * of this batch and returns its flags in *flags and its microseconds per attempt of the
  * whole batch in *us_per_attempt (either may be NULL). Not while an integration runs. */
+/* Partition of a batch across nranks GPUs (host code; no GPU needed). The systems are
+ * independent (Sec. 3 integrates each on its own), so a batch shards with no exchange in
+ * the integration: each rank advances its own systems and the states and stats are
+ * gathered once at the end. System q costs weight[q] x Mp log2 Mp per attempt (Mp = the
+ * FFT size; weight: expected attempts, NULL = 1). Longest-processing-time-first
+ * assignment: systems by decreasing cost, each to the least-loaded rank, ties to the
+ * lower index; the makespan is within 4/3 of the optimum. rank_of[count] receives the
+ * rank of each system, load[nranks] (may be NULL) each rank's total cost. Deterministic:
+ * every rank computes the same partition. Returns SMOL_OK or SMOL_EINVAL. */
+int smol_partition(int32_t count, const int64_t* M, const double* weight, int32_t nranks,
+                   int32_t* rank_of, double* load);
+
 int smol_batch_tune(smol_batch* batch, double* const* d_n, double tol, int32_t scheme,
                     int32_t attempts, int32_t* flags, double* us_per_attempt);
 int smol_batch_get_log(smol_batch* batch, int32_t system, double* h_t, double* h_tau,

@@ -89,6 +89,7 @@ SIGNATURES = {
     "smol_batch_destroy": (None, [_P]),
     "smol_tune": (ctypes.c_int, [_I64, _I32, _P, _P, _D, _P, _D, _I32, _I32, ctypes.POINTER(Opts), ctypes.POINTER(_D)]),
     "smol_batch_tune": (ctypes.c_int, [_P, _P, _D, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
+    "smol_partition": (ctypes.c_int, [_I32, _P, _P, _I32, _P, _P]),
 }
 
 # option flags (smol_opts.flags)
@@ -160,6 +161,42 @@ def tune(U, V, lam: float, n0, tol: float, scheme: str = "rkf45", precision: str
     _check(_lib.smol_tune(M, R, U.ctypes.data, V.ctypes.data, float(lam), n0.data_ptr(), float(tol), SCHEMES[scheme],
                           int(attempts), ctypes.byref(o), ctypes.byref(us)), "smol_tune")
     return {k: int(getattr(o, k)) for k in SCHEDULE_KEYS}, us.value
+
+
+def partition(Ms, nranks: int, weights=None):
+    """smol_partition: rank of each system of a batch across nranks GPUs (cost-balanced,
+    deterministic) and each rank's load."""
+    Ms = np.ascontiguousarray(Ms, dtype=np.int64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    rank_of = np.zeros(Ms.size, dtype=np.int32)
+    load = np.zeros(int(nranks), dtype=np.float64)
+    _check(_lib.smol_partition(Ms.size, Ms.ctypes.data, None if w is None else w.ctypes.data, int(nranks),
+                               rank_of.ctypes.data, load.ctypes.data), "smol_partition")
+    return rank_of, load
+
+
+def shard_indices(rank_of, rank: int):
+    """The systems of this rank, in batch order."""
+    return [q for q, r in enumerate(rank_of) if int(r) == int(rank)]
+
+
+def gather_shards(local: list, rank_of, dist=None, dst: int = 0):
+    """One gather at the end of a sharded batch run: `local` holds this rank's results in
+    the order of shard_indices(rank_of, rank); the destination rank receives all results
+    in batch order (others receive None). Host objects only (states copied to the host
+    by the caller); torch.distributed with any backend."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return list(local)
+    rank, world = dist.get_rank(), dist.get_world_size()
+    parts = [None] * world if rank == dst else None
+    dist.gather_object(list(local), parts, dst=dst)
+    if rank != dst:
+        return None
+    out = [None] * len(rank_of)
+    for r in range(world):
+        for q, item in zip(shard_indices(rank_of, r), parts[r]):
+            out[q] = item
+    return out
 
 
 def _check(rc: int, what: str):

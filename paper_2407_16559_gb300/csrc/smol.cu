@@ -1468,6 +1468,38 @@ void smol_batch_destroy(smol_batch* B) {
     delete B;
 }
 
+// ---------------------------------------------------------------------------
+// C interface: partition of a batch across GPUs (host only)
+// ---------------------------------------------------------------------------
+int smol_partition(int32_t count, const int64_t* M, const double* weight, int32_t nranks, int32_t* rank_of,
+                   double* load) {
+    if (count < 1 || !M || nranks < 1 || !rank_of) return SMOL_EINVAL;
+    // cost of a system: its work per attempt, Mp log2 Mp (the FFT route's O(M log M)),
+    // times the caller's weight (expected attempts; 1 if none)
+    std::vector<double> cost(count);
+    for (int q = 0; q < count; ++q) {
+        if (M[q] < 1 || (weight && !(weight[q] >= 0.0))) return SMOL_EINVAL;
+        const int lg = ilog2(M[q] < 4 ? 4 : M[q]);
+        cost[q] = (double)((int64_t)1 << lg) * (double)(lg + 1) * (weight ? weight[q] : 1.0);
+    }
+    // longest processing time first: systems by decreasing cost (ties by index), each
+    // to the least-loaded rank (ties by the lower rank); within 4/3 of the optimum
+    std::vector<int> ord(count);
+    for (int q = 0; q < count; ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> ld(nranks, 0.0);
+    for (int q : ord) {
+        int r = 0;
+        for (int k = 1; k < nranks; ++k)
+            if (ld[k] < ld[r]) r = k;
+        rank_of[q] = r;
+        ld[r] += cost[q];
+    }
+    if (load)
+        for (int k = 0; k < nranks; ++k) load[k] = ld[k];
+    return SMOL_OK;
+}
+
 const char* smol_strerror(int code) {
     switch (code) {
         case SMOL_OK: return "ok";
