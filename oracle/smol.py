@@ -195,11 +195,19 @@ class System:
     """The ODE system dn/dt = S(n) of Eq. (5) for Eq. (4) with a given kernel.
 
     route='direct' uses a dense K (O(M^2), the definition); route='lowrank' uses the
-    factors U, V and the FFT route."""
+    factors U, V and the FFT route. sources: {s: P_s} (1-based sizes), the constant
+    injection terms P_k of Eq. (3); with lam = 0 the system is Eq. (3) (Sec. 3.1 uses
+    P_1 = 1, P_100 = p). They are added to the total and reported as the term
+    'sources'."""
 
-    def __init__(self, M, lam, K=None, U=None, V=None, route="direct"):
+    def __init__(self, M, lam, K=None, U=None, V=None, route="direct", sources=None):
         self.M, self.lam, self.route = int(M), float(lam), route
         self.K, self.U, self.V = K, U, V
+        self.P = np.zeros(self.M)
+        for k, v in (sources or {}).items():
+            if not 1 <= int(k) <= self.M:
+                raise ValueError("source size outside 1..M")
+            self.P[int(k) - 1] += float(v)
         if route == "direct" and K is None:
             self.K = kernel_from_factors(U, V)
         if route == "lowrank" and (U is None or V is None):
@@ -210,8 +218,12 @@ class System:
     def rhs_terms(self, n):
         self.evals += 1
         if self.route == "direct":
-            return rhs_terms_direct(n, self.K, self.lam, self._cache)
-        return rhs_terms_lowrank(n, self.U, self.V, self.lam)
+            d = rhs_terms_direct(n, self.K, self.lam, self._cache)
+        else:
+            d = rhs_terms_lowrank(n, self.U, self.V, self.lam)
+        d["sources"] = self.P.copy()
+        d["total"] = d["total"] + self.P
+        return d
 
     def rhs(self, n):
         return self.rhs_terms(n)["total"]

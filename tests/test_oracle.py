@@ -326,3 +326,46 @@ def test_steady_tail_constant_kernel_shattering():
     S = sysm.rhs(n)
     assert np.linalg.norm(S) / np.linalg.norm(n) < 1e-8
     assert abs(oracle.total_mass(n) - 1.0) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Aggregation with constant sources, Eq. (3) (Sec. 3.1: P_1 = 1, P_100 = p)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("route", ["direct", "lowrank"])
+def test_sources_mass_identity(route):
+    """Eq. (3): sum_s s S_s(n) = sum_s s P_s minus the truncation flux, exactly (for any
+    n): injection adds sum_s s P_s of mass per unit time and coagulation conserves
+    mass up to the pairs lost above M. Fails if a source enters at the wrong size
+    (off by one) or with the wrong sign."""
+    M = 150
+    n = random_state(M, seed=11, decay=30.0)
+    U, V = kernel_factors("brownian", M, a=0.3)
+    K = oracle.kernel_closed_form("brownian", M, a=0.3)
+    P = {1: 1.0, 100: 0.05}
+    sysm = oracle.System(M, 0.0, K=K, U=U, V=V, route=route, sources=P)
+    S = sysm.rhs(n)
+    s = np.arange(1, M + 1, dtype=np.float64)
+    inj = 1.0 * 1 + 0.05 * 100
+    lhs = float(np.dot(s, S))
+    rhs = inj + oracle.mass_flux_direct(n, K)
+    assert abs(lhs - rhs) <= 1e-12 * (float(np.dot(s, np.abs(S))) + inj)
+    d = sysm.rhs_terms(n)
+    assert d["sources"][0] == 1.0 and d["sources"][99] == 0.05 and np.count_nonzero(d["sources"]) == 2
+
+
+def test_sources_constant_kernel_total_density_closed_form():
+    """K = 1, monomer source J, empty start: N = sum_s n_s obeys dN/dt = J - N^2 / 2 (the
+    pairs above M are negligible here), so N(t) = sqrt(2J) tanh(t sqrt(J/2)); and the
+    mass is J t. Pins Eq. (3)'s source and birth/death balance through an integration."""
+    M, J = 64, 1.0
+    sysm = oracle.System(M, 0.0, K=np.ones((M, M)), sources={1: J})
+    n, st, _ = oracle.integrate(sysm, np.zeros(M), 0.0, 3.0, 1e-11, oracle.Options(scheme="rkf45", tau0=1e-3))
+    assert st["status"] == 0
+    N_exact = math.sqrt(2 * J) * math.tanh(3.0 * math.sqrt(J / 2))
+    assert abs(oracle.number_density(n) - N_exact) <= 1e-8
+    assert abs(oracle.total_mass(n) - 3.0 * J) <= 1e-7
+
+
+def test_sources_rejects_size_outside_range():
+    with pytest.raises(ValueError):
+        oracle.System(10, 0.0, K=np.ones((10, 10)), sources={11: 1.0})
