@@ -216,6 +216,16 @@ int smol_integrate_finish(smol_system* sys, smol_stats* stats);
 int smol_profile_attempts(smol_system* sys, int32_t reps, double* kernel_ms, int64_t* kernel_launches,
                           int32_t nkinds);
 
+/* Constant point sources of Eq. (3): dn_s/dt = S_s(n) + P_s at up to SMOL_MAX_SOURCES
+ * sizes (Sec. 3.1 injects P_1 = 1 and P_100 = p). With lambda = 0 the system is Eq. (3);
+ * with lambda > 0 the sources are added to Eq. (4). sizes are 1-based (1..M), values
+ * finite; count = 0 removes them. They enter S(n) (smol_rhs and the integrators; for
+ * s = 1 through the FP64 monomer equation) but not the separate terms of
+ * smol_rhs_terms. Not while an integration runs (between smol_integrate_start and
+ * smol_integrate_finish). Returns SMOL_OK or SMOL_EINVAL. */
+#define SMOL_MAX_SOURCES 8
+int smol_set_sources(smol_system* sys, int32_t count, const int64_t* sizes, const double* values);
+
 /* Schedule autotuner (the FFT schedule and the launch mode are implementation choices
  * that the paper leaves open: it only states the O(M R log M) cost of the FFT route,
  * Sec. 1). For one system of the given problem it times `attempts` step attempts of
@@ -271,6 +281,10 @@ int smol_batch_integrate_finish(smol_batch* batch, smol_stats* stats);
  * for each launch mode that smol_tune tries, keeps the fastest for later integrations
  * of this batch and returns its flags in *flags and its microseconds per attempt of the
  * whole batch in *us_per_attempt (either may be NULL). Not while an integration runs. */
+/* The point sources of system `system` of a batch (as smol_set_sources). */
+int smol_batch_set_sources(smol_batch* batch, int32_t system, int32_t count, const int64_t* sizes,
+                           const double* values);
+
 /* Partition of a batch across nranks GPUs (host code; no GPU needed). The systems are
  * independent (Sec. 3 integrates each on its own), so a batch shards with no exchange in
  * the integration: each rank advances its own systems and the states and stats are

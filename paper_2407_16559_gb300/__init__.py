@@ -90,6 +90,8 @@ SIGNATURES = {
     "smol_tune": (ctypes.c_int, [_I64, _I32, _P, _P, _D, _P, _D, _I32, _I32, ctypes.POINTER(Opts), ctypes.POINTER(_D)]),
     "smol_batch_tune": (ctypes.c_int, [_P, _P, _D, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
     "smol_partition": (ctypes.c_int, [_I32, _P, _P, _I32, _P, _P]),
+    "smol_set_sources": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "smol_batch_set_sources": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
 }
 
 # option flags (smol_opts.flags)
@@ -281,6 +283,13 @@ class Batch:
             raise SmolError(rc, "smol_batch_integrate")
         return ns, [s.as_dict() for s in st]
 
+    def set_sources(self, system: int, sources: dict):
+        """Point sources {s: P_s} (1-based sizes) of Eq. (3) for one system of the batch."""
+        k = np.ascontiguousarray(list(sources.keys()), dtype=np.int64)
+        v = np.ascontiguousarray(list(sources.values()), dtype=np.float64)
+        _check(_lib.smol_batch_set_sources(self._h, int(system), k.size, k.ctypes.data, v.ctypes.data),
+               "smol_batch_set_sources")
+
     def tune(self, n0s, tol: float, scheme: str = "rkf45", attempts: int = 16):
         """smol_batch_tune: keeps the fastest launch mode for this batch; returns
         (flags, microseconds per attempt of the whole batch)."""
@@ -380,6 +389,12 @@ class System:
         return int(_lib.smol_num_transforms(self._h))
 
     # -- C interface ------------------------------------------------------------
+    def set_sources(self, sources: dict):
+        """Point sources {s: P_s} (1-based sizes) of Eq. (3); {} removes them."""
+        k = np.ascontiguousarray(list(sources.keys()), dtype=np.int64)
+        v = np.ascontiguousarray(list(sources.values()), dtype=np.float64)
+        _check(_lib.smol_set_sources(self._h, k.size, k.ctypes.data, v.ctypes.data), "smol_set_sources")
+
     def rhs(self, n, out=None):
         """S(n) of Eq. (4) (device tensor of M doubles)."""
         torch = _torch()

@@ -278,6 +278,7 @@ struct Engine {
     SysDev* d_sys = nullptr;   // descriptors used by integrations (control blocks ctl)
     SysDev* d_sysr = nullptr;  // descriptors of standalone evaluations (control blocks rctl)
     SysDev h_one{}, h_oner{};  // host copies for single-system launches (passed by value)
+    std::vector<SysDev> hs, hsr;  // host copies of every system's descriptors
     Ctl* d_ctl = nullptr;
     Ctl* d_rctl = nullptr;
     int2 *mapC = nullptr, *mapB = nullptr, *mapF = nullptr;
@@ -880,6 +881,8 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     CK(cudaStreamSynchronize(st));
     E->h_one = hs[0];
     E->h_oner = hsr[0];
+    E->hs = hs;
+    E->hsr = hsr;
     CK(cudaHostAlloc((void**)&E->h_ctl, (size_t)count * sizeof(Ctl), cudaHostAllocDefault));
     CK(cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
     return prec == SMOL_FP32CONV ? set_smem_attrs<float>(E) : set_smem_attrs<double>(E);
@@ -1162,6 +1165,41 @@ constexpr int TUNE_FLAGS[] = {0, SMOL_FLAG_NO_PDL, SMOL_FLAG_NO_PDL_FWD_COLS, SM
 constexpr int PDL_BITS = SMOL_FLAG_NO_PDL | SMOL_FLAG_NO_PDL_FWD_COLS | SMOL_FLAG_NO_PDL_ROWS |
                          SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP | SMOL_FLAG_NO_FUSE;
 
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Point sources of Eq. (3)
+// ---------------------------------------------------------------------------
+namespace {
+static_assert(SMOL_MAX_SOURCES == MAXSRC, "source capacity of the C interface and the kernels");
+int set_sources(Engine* E, int q, int32_t count, const int64_t* sizes, const double* values) {
+    if (!E || q < 0 || q >= E->count || count < 0 || count > MAXSRC || E->running) return SMOL_EINVAL;
+    if (count > 0 && (!sizes || !values)) return SMOL_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (sizes[k] < 1 || sizes[k] > E->sh[q].M || !isfinite(values[k])) return SMOL_EINVAL;
+    for (SysDev* d : {&E->hs[q], &E->hsr[q]}) {
+        d->nsrc = count;
+        for (int k = 0; k < MAXSRC; ++k) {
+            d->src_i[k] = k < count ? (int)(sizes[k] - 1) : 0;
+            d->src_v[k] = k < count ? values[k] : 0.0;
+        }
+    }
+    cudaStream_t st = E->stream;
+    CK(cudaMemcpyAsync(E->d_sys + q, &E->hs[q], sizeof(SysDev), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(E->d_sysr + q, &E->hsr[q], sizeof(SysDev), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (q == 0) {
+        E->h_one = E->hs[0];
+        E->h_oner = E->hsr[0];
+    }
+    // captured graphs hold the old descriptor (single systems pass it by value)
+    if (E->gexec) {
+        cudaGraphExecDestroy(E->gexec);
+        E->gexec = nullptr;
+    }
+    E->gkey = -1;
+    return SMOL_OK;
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1466,6 +1504,17 @@ void smol_batch_destroy(smol_batch* B) {
     if (!B) return;
     engine_free(B);
     delete B;
+}
+
+// ---------------------------------------------------------------------------
+// C interface: point sources of Eq. (3)
+// ---------------------------------------------------------------------------
+int smol_set_sources(smol_system* S, int32_t count, const int64_t* sizes, const double* values) {
+    return set_sources(S, 0, count, sizes, values);
+}
+int smol_batch_set_sources(smol_batch* B, int32_t system, int32_t count, const int64_t* sizes,
+                           const double* values) {
+    return set_sources(B, system, count, sizes, values);
 }
 
 // ---------------------------------------------------------------------------

@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(256) k_inv_finish(const SysDev* __restrict__ s
                                                     const EpiOut eo, const Comb2 cd, const CtlParams P) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
-    __shared__ double sm[40];
+    __shared__ InvSm<R> sm;
     __shared__ FinSm f;
     __shared__ __align__(16) Ctl cs;
     extern __shared__ __align__(16) unsigned char smraw[];

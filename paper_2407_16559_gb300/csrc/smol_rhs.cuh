@@ -43,6 +43,7 @@ constexpr int MAXT = 2 * MAXR;  // largest number of distinct transforms
 constexpr int MAXV = 10;        // terms of a stage-input linear combination
 constexpr int NVEC = 12;        // stage / work vectors per system
 constexpr int FPW = MAXT + 4;   // doubles per block of the finish / preparation partials
+constexpr int MAXSRC = 8;       // point sources P_k of Eq. (3) per system
 
 // Device-resident control block of one system's integration (and of standalone
 // evaluations).
@@ -98,7 +99,10 @@ struct SysDev {
     double pcoef[MAXR];
     int wexp[MAXT];          // ilogb(max_i |W_t[i]|)
     double bnorm;            // 1 / (2 Mp): the 1/Mp of the inverse and the 1/2 of the birth term
-    int pad[4];
+    int nsrc;                // point sources of Eq. (3): S_s += P_s at 0-based sizes src_i
+    int src_i[MAXSRC];
+    double src_v[MAXSRC];
+    int pad[3];
 };
 
 // Stage input y = sum_j c_j v_j. slot >= 0: work vector (type R); slot -1 / -2: the
@@ -331,8 +335,11 @@ __device__ void finalize_scalars(const SysDev& S, const CtlView& cv, const Stage
         D1 += del * w1s[t];
     }
     const double src = 0.5 * S.lambda * shat + S.lambda * y1 * mono;
+    double p1 = 0.0;  // a point source at s = 1 (Eq. (3))
+    for (int q = 0; q < S.nsrc; ++q)
+        if (S.src_i[q] == 0) p1 += S.src_v[q];
     S.rsc[MAXT] = src;
-    S.rsc[MAXT + 1] = -y1 * D1 + src;
+    S.rsc[MAXT + 1] = -y1 * D1 + src + p1;
 }
 
 // Programmatic dependent launch. The kernels of an evaluation sequence are launched
@@ -751,18 +758,25 @@ __device__ __forceinline__ void epi_inputs(const SysDev& S, const R* Wr, const R
 // Inverse pass after the wait: inverse column transforms of length N1 (only the first
 // half of the outputs is needed), then the epilogue: birth, death, shattering, monomer
 // source, the scaled output k = h S(y) (or S(y) to a caller vector). The tile twiddles
-// were issued by stage_tw and are fixed here. sm: shared scalars (>= 40 doubles).
+// were issued by stage_tw and are fixed here. sm: the CTA's shared scalars.
+template <typename R>
+struct InvSm {
+    double red[33];
+    double src_s, bscale_s, s1_s;
+    R rs[5];  // scale, birth scale, 1 + lambda, S_1, loss_1 in type R
+};
+
 template <typename R>
 __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, const StageIn& in, const EpiOut& eo,
-                                         int bx, const ColSm<R>& m, double* sm) {
+                                         int bx, const ColSm<R>& m, InvSm<R>& sm) {
     const int G = S.G;
     cx<R>* a = m.a;
     cx<R>* b = a + (S.N1 * G);
-    double* red = sm;  // 33
-    double& src_s = sm[33];
-    double& bscale_s = sm[34];
-    double& s1_s = sm[35];
-    R* rs = reinterpret_cast<R*>(sm + 36);  // scale, birth scale, 1 + lambda, S_1, loss_1 in type R
+    double* red = sm.red;
+    double& src_s = sm.src_s;
+    double& bscale_s = sm.bscale_s;
+    double& s1_s = sm.s1_s;
+    R* rs = sm.rs;
     const int n2b = bx * G;
     const cx<R>* G2 = reinterpret_cast<const cx<R>*>(S.G2);
     const Div DG = mkdiv(G);
@@ -819,8 +833,13 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
         const R l0 = (i == 0) ? l1r : lam1 * y0 * D0;
         const R l1 = lam1 * y1 * D1;
         R s0 = b0 - l0;
-        const R s1 = b1 - l1;
+        R s1 = b1 - l1;
         if (i == 0) s0 = s1r;
+        for (int q = 0; q < S.nsrc; ++q) {  // point sources of Eq. (3) (s = 1 is in S_1)
+            const int si = S.src_i[q];
+            if (si == i && i != 0) s0 += (R)S.src_v[q];
+            if (si == i + 1) s1 += (R)S.src_v[q];
+        }
         const bool two = i + 1 < S.M;
         if (kout) {
             if (two) *reinterpret_cast<typename vec2<R>::T*>(kout + i) = {scale * s0, scale * s1};
@@ -856,7 +875,7 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
                                                   const EpiOut eo) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
-    __shared__ double sm[40];
+    __shared__ InvSm<R> sm;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_desc(sysv, map, one, S);
     const ColSm<R> m = col_sm<R>(S, smraw);
@@ -880,7 +899,7 @@ __global__ void __launch_bounds__(256) k_inv_fwd(const SysDev* __restrict__ sysv
                                                  const EpiOut eo, const StageIn nx) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
-    __shared__ double sm[40];
+    __shared__ InvSm<R> sm;
     __shared__ double red[2 * MAXT][8];
     extern __shared__ __align__(16) unsigned char smraw[];
     const int bx = load_desc(sysv, map, one, S);

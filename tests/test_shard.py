@@ -103,8 +103,13 @@ def test_sharded_batch_two_ranks_matches_one_process(tmp_path):
 
 
 def test_sharded_batch_rank_failure_is_reported(tmp_path):
-    """A rank that raises before the gather: the run ends with that rank's error (the
-    other rank is stopped), instead of hanging in the collective."""
+    """A rank that raises before the gather: the run ends with an error instead of
+    hanging in the collective: the failing rank's own, or the other rank's gather
+    seeing its peer gone (whichever process the launcher reports first)."""
+    import time
+
     import torch.multiprocessing as mp
-    with pytest.raises(Exception, match="injected failure"):
+    t0 = time.time()
+    with pytest.raises(Exception, match="injected failure|Connection closed|peer"):
         mp.spawn(_worker, args=(2, _free_port(), str(tmp_path / "x.npy"), 1), nprocs=2, join=True)
+    assert time.time() - t0 < 25.0  # well inside the process group's 30 s timeout
