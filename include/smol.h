@@ -65,14 +65,19 @@ extern "C" {
 #define SMOL_RK4    1
 #define SMOL_RKF45  2
 
-/* Arithmetic of the birth-term convolution.
+/* Arithmetic of the right-hand side.
  *   SMOL_FP64:     everything in FP64 (the plain solver).
- *   SMOL_FP32CONV: FFTs, spectral products and the inverse in FP32 with each
- *                  transform's input scaled by a power of two; state, moments,
- *                  death and shattering terms, RK combination, error and step
- *                  control stay FP64. */
+ *   SMOL_FP32CONV: FFTs, spectral products, the inverse and the element-wise terms in
+ *                  FP32, each transform's input scaled by a power of two; the state,
+ *                  RK combination, error, step control, mass and the monomer equation
+ *                  stay FP64 (results within 1e-4 of FP64).
+ *   SMOL_DF64:     as SMOL_FP32CONV with FP32 replaced by double-float (pairs of FP32
+ *                  numbers, ~48 significant bits) on the FP32 pipes: FP64-level results
+ *                  (the FP64 tolerance, 1e-10) at FP32-pipe throughput; GB300 runs FP64
+ *                  at 1/64 of its FP32 rate. */
 #define SMOL_FP64      0
 #define SMOL_FP32CONV  1
+#define SMOL_DF64      2
 
 /* Step rule for RK2 / RK4 with step doubling (Sec. 2).
  *   SMOL_CTRL_DOUBLE_HALVE: err > tol -> reject, tau /= 2; else accept, tau *= 2.
@@ -101,7 +106,7 @@ extern "C" {
 typedef struct smol_system smol_system;   /* opaque, created by smol_init_system */
 
 typedef struct smol_opts {
-    int32_t precision;      /* SMOL_FP64 | SMOL_FP32CONV */
+    int32_t precision;      /* SMOL_FP64 | SMOL_FP32CONV | SMOL_DF64 */
     int32_t ctrl;           /* SMOL_CTRL_* (RK2 / RK4 only) */
     int32_t norm;           /* SMOL_NORM_* */
     int32_t log_capacity;   /* attempts kept in the device step log (ring); 0 = no log */

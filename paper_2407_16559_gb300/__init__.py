@@ -22,7 +22,7 @@ OK, STEADY = 0, 1
 EINVAL, ECUDA, ENONFINITE, ESTEP_UNDERFLOW, EMAXATTEMPTS, ETIMEOUT, ENOSPACE, EUNSUPPORTED = (
     -1, -2, -3, -4, -5, -6, -7, -8)
 SCHEMES = {"rk2": 0, "rk4": 1, "rkf45": 2}
-PRECISIONS = {"fp64": 0, "fp32conv": 1}
+PRECISIONS = {"fp64": 0, "fp32conv": 1, "df64": 2}
 CTRLS = {"double_halve": 0, "formula": 1}
 NORMS = {"abs": 0, "rel": 1}
 

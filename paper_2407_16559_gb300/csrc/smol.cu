@@ -127,7 +127,7 @@ Layout make_layout(const Shape& s, int R, int log_cap) {
     L.fpart = take((size_t)std::max(s.nfin, s.N2) * FPW * 8);  // finish CTAs or column CTAs
     L.sqpart = take((size_t)s.N2 * 8);
     L.aux = take((size_t)(MAXT + 1) * 8);
-    L.rsc = take((size_t)(MAXT + 2) * 8 + MAXT * 4);
+    L.rsc = take((size_t)(MAXT + 2) * 8 + 2 * MAXT * 4);
     L.shadow = take(2 * align256((size_t)s.Mp * s.rsz));
     L.log_t = take((size_t)log_cap * 8);
     L.log_h = take((size_t)log_cap * 8);
@@ -483,6 +483,7 @@ StageIn stage(std::initializer_list<std::pair<int, double>> terms) {
         in.slot[j] = tc.first;
         in.c[j] = tc.second;
         in.cf[j] = (float)tc.second;
+        in.cl[j] = (float)(tc.second - (double)in.cf[j]);
     }
     return in;
 }
@@ -506,7 +507,7 @@ void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cuda
     q.pr = pr;
     q.fuse = !(E->o.flags & SMOL_FLAG_NO_FUSE);
     auto Ev = [&](StageIn in, int k, double hfac, bool first) {
-        if (sizeof(R) == sizeof(float))
+        if (Tr<R>::shadowed)
             for (int j = 0; j < in.nv; ++j)
                 if (in.slot[j] == SLOT_CUR) in.slot[j] = SLOT_CURF;
         q.eval(in, epi_k(k, hfac, (first && P.steady) ? 1 : 0));
@@ -619,6 +620,7 @@ CtlParams make_params(const Engine* E, int scheme) {
 
 void enqueue_attempt_any(Engine* E, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
     if (E->o.precision == SMOL_FP32CONV) enqueue_attempt<float>(E, scheme, fixed, P, st, pr);
+    else if (E->o.precision == SMOL_DF64) enqueue_attempt<dd>(E, scheme, fixed, P, st, pr);
     else enqueue_attempt<double>(E, scheme, fixed, P, st, pr);
 }
 
@@ -755,7 +757,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         d.sqpart = (double*)(b + L.sqpart);
         d.aux = (double*)(b + L.aux);
         d.rsc = (double*)(b + L.rsc);
-        if (prec == SMOL_FP32CONV) {
+        if (prec != SMOL_FP64) {  // R-typed shadows of the state buffers
             d.shadow0 = b + L.shadow;
             d.shadow1 = b + L.shadow + align256((size_t)s.Mp * s.rsz);
         }
@@ -849,6 +851,12 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
             to_type<float>(twc, tcb);
             to_type<float>(twr, trb);
             to_type<float>(tws, tsb);
+        } else if (prec == SMOL_DF64) {
+            to_type<dd>(hW, Wb);
+            to_type<dd>(tw64, twb);
+            to_type<dd>(twc, tcb);
+            to_type<dd>(twr, trb);
+            to_type<dd>(tws, tsb);
         } else {
             to_type<double>(hW, Wb);
             to_type<double>(tw64, twb);
@@ -885,7 +893,9 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     E->hsr = hsr;
     CK(cudaHostAlloc((void**)&E->h_ctl, (size_t)count * sizeof(Ctl), cudaHostAllocDefault));
     CK(cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
-    return prec == SMOL_FP32CONV ? set_smem_attrs<float>(E) : set_smem_attrs<double>(E);
+    if (prec == SMOL_FP32CONV) return set_smem_attrs<float>(E);
+    if (prec == SMOL_DF64) return set_smem_attrs<dd>(E);
+    return set_smem_attrs<double>(E);
 }
 
 void engine_free(Engine* E) {
@@ -896,7 +906,7 @@ void engine_free(Engine* E) {
 }
 
 int check_opts(const smol_opts& o) {
-    if (o.precision != SMOL_FP64 && o.precision != SMOL_FP32CONV) return SMOL_EINVAL;
+    if (o.precision != SMOL_FP64 && o.precision != SMOL_FP32CONV && o.precision != SMOL_DF64) return SMOL_EINVAL;
     if (o.log_capacity < 0 || o.chunk < 0) return SMOL_EINVAL;
     if (o.fft_lgn1 < 0 || o.fft_lgn1 > 30 || o.fft_g < 0 || o.fft_g > 64 || (o.fft_g & (o.fft_g - 1)))
         return SMOL_EINVAL;
@@ -930,6 +940,9 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
     if (E->o.precision == SMOL_FP32CONV) {
         k_prep1<float><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
         k_prep2<float><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, E->o.euler_a);
+    } else if (E->o.precision == SMOL_DF64) {
+        k_prep1<dd><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
+        k_prep2<dd><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, E->o.euler_a);
     } else {
         k_prep1<double><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
         k_prep2<double><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, E->o.euler_a);
@@ -1123,6 +1136,9 @@ int rhs_common(smol_system* S, const double* d_n, double* d_out, double* d_birth
     if (S->o.precision == SMOL_FP32CONV) {
         k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n);
         launch_eval<float>(S, A, in, eo, st, nullptr);
+    } else if (S->o.precision == SMOL_DF64) {
+        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n);
+        launch_eval<dd>(S, A, in, eo, st, nullptr);
     } else {
         launch_eval<double>(S, A, in, eo, st, nullptr);
     }

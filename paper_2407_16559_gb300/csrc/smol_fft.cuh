@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "smol_dd.cuh"
+
 namespace smol {
 
 template <typename R>
@@ -55,6 +57,18 @@ __device__ __forceinline__ cx<double> ldg(const cx<double>* p) {
 __device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
     float2 v = __ldg(reinterpret_cast<const float2*>(p));
     return mk(v.x, v.y);
+}
+__device__ __forceinline__ cx<dd> ldg(const cx<dd>* p) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return mk(dd(v.x, v.y), dd(v.z, v.w));
+}
+
+// 1/sqrt(2) in type R (the radix-8 butterfly's rotation by W_8).
+template <typename R>
+__device__ __forceinline__ R sqrt_half() { return (R)0.70710678118654752440; }
+template <>
+__device__ __forceinline__ dd sqrt_half<dd>() {
+    return dd(0.70710677f, 1.21016175e-08f);  // 0.7071067811865475244 split into two floats
 }
 
 // Twiddle table: tw[e] = exp(-2 pi i e / (2 Mp)) for e in [0, Mp). Returns W_{2Mp}^e
@@ -103,7 +117,7 @@ __device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3)
 // W_8^m), then two length-4 DFTs giving the even and the odd outputs.
 template <typename R, bool INV>
 __device__ __forceinline__ void dft8(cx<R>* u) {
-    const R h = (R)0.70710678118654752440;
+    const R h = sqrt_half<R>();
     cx<R> a0 = u[0] + u[4], a1 = u[1] + u[5], a2 = u[2] + u[6], a3 = u[3] + u[7];
     cx<R> b0 = u[0] - u[4], b1 = u[1] - u[5], b2 = u[2] - u[6], b3 = u[3] - u[7];
     if (INV) {

@@ -4,6 +4,8 @@
 // step. The state, its update, the error estimate, the controller and the mass moment
 // sum_s s n_s are FP64 whatever the precision of the right-hand side.
 #pragma once
+#include <type_traits>
+
 #include "smol_rhs.cuh"
 
 namespace smol {
@@ -232,7 +234,7 @@ __device__ __forceinline__ FinAcc fin_acc() {
 }
 template <typename R>
 __device__ __forceinline__ void fin_acc_close(FinAcc& a) {
-    if (sizeof(R) == sizeof(float)) {
+    if (std::is_same<R, float>::value) {
         a.se = (double)a.fse;
         a.sc = (double)a.fsc;
         a.mxb = a.fbad ? INF_BITS : absbits((double)a.fmx);
@@ -245,11 +247,12 @@ __device__ __forceinline__ void fin_acc_close(FinAcc& a) {
 // kernel reads the stage vector it has just written).
 template <typename R>
 __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const Terms<R>& tp, double* outp,
-                                         float* shad, int i, FinAcc& a) {
+                                         void* shadv, int i, FinAcc& a) {
     const StageIn& in = cd.in;
     const int p = i >> 1;
     const bool two = i + 1 < S.M;
-    if constexpr (sizeof(R) == sizeof(float)) {
+    if constexpr (std::is_same<R, float>::value) {
+        float* shad = reinterpret_cast<float*>(shadv);
         // FP32 form: the FP32 stage terms are combined in double-float arithmetic, the FP64
         // terms (state, half-step state) in FP64; FP64 is used only for those terms, the
         // candidate's final sum and the mass moment. Norms, max and the finite test work
@@ -309,6 +312,63 @@ __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const
         a.fsc += f0 * f0 + f1 * f1;
         a.fmx = fmaxf(a.fmx, fmaxf(fabsf(f0), fabsf(f1)));
         a.fbad = a.fbad || !isfinite(f0) || !isfinite(f1);
+    } else if constexpr (std::is_same<R, dd>::value) {
+        // Double-float form: the stage terms (double-float) are combined in double-float
+        // arithmetic (high and low parts each through df_fma), the FP64 terms in FP64;
+        // the candidate, its error vector, norms and mass in FP64, and the candidate's
+        // double-float image becomes the next state's shadow.
+        dd* shad = reinterpret_cast<dd*>(shadv);
+        DF c0 = {0.f, 0.f}, c1 = {0.f, 0.f}, d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
+        double b0 = 0.0, b1 = 0.0, e0 = 0.0, e1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < MAXV; ++j)
+            if (j < in.nv) {
+                if ((tp.dmask >> j) & 1u) {
+                    const double* v = reinterpret_cast<const double*>(tp.p[j]);
+                    const double v0 = __ldcg(v + i), v1 = two ? __ldcg(v + i + 1) : 0.0;
+                    b0 += in.c[j] * v0;
+                    b1 += in.c[j] * v1;
+                    if (cd.d[j] != 0.0) {
+                        e0 += cd.d[j] * v0;
+                        e1 += cd.d[j] * v1;
+                    }
+                } else {
+                    const dd* v = reinterpret_cast<const dd*>(tp.p[j]);
+                    dd v0, v1;
+                    if (two) {
+                        const dd2 w = ld2cg<dd>(v, p);
+                        v0 = w.x;
+                        v1 = w.y;
+                    } else {
+                        v0 = ld1cg<dd>(v + i);
+                        v1 = dd(0.f, 0.f);
+                    }
+                    df_fma(c0, cd.ch[j], cd.cl[j], v0.hi);
+                    df_fma(c0, cd.ch[j], cd.cl[j], v0.lo);
+                    df_fma(c1, cd.ch[j], cd.cl[j], v1.hi);
+                    df_fma(c1, cd.ch[j], cd.cl[j], v1.lo);
+                    df_fma(d0, cd.dh[j], cd.dl[j], v0.hi);
+                    df_fma(d0, cd.dh[j], cd.dl[j], v0.lo);
+                    df_fma(d1, cd.dh[j], cd.dl[j], v1.hi);
+                    df_fma(d1, cd.dh[j], cd.dl[j], v1.lo);
+                }
+            }
+        const double y0 = b0 + df_value(c0), y1 = b1 + df_value(c1);
+        const double q0 = e0 + df_value(d0), q1 = e1 + df_value(d1);
+        if (two) {
+            *reinterpret_cast<double2*>(outp + i) = make_double2(y0, y1);
+            dd2 sh;
+            sh.x = dd(y0);
+            sh.y = dd(y1);
+            *reinterpret_cast<dd2*>(shad + i) = sh;
+        } else {
+            outp[i] = y0;
+            shad[i] = dd(y0);
+        }
+        a.se += q0 * q0 + q1 * q1;
+        a.sc += y0 * y0 + y1 * y1;
+        a.ms += (double)(i + 1) * y0 + (double)(i + 2) * y1;
+        a.mxb = max(a.mxb, max(absbits(y0), absbits(y1)));
     } else {
         double y0 = 0.0, y1 = 0.0, d0 = 0.0, d1 = 0.0;
         if (two) {
@@ -321,7 +381,7 @@ __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const
                         v0[j] = v.x;
                         v1[j] = v.y;
                     } else {
-                        const typename vec2<R>::T v = __ldcg(reinterpret_cast<const typename vec2<R>::T*>(tp.p[j]) + p);
+                        const typename vec2<R>::T v = ld2cg<R>(reinterpret_cast<const R*>(tp.p[j]), p);
                         v0[j] = (double)v.x;
                         v1[j] = (double)v.y;
                     }
@@ -340,7 +400,7 @@ __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const
             for (int j = 0; j < MAXV; ++j)
                 if (j < in.nv) {
                     const double v = ((tp.dmask >> j) & 1u) ? __ldcg(reinterpret_cast<const double*>(tp.p[j]) + i)
-                                                            : (double)__ldcg(reinterpret_cast<const R*>(tp.p[j]) + i);
+                                                            : (double)ld1cg<R>(reinterpret_cast<const R*>(tp.p[j]) + i);
                     y0 += in.c[j] * v;
                     d0 += cd.d[j] * v;
                 }
@@ -473,7 +533,7 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     if (cv.done) return;
     copy_ctl(S.ctl, cs);
     double* outp = const_cast<double*>(cv.cur ? cv.s0 : cv.s1);
-    float* shad = reinterpret_cast<float*>(cv.cur ? S.shadow0 : S.shadow1);
+    void* shad = cv.cur ? S.shadow0 : S.shadow1;
     const Terms<R> tp = resolve_terms<R>(cd.in, S, cv, false);
     FinAcc acc = fin_acc();
     const int np = (S.M + 1) >> 1;
@@ -506,7 +566,7 @@ __global__ void __launch_bounds__(256) k_inv_finish(const SysDev* __restrict__ s
     copy_ctl(S.ctl, cs);
     inv_body<R>(S, cv, in, eo, bx, m, sm);
     double* outp = const_cast<double*>(cv.cur ? cv.s0 : cv.s1);
-    float* shad = reinterpret_cast<float*>(cv.cur ? S.shadow0 : S.shadow1);
+    void* shad = cv.cur ? S.shadow0 : S.shadow1;
     const Terms<R> tp = resolve_terms<R>(cd.in, S, cv, false);
     FinAcc acc = fin_acc();
     const Div DG = mkdiv(S.G);

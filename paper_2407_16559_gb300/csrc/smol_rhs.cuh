@@ -116,7 +116,8 @@ struct StageIn {
     int nv, direct;  // direct: y is the single FP64 term itself (c == 1)
     int slot[MAXV];
     double c[MAXV];
-    float cf[MAXV];  // c rounded to FP32 (set on the host; the FP32 form's stage inputs)
+    float cf[MAXV];  // c rounded to FP32 and the remainder c - cf rounded to FP32 (set on
+    float cl[MAXV];  // the host; the FP32 and double-float forms' stage inputs)
     const double* ext;
 };
 
@@ -189,6 +190,74 @@ template <>
 struct vec2<float> {
     typedef float2 T;
 };
+template <>
+struct vec2<dd> {
+    typedef dd2 T;
+};
+
+// What the right-hand side's arithmetic type R implies: inputs scaled per transform
+// (FP32 exponent range), an R-typed shadow of the FP64 state for stage inputs, the
+// FP64 form's folded spectral constants.
+template <typename R>
+struct Tr {
+    static constexpr bool scaled = true, shadowed = true, fp64 = false;
+};
+template <>
+struct Tr<double> {
+    static constexpr bool scaled = false, shadowed = false, fp64 = true;
+};
+
+// Loads of one R value and of the R pair at 2 * pair, 2 * pair + 1: read-only path
+// (ldg) or coherent L2 path (ldcg).
+template <typename R>
+__device__ __forceinline__ typename vec2<R>::T ld2g(const R* p, int pair) {
+    return __ldg(reinterpret_cast<const typename vec2<R>::T*>(p) + pair);
+}
+template <>
+__device__ __forceinline__ dd2 ld2g<dd>(const dd* p, int pair) {
+    return as_dd2(__ldg(reinterpret_cast<const float4*>(p) + pair));
+}
+template <typename R>
+__device__ __forceinline__ typename vec2<R>::T ld2cg(const R* p, int pair) {
+    return __ldcg(reinterpret_cast<const typename vec2<R>::T*>(p) + pair);
+}
+template <>
+__device__ __forceinline__ dd2 ld2cg<dd>(const dd* p, int pair) {
+    return as_dd2(__ldcg(reinterpret_cast<const float4*>(p) + pair));
+}
+template <typename R>
+__device__ __forceinline__ R ld1cg(const R* p) {
+    return __ldcg(p);
+}
+template <>
+__device__ __forceinline__ dd ld1cg<dd>(const dd* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return dd(v.x, v.y);
+}
+template <typename R>
+__device__ __forceinline__ R ld1g(const R* p) {
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ dd ld1g<dd>(const dd* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return dd(v.x, v.y);
+}
+
+// Stage-input coefficient c_j in type A (from the host's FP32 split for the FP32 and
+// double-float forms, so that no FP64 conversion runs per element).
+template <typename A>
+__device__ __forceinline__ A coef(const StageIn& in, int j) {
+    return (A)in.c[j];
+}
+template <>
+__device__ __forceinline__ float coef<float>(const StageIn& in, int j) {
+    return in.cf[j];
+}
+template <>
+__device__ __forceinline__ dd coef<dd>(const StageIn& in, int j) {
+    return dd(in.cf[j], in.cl[j]);
+}
 
 // Stage input at indices i, i+1 (i even), accumulated in type A: zero at and beyond M.
 // All term loads are issued before the first multiply-add so that their latencies
@@ -208,7 +277,7 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
                     v0[j] = (A)v.x;
                     v1[j] = (A)v.y;
                 } else {
-                    const typename vec2<R>::T v = __ldcg(reinterpret_cast<const typename vec2<R>::T*>(P.p[j]) + (i >> 1));
+                    const typename vec2<R>::T v = ld2cg<R>(reinterpret_cast<const R*>(P.p[j]), i >> 1);
                     v0[j] = (A)v.x;
                     v1[j] = (A)v.y;
                 }
@@ -216,7 +285,7 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
 #pragma unroll
         for (int j = 0; j < MAXV; ++j)
             if (j < in.nv) {
-                const A c = sizeof(A) == sizeof(float) ? (A)in.cf[j] : (A)in.c[j];
+                const A c = coef<A>(in, j);
                 y0 += c * v0[j];
                 y1 += c * v1[j];
             }
@@ -225,8 +294,8 @@ __device__ __forceinline__ void stage_pair(const StageIn& in, const Terms<R>& P,
         for (int j = 0; j < MAXV; ++j)
             if (j < in.nv) {
                 const A v = ((P.dmask >> j) & 1u) ? (A)__ldcg(reinterpret_cast<const double*>(P.p[j]) + i)
-                                                  : (A)__ldcg(reinterpret_cast<const R*>(P.p[j]) + i);
-                y0 += (sizeof(A) == sizeof(float) ? (A)in.cf[j] : (A)in.c[j]) * v;
+                                                  : (A)ld1cg<R>(reinterpret_cast<const R*>(P.p[j]) + i);
+                y0 += coef<A>(in, j) * v;
             }
     }
 }
@@ -243,7 +312,7 @@ __device__ __forceinline__ V pick(const V (&v)[WPRE], int t) {
 // x_t by 2^(ilogb(max|W_t|) + ilogb(max|y|)) so that its largest entry is near 1.
 template <typename R>
 __device__ __forceinline__ int xexp(const SysDev& S, const CtlView& cv, int t) {
-    return sizeof(R) == sizeof(double) ? 0 : cv.xe[t];
+    return Tr<R>::scaled ? cv.xe[t] : 0;
 }
 
 // Sets the input scale exponents of the FP32 form from max|n| (once per accepted
@@ -256,12 +325,17 @@ __device__ __forceinline__ void set_xe(Ctl* c, const SysDev& S, double ymax) {
 // 2^e as R, exactly, without a double-precision ldexp (e within the normal range).
 template <typename R>
 __device__ __forceinline__ R pow2(int e) {
-    if (sizeof(R) == sizeof(float)) {
-        e = max(-126, min(127, e));
-        return (R)__int_as_float((127 + e) << 23);
-    }
     e = max(-1022, min(1023, e));
     return (R)__longlong_as_double((long long)(1023 + e) << 52);
+}
+template <>
+__device__ __forceinline__ float pow2<float>(int e) {
+    e = max(-126, min(127, e));
+    return __int_as_float((127 + e) << 23);
+}
+template <>
+__device__ __forceinline__ dd pow2<dd>(int e) {
+    return dd(pow2<float>(e));
 }
 
 // Last-CTA-done pattern: every CTA of a system writes its partials, then one atomic
@@ -278,8 +352,21 @@ __device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
     return *flag;
 }
 
-// The FP32 copies of delta_t behind the FP64 scalars.
+// FP32 copies of delta_t behind the FP64 scalars: [0, MAXT) rounded, [MAXT, 2 MAXT) the
+// remainders (the double-float form's low parts).
 __device__ __forceinline__ float* rsc_f(const SysDev& S) { return reinterpret_cast<float*>(S.rsc + MAXT + 2); }
+template <typename R>
+__device__ __forceinline__ R delta_r(const SysDev& S, int t) {
+    return (R)__ldcg(S.rsc + t);
+}
+template <>
+__device__ __forceinline__ float delta_r<float>(const SysDev& S, int t) {
+    return __ldcg(rsc_f(S) + t);
+}
+template <>
+__device__ __forceinline__ dd delta_r<dd>(const SysDev& S, int t) {
+    return dd(__ldcg(rsc_f(S) + t), __ldcg(rsc_f(S) + MAXT + t));
+}
 
 // Scalars of one evaluation (the scalar CTA of the row kernel): y_1 in FP64, the
 // moments mu_t, nu_t summed over the column CTAs' partials in a fixed order, then
@@ -301,7 +388,7 @@ __device__ void finalize_scalars(const SysDev& S, const CtlView& cv, const Stage
         double v = 0.0;
         if (lane < in.nv)
             v = ((P.dmask >> lane) & 1u) ? __ldg(reinterpret_cast<const double*>(P.p[lane]))
-                                         : (double)__ldg(reinterpret_cast<const R*>(P.p[lane]));
+                                         : (double)ld1g<R>(reinterpret_cast<const R*>(P.p[lane]));
         double y1 = 0.0;
         for (int j = 0; j < in.nv; ++j) y1 += in.c[j] * __shfl_sync(0xffffffffu, v, j);
         if (lane == 0) *y1p = y1;
@@ -331,7 +418,9 @@ __device__ void finalize_scalars(const SysDev& S, const CtlView& cv, const Stage
         for (int al = 0; al < S.R; ++al)
             if (S.au[al] == t) del += S.acoef[al] * mom[2 * S.av[al]];
         S.rsc[t] = del;
-        rsc_f(S)[t] = (float)del;
+        const float dh = (float)del;
+        rsc_f(S)[t] = dh;
+        rsc_f(S)[MAXT + t] = (float)(del - (double)dh);
         D1 += del * w1s[t];
     }
     const double src = 0.5 * S.lambda * shat + S.lambda * y1 * mono;
@@ -455,7 +544,7 @@ __device__ __forceinline__ void fwd_prologue(const SysDev& S, int bx, const ColS
         const int i = col_elem(S, mkdiv(G), bx, threadIdx.x);
 #pragma unroll
         for (int t = 0; t < WPRE; ++t)
-            if (t < S.T) wpre[t] = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wall + (size_t)t * S.Mp + i));
+            if (t < S.T) wpre[t] = ld2g<R>(Wall + (size_t)t * S.Mp, i >> 1);
     }
 }
 
@@ -494,7 +583,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
     // buffer, unused until the transform) and each is summed by one warp, which takes
     // far fewer FP64 instructions than a shuffle tree in every warp; the FP32 form sums
     // in FP32 shuffles and then in FP64 across warps.
-    const bool viasm = sizeof(R) == sizeof(double) && N1 * G >= (int)blockDim.x;
+    const bool viasm = Tr<R>::fp64 && N1 * G >= (int)blockDim.x;
     double* rb = reinterpret_cast<double*>(b);
     for (int t = 0; t < T; ++t) {
         const R sc = pow2<R>(-xexp<R>(S, cv, t));
@@ -504,9 +593,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
             int g, n1;
             divmod(DG, idx, n1, g);
             const int i = 2 * ((n1 << S.lgN2) + n2b + g);
-            const typename vec2<R>::T w = (idx == (int)threadIdx.x && t < WPRE)
-                                              ? pick(wpre, t)
-                                              : __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wt + i));
+            const typename vec2<R>::T w = (idx == (int)threadIdx.x && t < WPRE) ? pick(wpre, t) : ld2g<R>(Wt, i >> 1);
             const R x0 = w.x * ys[2 * idx], x1 = w.y * ys[2 * idx + 1];
             mu += x0 + x1;
             nu += (R)(i + 1) * x0 + (R)(i + 2) * x1;
@@ -518,8 +605,8 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
             continue;
         }
         for (int o = 16; o > 0; o >>= 1) {
-            mu += __shfl_down_sync(0xffffffffu, mu, o);
-            nu += __shfl_down_sync(0xffffffffu, nu, o);
+            mu += shfl_down(mu, o);
+            nu += shfl_down(nu, o);
         }
         if (lane == 0) {
             red[2 * t][warp] = (double)mu;
@@ -580,6 +667,11 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
 // inverse row transforms and the inverse twiddle. CTA 0 of a system is its scalar CTA;
 // CTA b + 1 owns rows (b, N1 - b), CTA 1 rows (0, N1 / 2).
 // ---------------------------------------------------------------------------
+// Whether a pair coefficient must be applied (the FP64 form skips an exact 1).
+__device__ __forceinline__ bool pc_not_one(double c) { return c != 1.0; }
+template <typename R>
+__device__ __forceinline__ bool pc_not_one(R) { return true; }
+
 // FP64 form (FOLD): the factors 1/2 of E, O and of the packed inverse and the first
 // pair's coefficient are taken out of the per-frequency arithmetic (it then forms 2 X,
 // sums pc[p] / pc[0] (2X_u)(2X_v) and returns 2 Y / pc[0] * 4) and applied once in the
@@ -590,7 +682,7 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
                                               const R* pc, cx<R>& Ya, cx<R>& Yb) {
     // Z holds the row spectra as Z[k2 * G + col], col = 2 t + rho; ia / ib are the
     // offsets k2 * G + rho of the pair's two frequencies ka and Mp - ka; w = W_L^ka.
-    constexpr bool FOLD = sizeof(R) == sizeof(double);
+    constexpr bool FOLD = Tr<R>::fp64;
     cx<R> Ca = mk<R>((R)0, (R)0), Cb = Ca;
     for (int p = 0; p < S.npairs; ++p) {
         const int u = S.pu[p], v = S.pv[p];
@@ -610,7 +702,7 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
             Xb[q] = conj(E - wO);
         }
         cx<R> pa = Xa[0] * Xa[1], pb = Xb[0] * Xb[1];
-        if (!FOLD || pc[p] != (R)1) {
+        if (!FOLD || pc_not_one(pc[p])) {
             pa = scl(pa, pc[p]);
             pb = scl(pb, pc[p]);
         }
@@ -659,7 +751,6 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     const int r0 = blk ? blk : 0;
     const int r1 = blk ? S.N1 - blk : (S.N1 >> 1);
     const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
-    const uint32_t mask2 = 2u * (uint32_t)S.Mp - 1u;
     stage_tw(twP, S.lgN2, tw, S.lgMp);
     for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
         const int rho = idx >> S.lgN2, k2 = idx & (N2 - 1);
@@ -676,11 +767,11 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
         // FP32: pair p carries 2^(e_u + e_v - e_max) so that the sum stays in range.
         // FP64: pc[0] is folded into the birth scale (spectral_pair).
         R c = (R)S.pcoef[threadIdx.x];
-        if (sizeof(R) == sizeof(double)) c = (R)(S.pcoef[threadIdx.x] / fold_coef(S));
-        if (sizeof(R) == sizeof(float)) {
+        if (Tr<R>::fp64) c = (R)(S.pcoef[threadIdx.x] / fold_coef(S));
+        if (Tr<R>::scaled) {
             int emax = -100000;
             for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, cv, S.pu[p]) + xexp<R>(S, cv, S.pv[p]));
-            c *= pow2<R>(xexp<R>(S, cv, S.pu[threadIdx.x]) + xexp<R>(S, cv, S.pv[threadIdx.x]) - emax);
+            c = c * pow2<R>(xexp<R>(S, cv, S.pu[threadIdx.x]) + xexp<R>(S, cv, S.pv[threadIdx.x]) - emax);
         }
         pc[threadIdx.x] = c;
     }
@@ -740,8 +831,8 @@ __device__ __forceinline__ void epi_inputs(const SysDev& S, const R* Wr, const R
     D0 = (R)0;
     D1 = (R)0;
     for (int t = 0; t < S.T; ++t) {
-        const R d = sizeof(R) == sizeof(float) ? (R)__ldcg(rsc_f(S) + t) : (R)__ldcg(S.rsc + t);
-        const typename vec2<R>::T w = __ldg(reinterpret_cast<const typename vec2<R>::T*>(Wr + (size_t)t * S.Mp + i));
+        const R d = delta_r<R>(S, t);
+        const typename vec2<R>::T w = ld2g<R>(Wr + (size_t)t * S.Mp, i >> 1);
         D0 += d * w.x;
         D1 += d * w.y;
     }
@@ -800,13 +891,13 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
         src_s = __ldcg(S.rsc + MAXT);
         s1_s = __ldcg(S.rsc + MAXT + 1);
         int emax = 0;
-        if (sizeof(R) == sizeof(float)) {
+        if (Tr<R>::scaled) {
             emax = -100000;
             for (int p = 0; p < S.npairs; ++p) emax = max(emax, xexp<R>(S, cv, S.pu[p]) + xexp<R>(S, cv, S.pv[p]));
         }
         bscale_s = S.bnorm * (double)pow2<float>(emax);
         // FP64: the factors the spectral product left out, (1/2)^3 pc[0]
-        if (sizeof(R) == sizeof(double)) bscale_s *= 0.125 * fold_coef(S);
+        if (Tr<R>::fp64) bscale_s *= 0.125 * fold_coef(S);
         // the epilogue's scalars, converted once per CTA
         rs[0] = (R)(eo.out_slot >= 0 ? cv.h * eo.hfac : 1.0);
         rs[1] = (R)bscale_s;

@@ -43,7 +43,7 @@ constexpr size_t OFF_SYS = OFF_MPART + al((size_t)SMAX_T * 1024 * 2 * 8);
 constexpr size_t OFF_MAPC = OFF_SYS + al(sizeof(SysDev));
 constexpr size_t OFF_MAPB = OFF_MAPC + al((size_t)1024 * sizeof(int2));
 constexpr size_t OFF_RSC = OFF_MAPB + al((size_t)1024 * sizeof(int2));
-constexpr size_t SCRATCH_BYTES = OFF_RSC + al((size_t)(MAXT + 2) * 8 + MAXT * 4);
+constexpr size_t SCRATCH_BYTES = OFF_RSC + al((size_t)(MAXT + 2) * 8 + 2 * MAXT * 4);
 
 // The scratch memory of smol_rhs_static.
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 15,320,320 bytes

@@ -38,7 +38,7 @@ def _systems(specs):
 SPECS = [(1000, 0.3, 0.01), (4096, 0.7, 0.05), (513, 0.5, 0.1), (16384, 0.9, 0.005), (64, 0.2, 0.02)]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32conv"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
 def test_batch_equals_single_systems(smol, precision):
     import torch
     Us, Vs, lams, n0s = _systems(SPECS)

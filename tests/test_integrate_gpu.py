@@ -229,3 +229,14 @@ def test_fused_kernels_at_full_size(smol, precision):
         assert st["status"] == 0 and abs(st["t"] - 0.05) < 1e-12
     tol = 1e-12 if precision == "fp64" else 1e-6
     assert np.linalg.norm(out[0] - out[1]) <= tol * np.linalg.norm(out[1])
+
+
+@pytest.mark.parametrize("scheme", ["rkf45", "rk4"])
+def test_df64_adaptive_parity(smol, scheme):
+    """The double-float form takes the oracle's accept / reject decisions and ends on
+    its state at the FP64 parity bar."""
+    n, st, m, ost, _, _ = run_both(smol, 512, "brownian", 0.3, 0.01, 20.0, 1e-8, scheme, precision="df64",
+                                   tau0=0.01)
+    assert st["status"] == ost["status"] == 0
+    assert (st["accepted"], st["rejected"]) == (ost["accepted"], ost["rejected"])
+    assert np.linalg.norm(n - m) <= 1e-9 * np.linalg.norm(m)

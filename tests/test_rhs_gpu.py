@@ -16,7 +16,7 @@ from synth import kernel_factors, random_factors, random_state, sample_state
 
 pytestmark = pytest.mark.gpu
 
-RTOL = {"fp64": 1e-10, "fp32conv": 1e-4}
+RTOL = {"fp64": 1e-10, "fp32conv": 1e-4, "df64": 1e-10}
 
 
 @pytest.fixture(scope="module")
@@ -202,3 +202,40 @@ def test_rhs_bad_schedule_rejected(smol):
     U, V = kernel_factors("brownian", 64, a=0.5)
     with pytest.raises(smol.SmolError):
         smol.System(U, V, 0.0, fft_g=3)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 17, 100, 1000, 4096, 65537, 131072])
+@pytest.mark.parametrize("kind,a", [("const", 0.0), ("brownian", 0.9), ("brownian_const", 1.0 / 3.0)])
+def test_rhs_df64(smol, M, kind, a):
+    """The double-float form meets the FP64 tolerance at every size."""
+    U, V = kernel_factors(kind, M, a=a)
+    check_rhs(smol, sample_state(M, 0.01, seed=M + 1), U, V, 0.01, precision="df64")
+
+
+def test_rhs_df64_scaled_states_and_random_factors(smol):
+    """Per-transform power-of-two scaling keeps the double-float spectra in FP32's
+    exponent range for dilute and dense states; non-symmetric factors (T = 2R)."""
+    M = 4096
+    U, V = kernel_factors("brownian", M, a=0.6)
+    for mag in (1e-12, 1e12):
+        check_rhs(smol, sample_state(M, 0.01) * mag, U, V, 0.01, precision="df64")
+    U, V = random_factors(1500, 4, seed=9)
+    check_rhs(smol, random_state(1500, seed=4), U, V, 0.2, precision="df64")
+
+
+def test_rhs_df64_full_size_sampled_direct_entries(smol):
+    """M = 2^17 in the double-float form: sampled outputs against the direct O(M)
+    per-entry sums of Eq. (4) at the FP64 tolerance."""
+    import torch
+    M, a, lam = 131072, 0.9, 0.005
+    U, V = kernel_factors("brownian", M, a=a)
+    n = sample_state(M, lam, seed=11)
+    sysm = smol.System(U, V, lam, precision="df64")
+    S = sysm.rhs(torch.from_numpy(n).cuda()).cpu().numpy()
+    b, l, _ = (t.cpu().numpy() for t in sysm.rhs_terms(torch.from_numpy(n).cuda()))
+    rng = np.random.default_rng(0)
+    sizes = sorted(set([2, 3, M // 2, M - 1, M] + list(rng.integers(2, M + 1, 40))))
+    ref = oracle.rhs_entries_direct(n, lambda i, j: (i / j) ** a + (j / i) ** a, lam, sizes)
+    got = S[np.array(sizes) - 1]
+    scale = np.max(np.abs(b)) + np.abs(l[np.array(sizes) - 1])
+    assert np.all(np.abs(got - ref) <= 1e-10 * scale), np.max(np.abs(got - ref) / scale)
