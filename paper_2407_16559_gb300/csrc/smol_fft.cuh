@@ -102,11 +102,16 @@ __device__ __forceinline__ void divmod(const Div& D, int x, int& q, int& r) {
     }
 }
 
-// Length-4 DFT in place (forward: W_4 = -i; INV: +i).
-template <typename R, bool INV>
-__device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3) {
+// The transform direction is a run-time argument (inv: the sign +i, the unnormalised
+// inverse). Both directions compute the same sums and products (the rotations differ
+// only in signs and in which of them goes to the real part).
+
+// Length-4 DFT in place (forward: W_4 = -i; inverse: +i).
+template <typename R>
+__device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3, bool inv) {
     const cx<R> s0 = x0 + x2, d0 = x0 - x2, s1 = x1 + x3;
-    const cx<R> d1 = INV ? mul_pi(x1 - x3) : mul_mi(x1 - x3);
+    const cx<R> t = x1 - x3;
+    const cx<R> d1 = inv ? mul_pi(t) : mul_mi(t);
     x0 = s0 + s1;
     x2 = s0 - s1;
     x1 = d0 + d1;
@@ -115,22 +120,19 @@ __device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3)
 
 // Length-8 DFT in place: a radix-2 split (u_m +- u_{m+4}, the difference rotated by
 // W_8^m), then two length-4 DFTs giving the even and the odd outputs.
-template <typename R, bool INV>
-__device__ __forceinline__ void dft8(cx<R>* u) {
+template <typename R>
+__device__ __forceinline__ void dft8(cx<R>* u, bool inv) {
     const R h = sqrt_half<R>();
     cx<R> a0 = u[0] + u[4], a1 = u[1] + u[5], a2 = u[2] + u[6], a3 = u[3] + u[7];
     cx<R> b0 = u[0] - u[4], b1 = u[1] - u[5], b2 = u[2] - u[6], b3 = u[3] - u[7];
-    if (INV) {
-        b1 = mk<R>((b1.x - b1.y) * h, (b1.x + b1.y) * h);    // * (1 + i)/sqrt 2
-        b2 = mul_pi(b2);                                     // * i
-        b3 = mk<R>(-(b3.x + b3.y) * h, (b3.x - b3.y) * h);   // * (-1 + i)/sqrt 2
-    } else {
-        b1 = mk<R>((b1.x + b1.y) * h, (b1.y - b1.x) * h);    // * (1 - i)/sqrt 2
-        b2 = mul_mi(b2);                                     // * -i
-        b3 = mk<R>((b3.y - b3.x) * h, -(b3.x + b3.y) * h);   // * (-1 - i)/sqrt 2
-    }
-    dft4<R, INV>(a0, a1, a2, a3);
-    dft4<R, INV>(b0, b1, b2, b3);
+    // b1 * (1 -+ i)/sqrt 2, b2 * (-+ i), b3 * (-1 -+ i)/sqrt 2 (upper sign: forward)
+    const R s1 = (b1.x + b1.y) * h, d1 = (b1.x - b1.y) * h;
+    const R s3 = (b3.x + b3.y) * h, d3 = (b3.x - b3.y) * h;
+    b1 = inv ? mk<R>(d1, s1) : mk<R>(s1, -d1);
+    b2 = inv ? mul_pi(b2) : mul_mi(b2);
+    b3 = inv ? mk<R>(-s3, d3) : mk<R>(-d3, -s3);
+    dft4<R>(a0, a1, a2, a3, inv);
+    dft4<R>(b0, b1, b2, b3, inv);
     u[0] = a0;
     u[1] = b0;
     u[2] = a1;
@@ -145,10 +147,10 @@ __device__ __forceinline__ void dft8(cx<R>* u) {
 // length-P transform over G interleaved sequences: for butterfly i in [0, P/RAD),
 // k = i mod p, inputs in[i + m P/RAD] (m < RAD) are multiplied by W_{RAD p}^{m k},
 // transformed by a length-RAD DFT and stored at out[(i-k) RAD + k + m p].
-// twP is a shared-memory table twP[e] = W_P^e, e < P (conjugated for INV).
-template <typename R, bool INV, int RAD>
+// twP is a shared-memory table twP[e] = W_P^e, e < P (conjugated for the inverse).
+template <typename R, int RAD>
 __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>* __restrict__ b, int lgP, int lgp,
-                                              int G, const cx<R>* __restrict__ twP) {
+                                              int G, const cx<R>* __restrict__ twP, bool inv) {
     constexpr int LGR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
     const int P = 1 << lgP;
     const int p = 1 << lgp;
@@ -167,14 +169,14 @@ __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>
 #pragma unroll
             for (int m = 1; m < RAD; ++m) {
                 cx<R> w = twP[(m * k) << sh];
-                if (INV) w = conj(w);
+                if (inv) w = conj(w);
                 u[m] = u[m] * w;
             }
         }
         if (RAD == 8) {
-            dft8<R, INV>(u);
+            dft8<R>(u, inv);
         } else if (RAD == 4) {
-            dft4<R, INV>(u[0], u[1], u[2], u[3]);
+            dft4<R>(u[0], u[1], u[2], u[3], inv);
         } else {
             const cx<R> t = u[0] - u[1];
             u[0] = u[0] + u[1];
@@ -189,22 +191,23 @@ __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>
 // Stockham autosort FFT of length P = 2^lgP on G interleaved sequences held in shared
 // memory as buf[p * G + g] (g fastest), radix-8 passes first, then one radix-4 or
 // radix-2 pass for the remaining factor. Ping-pongs between a and b and returns the
-// buffer holding the result, in natural order. INV selects the sign +i (unnormalised
+// buffer holding the result, in natural order. inv selects the sign +i (unnormalised
 // inverse). twP: shared table W_P^e, e < P. Every thread of the block must call it;
 // the caller synchronises before.
-template <typename R, bool INV>
-__device__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ twP) {
+template <typename R>
+__device__ __forceinline__ cx<R>* tile_fft_body(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ twP,
+                                                bool inv) {
     int lgp = 0;
     while (lgp < lgP) {
         const int rem = lgP - lgp;
         if (rem >= 3) {
-            stockham_pass<R, INV, 8>(a, b, lgP, lgp, G, twP);
+            stockham_pass<R, 8>(a, b, lgP, lgp, G, twP, inv);
             lgp += 3;
         } else if (rem == 2) {
-            stockham_pass<R, INV, 4>(a, b, lgP, lgp, G, twP);
+            stockham_pass<R, 4>(a, b, lgP, lgp, G, twP, inv);
             lgp += 2;
         } else {
-            stockham_pass<R, INV, 2>(a, b, lgP, lgp, G, twP);
+            stockham_pass<R, 2>(a, b, lgP, lgp, G, twP, inv);
             lgp += 1;
         }
         __syncthreads();
@@ -213,6 +216,11 @@ __device__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __re
         b = t;
     }
     return a;
+}
+template <typename R>
+__device__ __forceinline__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ twP,
+                                           bool inv) {
+    return tile_fft_body<R>(a, b, lgP, G, twP, inv);
 }
 
 // Asynchronous global -> shared copies of one element (4, 8 or 16 bytes; both addresses

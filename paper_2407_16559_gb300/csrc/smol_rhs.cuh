@@ -628,7 +628,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
         const int t = threadIdx.x >> 1;
         S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
     }
-    cx<R>* res = tile_fft<R, false>(a, b, S.lgN1, GT, m.twP);
+    cx<R>* res = tile_fft<R>(a, b, S.lgN1, GT, m.twP, false);
     cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
     const Div DGT = mkdiv(GT);
     for (int idx = threadIdx.x; idx < N1 * GT; idx += blockDim.x) {
@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     cp_async_wait();
     stage_tw_fix(twP, S.lgN2, S.lgMp);
     __syncthreads();
-    cx<R>* Z = tile_fft<R, false>(a, b, S.lgN2, G, twP);
+    cx<R>* Z = tile_fft<R>(a, b, S.lgN2, G, twP, false);
     cx<R>* Yo = (Z == a) ? b : a;  // packed inverse spectrum, [k2 * 2 + rho]
     const int ntask = blk ? N2 : N2 + 1;
     for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
         if (k2a != k2b || rhoa != rhob) Yo[k2b * 2 + rhob] = Yb;
     }
     __syncthreads();
-    cx<R>* res = tile_fft<R, true>(Yo, Z, S.lgN2, 2, twP);
+    cx<R>* res = tile_fft<R>(Yo, Z, S.lgN2, 2, twP, true);
     cx<R>* G2 = reinterpret_cast<cx<R>*>(S.G2);
     for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
         const int n2 = idx & (N2 - 1);
@@ -908,7 +908,7 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
     cp_async_wait();
     stage_tw_fix(m.twP, S.lgN1, S.lgMp);
     __syncthreads();
-    cx<R>* res = tile_fft<R, true>(a, b, S.lgN1, G, m.twP);
+    cx<R>* res = tile_fft<R>(a, b, S.lgN1, G, m.twP, true);
     const R scale = rs[0], bscale = rs[1], lam1 = rs[2], s1r = rs[3], l1r = rs[4];
     const double src = src_s;
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
