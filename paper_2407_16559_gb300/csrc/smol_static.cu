@@ -46,7 +46,8 @@ constexpr size_t OFF_RSC = OFF_MAPB + al((size_t)1024 * sizeof(int2));
 constexpr size_t SCRATCH_BYTES = OFF_RSC + al((size_t)(MAXT + 2) * 8 + 2 * MAXT * 4);
 
 // The scratch memory of smol_rhs_static.
-static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];  // 15,320,320 bytes
+static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
+static_assert(SCRATCH_BYTES == 15320576, "the scratch size documented in smol.h");
 
 constexpr int MAX_DEVICES = 64;
 unsigned char* g_scratch_ptr[MAX_DEVICES];  // device address of g_scratch per device
