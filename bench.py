@@ -38,8 +38,10 @@ if ROOT not in sys.path:
 WORKLOAD = dict(name="oscill_M131072_brownian0.9_rkf45", M=131072, a=0.9, lam=0.005, tol=1e-8, t1=5000.0,
                 t_setup=5.0, scheme="rkf45")
 EVALS_PER_STEP = 6          # RKF45 stages
-LAUNCHES_PER_STEP = 13      # forward columns, 6 x row kernel, 5 x fused inverse+forward columns,
-                            # fused last inverse + combination / control (19 with fusion off)
+LAUNCHES_FUSED = 13         # forward columns, 6 x row kernel, 5 x fused inverse+forward columns,
+                            # fused last inverse + combination / control
+LAUNCHES_UNFUSED = 19       # 6 x (forward columns, rows, inverse columns) + combination / control
+FLAG_NO_FUSE = 32           # smol_opts.flags bit (SMOL_FLAG_NO_FUSE)
 L2_FLUSH_BYTES = 256 << 20
 
 # Measured peaks (MEASURED_PEAKS.json of this machine, written by the pool's driver; read
@@ -370,7 +372,8 @@ def gpu_arm(args):
                        schedule=sched or "rule (untuned)"),
         "accepted_steps_per_s": accepted_per_s,
         "attempts": {"accepted": stats["accepted"], "rejected": stats["rejected"], "t_end": stats["t"]},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * K,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K * (LAUNCHES_UNFUSED if sched.get("flags", 0) & FLAG_NO_FUSE
+                                                        else LAUNCHES_FUSED),
         "clocks": clocks,
     }
     if args.both and precision == "fp64":
