@@ -20,6 +20,9 @@
  *   linear convolution computed with zero-padded FFTs, and the death and monomer
  *   terms from rank-R moment sums, O(M R log M) per evaluation (Sec. 1, Sec. 2).
  *
+ *   Constant point sources (Eq. (3), Sec. 3.1): dn_s/dt = S_s(n) + P_s
+ *   (smol_set_sources); with lambda = 0 that is aggregation with sources.
+ *
  *   Operator form (Eq. (5)): dn/dt = S(n), n(0) = n_0, integrated with the explicit
  *   RK2, RK4 and Runge-Kutta-Fehlberg 4(5) schemes of Sec. 2 with adaptive steps:
  *   step doubling for RK2 / RK4 (error ||n_hat - n||_2, Eq. (6) or the halve/double
@@ -34,9 +37,11 @@
  *   - Work is enqueued on the stream given in smol_opts.stream (NULL = legacy
  *     default stream). smol_rhs returns without synchronising; smol_integrate
  *     synchronises that stream once before it returns.
- *   - The library never allocates device memory: every device buffer it uses lives
- *     in the caller's workspace (smol_workspace_bytes) or is a caller argument.
- *     It allocates a small pinned host block per system for status read-back.
+ *   - The library never allocates device memory on the solver's path: every device
+ *     buffer it uses lives in the caller's workspace (smol_workspace_bytes) or is a
+ *     caller argument. It allocates a small pinned host block per system for status
+ *     read-back. The set-up calls smol_tune and smol_batch_tune allocate and free
+ *     their own scratch.
  */
 #ifndef SMOL_H
 #define SMOL_H
