@@ -241,7 +241,7 @@ int smol_set_sources(smol_system* sys, int32_t count, const int64_t* sizes, cons
  * Sec. 1). For one system of the given problem it times `attempts` step attempts of
  * `scheme` at tolerance tol, after one warm-up chunk, for each candidate schedule:
  *   - log2 N1 of the four-step split Mp = N1 N2: the rule's value and one either side;
- *   - columns per CTA of the column kernels: the rule's value and twice it;
+ *   - columns per CTA of the column kernels: the rule's value, twice and four times it;
  *   - launch mode: programmatic dependent launch for every kernel, for none, or for
  *     all but the forward column kernel; fused column passes (default) or not.
  * Candidates whose shared memory does not fit are skipped. *opts is read as the base

@@ -1367,9 +1367,9 @@ int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double
         const int lg = def.lgN1 + dl;
         if (lg < 1 || lg >= def.lgMp) continue;
         const int g0 = make_shape(M, base.precision, false, lg, 0).G;
-        for (int gm : {1, 2}) {
+        for (int gm : {1, 2, 4}) {
             const int g = g0 * gm;
-            if (g > 64 || g > (1 << (def.lgMp - lg)) || (gm > 1 && g0 * gm == g0)) continue;
+            if (g > 64 || g > (1 << (def.lgMp - lg))) continue;  // beyond the columns there are
             smol_opts c = base;
             c.fft_lgn1 = lg;
             c.fft_g = g;

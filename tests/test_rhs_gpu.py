@@ -89,13 +89,15 @@ def test_rhs_lambda(smol, lam):
     check_rhs(smol, sample_state(M, lam), U, V, lam)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
 @pytest.mark.parametrize("M,R", [(50, 1), (300, 3), (1500, 4), (4096, 8)])
-def test_rhs_random_nonsymmetric_factors(smol, M, R):
-    """Non-symmetric factors with no shared transforms (T = 2R): a transposed U / V or
-    a wrong pairing in the spectral product fails the loss or source term."""
+def test_rhs_random_nonsymmetric_factors(smol, M, R, precision):
+    """Non-symmetric factors with no shared transforms (T = 2R, up to 16: beyond the
+    column kernels' weight prefetch of 4): a transposed U / V or a wrong pairing in the
+    spectral product fails the loss or source term."""
     U, V = random_factors(M, R, seed=5 * M + R)
     n = random_state(M, seed=M)
-    s = check_rhs(smol, n, U, V, 0.2)
+    s = check_rhs(smol, n, U, V, 0.2, precision=precision)
     assert s.num_transforms == 2 * R
 
 
