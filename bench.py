@@ -56,7 +56,13 @@ FIXED_SCHEDULE = {}
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
 # (precision, kernel class); valid only while the kernel sources are unchanged.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/k_rows_M131072_fp64.md, profiles/k_inv_fwd_M131072_fp32conv.md (read + write)
+    ("fp64", "rows"): {"bytes": 8503552.0, "src": "e1a2230da4f0dcbe"},
+    ("fp64", "inv_fwd"): {"bytes": 8479744.0, "src": "e1a2230da4f0dcbe"},
+    ("fp32conv", "inv_fwd"): {"bytes": 4269568.0, "src": "e1a2230da4f0dcbe"},
+    ("fp32conv", "rows"): {"bytes": 4297472.0, "src": "e1a2230da4f0dcbe"},
+}
 
 
 def src_digest() -> str:
