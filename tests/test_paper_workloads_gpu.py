@@ -97,3 +97,38 @@ def test_tables_rkf45_counts_in_range(smol):
         _, st = s.integrate(torch.from_numpy(monodisperse(M)).cuda(), 0.0, 200.0, tol)
         assert st["status"] == 0
         assert printed / 3 <= st["rhs_evals_paper"] <= 3 * printed, (tol, st["rhs_evals_paper"])
+
+
+def test_config4_reduced_precision_trajectories(smol):
+    """The relaxation workload (M = 2^16, Brownian 1/3 + constant 2, lambda = 0.1, RKF45,
+    tol 1e-9) in the FP32 form and in the double-float form against the FP64 solver at
+    log-spaced checkpoints: the double-float form follows the FP64 trajectory to the
+    tolerance's level with the same amount of work; the FP32 form stays within 1e-3 early
+    on (its error estimate carries FFT rounding of ~1e-7 relative, which the controller at
+    tol 1e-9 cannot tell from truncation error)."""
+    import torch
+    M = 65536
+    U, V = kernel_factors("brownian_const", M, a=1.0 / 3.0)
+    k = np.arange(1, M + 1, dtype=np.float64)
+
+    def run(precision, ts):
+        s = smol.System(U, V, 0.1, precision=precision, tau0=1e-3)
+        n = torch.from_numpy(monodisperse(M)).cuda()
+        t, out, att = 0.0, [], 0
+        for tc in ts:
+            n, st = s.integrate(n, t, float(tc), 1e-9, inplace=True)
+            assert st["status"] == 0
+            t, att = tc, att + st["attempts"]
+            out.append(n.cpu().numpy().copy())
+        return out, att
+
+    ts = np.logspace(-1, 2, 10)
+    ref, att64 = run("fp64", ts)
+    dd, attdd = run("df64", ts)
+    for a, b in zip(dd, ref):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
+    assert abs(attdd - att64) <= 0.15 * att64  # near-boundary decisions round differently
+    assert abs(np.dot(k, dd[-1]) - np.dot(k, ref[-1])) <= 1e-9
+    f32, _ = run("fp32conv", ts[:6])
+    for a, b in zip(f32, ref[:6]):
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
