@@ -1,6 +1,8 @@
-// smol_rhs.cuh - device data structures and the three kernels of one evaluation of
-// the right-hand side S(y) of Eq. (4) (aggregation-shattering, truncated at M) for a
-// low-rank kernel K = U V (Sec. 1), for one system or a ragged batch of systems.
+// smol_rhs.cuh - device data structures and the kernels of one evaluation of the
+// right-hand side S(y) of Eq. (4) (aggregation-shattering, truncated at M; with the
+// point sources of Eq. (3)) for a low-rank kernel K = U V (Sec. 1), for one system or a
+// ragged batch of systems: the forward column pass, the row kernel (with the scalar
+// CTA), the inverse column pass, and the fused inverse + forward column kernel.
 //
 // Notation. Sizes s = 1..M are stored 0-based (y[s-1] = y_s). The distinct vectors
 // among the columns U_alpha and rows V_alpha are W_t (t < T); U_alpha = cu W_{u(alpha)},
@@ -26,7 +28,8 @@
 // the birth term are applied in the epilogue).
 //
 // Precision. R is the arithmetic type of everything inside S(y) and of the stage
-// vectors k_j = h S(y_j): double for the plain FP64 solver, float for the FP32 form.
+// vectors k_j = h S(y_j): double for the plain FP64 solver, float for the FP32 form,
+// dd (double-float, smol_dd.cuh) for the FP64-accurate form on the FP32 pipes.
 // The state n and its update, the error estimate, the step control and the mass
 // moment are always FP64 (they are handled in smol_int.cuh); the moment sums are
 // accumulated per thread in R and reduced across threads in FP64.
