@@ -240,8 +240,9 @@ def reference_arm(args):
     line = {
         "impl": "reference", "metric": "rhs_evals_per_s", "value": v, "unit": "RHS evals/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": config_dict("fp64"),
+        "ms_per_step": EVALS_PER_STEP * 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(config_dict("fp64"), n0="monodisperse, oracle attempts from t = 0"),
         "cpu_baseline": {"value": v, "unit": "RHS evals/s", "cores": 1, "kind": "oracle",
                          "sample": f"{res['evals']} evaluations of S(n) (numpy-FFT route) inside oracle RKF45 "
                                    f"attempts at M=2^17 from the monodisperse start, one thread"},
