@@ -202,8 +202,10 @@ int smol_integrate(smol_system* sys, double* d_n, double t0, double t1, double t
  *   smol_integrate_advance: enqueues one graph launch (that many attempts) on the
  *                           stream and returns at once. Attempts after termination
  *                           (t1 reached or a status set) do no work.
- *   smol_integrate_finish:  synchronises the stream, writes the state back to d_n and
- *                           fills *stats; returns the status like smol_integrate.
+ *   smol_integrate_finish:  writes the state back to d_n (on the device), synchronises
+ *                           the stream once and fills *stats; returns the status like
+ *                           smol_integrate. Further smol_integrate_advance calls then
+ *                           continue the same run from d_n.
  * smol_integrate is start + advance until done + finish. */
 int smol_integrate_start(smol_system* sys, double* d_n, double t0, double t1, double tol, int32_t scheme);
 int smol_integrate_advance(smol_system* sys);

@@ -315,8 +315,7 @@ class Batch:
         rc = _lib.smol_batch_integrate_finish(self._h, st)
         if rc in (EINVAL, ECUDA):
             raise SmolError(rc, "smol_batch_integrate_finish")
-        ns, self._run = self._run, None
-        return ns, [s.as_dict() for s in st]
+        return self._run, [s.as_dict() for s in st]  # the run may continue after finish
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -447,8 +446,7 @@ class System:
         rc = _lib.smol_integrate_finish(self._h, ctypes.byref(st))
         if rc in (EINVAL, ECUDA):
             raise SmolError(rc, "smol_integrate_finish")
-        n, self._run = self._run, None
-        return n, st.as_dict()
+        return self._run, st.as_dict()  # the run may continue (advance) after finish
 
     PROF_KINDS = ("fwd_cols", "rows", "inv_cols", "step", "inv_fwd", "inv_step")
 

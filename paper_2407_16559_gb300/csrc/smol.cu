@@ -285,6 +285,8 @@ struct Engine {
     size_t smemC = 0, smemB = 0;
     int thrC = 32, thrB = 32;
     Ctl* h_ctl = nullptr;  // pinned host copies of the control blocks
+    cudaEvent_t ev_rb[2] = {nullptr, nullptr};  // completions of read-backs into h_ctl
+    cudaEvent_t ev_hctl = nullptr;  // the last stream operation that reads or writes h_ctl
     cudaGraphExec_t gexec = nullptr;
     int64_t gkey = -1;
     std::vector<int64_t> last_attempts;
@@ -892,6 +894,8 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     E->hs = hs;
     E->hsr = hsr;
     CK(cudaHostAlloc((void**)&E->h_ctl, (size_t)count * sizeof(Ctl), cudaHostAllocDefault));
+    for (cudaEvent_t* e : {&E->ev_rb[0], &E->ev_rb[1], &E->ev_hctl})
+        CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
     if (prec == SMOL_FP32CONV) return set_smem_attrs<float>(E);
     if (prec == SMOL_DF64) return set_smem_attrs<dd>(E);
@@ -903,6 +907,8 @@ void engine_free(Engine* E) {
     if (E->gexec) cudaGraphExecDestroy(E->gexec);
     if (E->cap) cudaStreamDestroy(E->cap);
     if (E->h_ctl) cudaFreeHost(E->h_ctl);
+    for (cudaEvent_t e : {E->ev_rb[0], E->ev_rb[1], E->ev_hctl})
+        if (e) cudaEventDestroy(e);
 }
 
 int check_opts(const smol_opts& o) {
@@ -922,8 +928,9 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
     const bool fixed = E->o.fixed_tau > 0.0;
     if (!fixed && !(tol > 0.0)) return SMOL_EINVAL;
     cudaStream_t st = E->stream;
-    // the pinned blocks may still be the target of an earlier read-back: wait for it
-    CK(cudaStreamSynchronize(st));
+    // the pinned blocks may still be read or written by an earlier copy: wait for that
+    // copy only (not for the rest of the stream)
+    CK(cudaEventSynchronize(E->ev_hctl));
     for (int q = 0; q < E->count; ++q) {
         Ctl& h = E->h_ctl[q];
         memset(&h, 0, sizeof(h));
@@ -936,6 +943,7 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
         h.state[1] = (double*)(E->ws + E->base[q] + E->lay[q].stateB);
     }
     CK(cudaMemcpyAsync(E->d_ctl, E->h_ctl, (size_t)E->count * sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(E->ev_hctl, st));
     const LaunchArgs A = args_for(E, false);
     if (E->o.precision == SMOL_FP32CONV) {
         k_prep1<float><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
@@ -1009,26 +1017,23 @@ void fill_stats(const Ctl& c, smol_stats* s) {
 int integrate_finish(Engine* E, smol_stats* stats) {
     if (!E || !E->running) return SMOL_EINVAL;
     cudaStream_t st = E->stream;
+    // the state back into the callers' buffers (on the device), then one read-back of
+    // the control blocks and one synchronisation
+    const LaunchArgs A = args_for(E, false);
+    if (E->o.precision == SMOL_FP32CONV) k_restore<float><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
+    else if (E->o.precision == SMOL_DF64) k_restore<dd><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
+    else k_restore<double><<<E->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(E->h_ctl, E->d_ctl, (size_t)E->count * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(E->ev_hctl, st));
     CK(cudaStreamSynchronize(st));
-    std::vector<Ctl> fin(E->count);
-    CK(cudaMemcpy(fin.data(), E->d_ctl, (size_t)E->count * sizeof(Ctl), cudaMemcpyDeviceToHost));
     int rc = SMOL_OK;
-    bool moved = false;
     for (int q = 0; q < E->count; ++q) {
-        if (fin[q].cur == 1) {
-            CK(cudaMemcpyAsync(E->run_dn[q], fin[q].state[1], (size_t)E->sh[q].M * 8, cudaMemcpyDeviceToDevice, st));
-            moved = true;
-        }
-        E->last_attempts[q] = fin[q].attempts;
-        if (stats) fill_stats(fin[q], stats + q);
-        if (fin[q].status < 0 && rc >= 0) rc = fin[q].status;
-        else if (fin[q].status == SMOL_STEADY && rc == SMOL_OK) rc = SMOL_STEADY;
-    }
-    if (moved) {
-        // the callers' buffers hold the states again: later advances continue from there
-        for (int q = 0; q < E->count; ++q) fin[q].cur = 0;
-        CK(cudaMemcpyAsync(E->d_ctl, fin.data(), (size_t)E->count * sizeof(Ctl), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
+        const Ctl& c = E->h_ctl[q];
+        E->last_attempts[q] = c.attempts;
+        if (stats) fill_stats(c, stats + q);
+        if (c.status < 0 && rc >= 0) rc = c.status;
+        else if (c.status == SMOL_STEADY && rc == SMOL_OK) rc = SMOL_STEADY;
     }
     return rc;
 }
@@ -1046,17 +1051,17 @@ int integrate_all(Engine* E, double* const* d_n, double t0, double t1, double to
     if (!(t1 > t0)) return integrate_finish(E, stats);  // nothing to integrate
     cudaStream_t st = E->stream;
     // Launch chunks, keeping one in flight while the status of the previous one is read
-    // from pinned copies of the control blocks.
-    cudaEvent_t ev[2];
-    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    // from pinned copies of the control blocks. A run that one chunk covers
+    // (max_attempts <= chunk) reads nothing back before integrate_finish.
+    cudaEvent_t* ev = E->ev_rb;
     const size_t cbytes = (size_t)E->count * sizeof(Ctl);
     const int64_t maxa = E->o.max_attempts;
     int64_t launched = E->run_attempts;  // attempts enqueued so far
     int cur = 0;
-    if (cudaGraphLaunch(E->gexec, st) != cudaSuccess ||
-        cudaMemcpyAsync(E->h_ctl, E->d_ctl, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaEventRecord(ev[cur], st) != cudaSuccess)
+    if (cudaGraphLaunch(E->gexec, st) != cudaSuccess) rc = SMOL_ECUDA;
+    if (rc == SMOL_OK && launched < maxa &&
+        (cudaMemcpyAsync(E->h_ctl, E->d_ctl, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaEventRecord(ev[cur], st) != cudaSuccess || cudaEventRecord(E->ev_hctl, st) != cudaSuccess))
         rc = SMOL_ECUDA;
     while (rc == SMOL_OK && launched < maxa) {
         if (cudaGraphLaunch(E->gexec, st) != cudaSuccess) {
@@ -1068,19 +1073,19 @@ int integrate_all(Engine* E, double* const* d_n, double t0, double t1, double to
             rc = SMOL_ECUDA;
             break;
         }
-        if (all_done(E)) break;
+        if (all_done(E) || launched >= maxa) break;
         if (cudaMemcpyAsync(E->h_ctl, E->d_ctl, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaEventRecord(ev[cur ^ 1], st) != cudaSuccess) {
+            cudaEventRecord(ev[cur ^ 1], st) != cudaSuccess || cudaEventRecord(E->ev_hctl, st) != cudaSuccess) {
             rc = SMOL_ECUDA;
             break;
         }
         cur ^= 1;
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) rc = SMOL_ECUDA;
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-    if (rc != SMOL_OK) return rc;
-    return integrate_finish(E, stats);
+    if (rc != SMOL_OK) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    return integrate_finish(E, stats);  // synchronises once
 }
 
 int get_log(Engine* E, int q, double* h_t, double* h_tau, double* h_err, int32_t* h_acc, int32_t cap,

@@ -578,6 +578,34 @@ __global__ void __launch_bounds__(256) k_inv_finish(const SysDev* __restrict__ s
     fin_tail<R>(S, P, S.ctl, cs, bx, S.nbx, acc, f);
 }
 
+// End of an integration: where the current state is the engine's second buffer, copy it
+// and its R-typed shadow to the caller's buffer and make that buffer current (the last
+// CTA of the system, after all copies), so that the caller's vector holds the result
+// and later attempts continue from it. Runs on the device: the host learns the outcome
+// with the statistics, after a single synchronisation.
+template <typename R>
+__global__ void __launch_bounds__(128) k_restore(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                                 const __grid_constant__ SysDev one) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ bool last;
+    const int blk = load_sys(sysv, map, one, S, cv);
+    if (!cv.cur) return;
+    double* dst = const_cast<double*>(cv.s0);
+    const double* src = cv.s1;
+    for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) dst[i] = __ldcg(src + i);
+    if (S.shadow0) {
+        R* sd = reinterpret_cast<R*>(S.shadow0);
+        const R* ss = reinterpret_cast<const R*>(S.shadow1);
+        for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) sd[i] = ss[i];
+    }
+    if (!arrive_last(S.ctl, S.nfin, &last)) return;
+    if (threadIdx.x == 0) {
+        S.ctl->arrive = 0;
+        S.ctl->cur = 0;
+    }
+}
+
 // Preparation of an integration, pass 1: moments mu_t of n0, ||n0||^2, max|n0| and
 // sum_s s n0_s, in FP64 (the weights are read in type R). The last CTA of each system
 // stores nrm2, ymax and mass in the control block and delta_t = sum_{alpha: u=t} coef

@@ -240,3 +240,27 @@ def test_df64_adaptive_parity(smol, scheme):
     assert st["status"] == ost["status"] == 0
     assert (st["accepted"], st["rejected"]) == (ost["accepted"], ost["rejected"])
     assert np.linalg.norm(n - m) <= 1e-9 * np.linalg.norm(m)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
+def test_finish_then_advance_continues(smol, precision):
+    """smol_integrate_finish leaves the state in the caller's vector and the run able to
+    continue: start, two chunks, finish, one more chunk, finish equals start, three
+    chunks, finish (bit for bit; the reduced-precision forms also carry their shadow
+    of the state across)."""
+    import torch
+    M = 4096
+    U, V = kernel_factors("brownian", M, a=0.5)
+    outs = []
+    for split in (True, False):
+        s = smol.System(U, V, 0.02, precision=precision, tau0=1e-3, chunk=3)
+        n = s.start(torch.from_numpy(monodisperse(M)).cuda(), 0.0, 50.0, 1e-8)
+        s.advance()
+        s.advance()
+        if split:
+            n, st = s.finish()
+            assert st["attempts"] == 6
+        s.advance()
+        n, st = s.finish()
+        outs.append((n.cpu().numpy(), st["attempts"], st["accepted"]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
