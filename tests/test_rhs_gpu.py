@@ -241,3 +241,17 @@ def test_rhs_df64_full_size_sampled_direct_entries(smol):
     got = S[np.array(sizes) - 1]
     scale = np.max(np.abs(b)) + np.abs(l[np.array(sizes) - 1])
     assert np.all(np.abs(got - ref) <= 1e-10 * scale), np.max(np.abs(got - ref) / scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
+def test_rhs_at_maximum_size(smol, precision):
+    """The largest M the kernels take for R = 2 (smol_max_m; the row tiles' shared
+    memory sets it): parity with the oracle's FFT route there, and the next size is
+    refused with SMOL_EUNSUPPORTED."""
+    M = smol.max_m(2, precision)
+    U, V = kernel_factors("brownian", M, a=0.7)
+    check_rhs(smol, sample_state(M, 0.002, seed=5), U, V, 0.002, precision=precision, route="lowrank")
+    U1, V1 = kernel_factors("brownian", M + 1, a=0.7)
+    with pytest.raises(smol.SmolError) as e:
+        smol.System(U1, V1, 0.002, precision=precision)
+    assert e.value.code == smol.EUNSUPPORTED
