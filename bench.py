@@ -300,6 +300,35 @@ def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: 
     return ms, stats, prof_ms, prof_cnt, tsys, U, V, sched
 
 
+def roofline(precision: str, prof_ms: dict, prof_cnt: dict, T: int, sched: dict) -> dict:
+    """Roofline of the dominant kernel class of one form: FP64 against the FP64 pipe
+    (the bound of its FFTs), the FP32 and double-float forms against the measured copy
+    bandwidth (their bound in principle: they are latency-bound, and the fraction says
+    how far they are from streaming). Durations are the live CUDA-event means per
+    launch; work per launch from `algorithmic`."""
+    csz = 8 if precision == "fp32conv" else 16
+    fl, by = algorithmic(WORKLOAD["M"], T, csz, sched.get("fft_lgn1", 0))
+    per_step = {k: prof_ms[k] * prof_cnt[k] for k in prof_ms}
+    dom = max(("fwd_cols", "rows", "inv_cols", "inv_fwd"), key=lambda k: per_step.get(k, 0.0))
+    peaks, pk_src = measured_peaks()
+    if precision == "fp64":
+        achieved = fl[dom] / (prof_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "FP64 FMA pipe: 152 SMs x 2070 MHz x 2 DFMA/clk",
+                "algorithmic_per_launch": fl[dom]}
+    else:
+        pk = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+        achieved = by[dom] / (prof_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk, "unit": "GB/s",
+                "frac": achieved / pk, "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({pk_src})",
+                "algorithmic_per_launch": by[dom]}
+    tr = TRAFFIC.get((precision, dom))
+    roof["traffic"] = tr["bytes"] if tr and tr.get("src") == src_digest() else None
+    roof["kernel_ms"] = {k: round(v * 1000.0, 3) for k, v in prof_ms.items()}
+    roof["kernel_ms_unit"] = "us per launch (CUDA events, one kernel at a time)"
+    return roof
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -351,28 +380,7 @@ def gpu_arm(args):
     sopts = {k: v for k, v in sched.items() if k in smol.SCHEDULE_KEYS}
     e2e = e2e_leg(smol, torch, precision, max(10, min(K, 400)), U, V, stream, sopts)
 
-    # roofline of the dominant kernel class
-    Tn = tsys.num_transforms
-    csz = 8 if precision == "fp32conv" else 16
-    fl, by = algorithmic(WORKLOAD["M"], Tn, csz, sched.get("fft_lgn1", 0))
-    per_step = {k: prof_ms[k] * prof_cnt[k] / 10 for k in prof_ms}
-    dom = max(("fwd_cols", "rows", "inv_cols", "inv_fwd"), key=lambda k: per_step.get(k, 0.0))
-    peaks, pk_src = measured_peaks()
-    if precision == "fp64":
-        achieved = fl[dom] / (prof_ms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "FP64 FMA pipe: 152 SMs x 2070 MHz x 2 DFMA/clk",
-                "algorithmic_per_launch": fl[dom]}
-    else:
-        pk = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
-        achieved = by[dom] / (prof_ms[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk, "unit": "GB/s",
-                "frac": achieved / pk, "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({pk_src})",
-                "algorithmic_per_launch": by[dom]}
-    tr = TRAFFIC.get((precision, dom))
-    roof["traffic"] = tr["bytes"] if tr and tr.get("src") == src_digest() else None
-    roof["kernel_ms"] = {k: round(v * 1000.0, 3) for k, v in prof_ms.items()}
-    roof["kernel_ms_unit"] = "us per launch (CUDA events, one kernel at a time)"
+    roof = roofline(precision, prof_ms, prof_cnt, tsys.num_transforms, sched)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -399,6 +407,7 @@ def gpu_arm(args):
         v32 = world * EVALS_PER_STEP * K / (ms32 / 1000.0)
         line["fp32conv"] = {"value": v32, "ms_per_step": ms32 / K, "speedup_vs_fp64": v32 / value,
                             "kernel_us": {k: round(v * 1000.0, 3) for k, v in pm32.items()}, "schedule": sch32,
+                            "roofline": roofline("fp32conv", pm32, pc32, tsys32.num_transforms, sch32),
                             "rhs_rel_err_vs_fp64": rhs_accuracy(smol, torch, U, V)}
         # the FP64-accurate double-float form (FP64 parity tolerance 1e-10)
         msd, std_, pmd, pcd, tsysd, _, _, schd = time_form(smol, torch, "df64", K, W, stream, flush, rank,
@@ -406,6 +415,7 @@ def gpu_arm(args):
         vd = world * EVALS_PER_STEP * K / (msd / 1000.0)
         line["df64"] = {"value": vd, "ms_per_step": msd / K, "speedup_vs_fp64": vd / value,
                         "kernel_us": {k: round(v * 1000.0, 3) for k, v in pmd.items()}, "schedule": schd,
+                        "roofline": roofline("df64", pmd, pcd, tsysd.num_transforms, schd),
                         "rhs_rel_err_vs_fp64": rhs_accuracy(smol, torch, U, V, "df64"),
                         "note": "FFTs, products and element-wise terms in double-float (FP32 pairs) on the "
                                 "FP32 pipes; state, update, error, control in FP64; parity bar 1e-10 as FP64"}
