@@ -264,3 +264,20 @@ def test_finish_then_advance_continues(smol, precision):
         n, st = s.finish()
         outs.append((n.cpu().numpy(), st["attempts"], st["accepted"]))
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
+def test_mass_statistic_and_conservation(smol, precision):
+    """stats.mass is sum_s s n_s of the returned state (FP64 in every form); with the
+    distribution far from M the truncation flux is negligible and shattering conserves
+    mass, so it stays 1 to the integration error."""
+    import torch
+    M = 8192
+    U, V = kernel_factors("brownian", M, a=0.4)
+    n, st = smol.System(U, V, 0.05, precision=precision, tau0=1e-3).integrate(
+        torch.from_numpy(monodisperse(M)).cuda(), 0.0, 3.0, 1e-9)
+    assert st["status"] == 0
+    s = np.arange(1, M + 1, dtype=np.float64)
+    m = float(np.dot(s, n.cpu().numpy()))
+    assert abs(st["mass"] - m) <= 1e-13 * m
+    assert abs(m - 1.0) <= (1e-7 if precision != "fp32conv" else 1e-4)
