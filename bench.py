@@ -5,15 +5,16 @@ Workload (oscillatory regime): M = 2^17 sizes, kernel K_ij = (i/j)^0.9 + (j/i)^0
 with tol 1e-8 (Sec. 2 schemes, Eq. (4) system). Synthetic by definition: the paper's
 experiments are fully specified by (M, K, lambda, n0).
 
-One step = one RKF45 attempt: 6 evaluations of S(n), the stage combination, the
-embedded error norm and the step-size control, all on the device (13 kernel launches
+One step = one RKF45 attempt: 6 evaluations of S(n) (5 when it retries a rejected
+attempt, whose S(n^k) it keeps), the stage combination, the embedded error norm and the
+step-size control, all on the device (13 kernel launches
 with the column passes of consecutive evaluations fused, 19 without; captured in a CUDA
 graph). Before the timed steps the system is advanced from t = 0 to t = 5 (untimed), and
 the FFT schedule and launch mode are tuned (untimed), so that the attempts run
 mid-trajectory with the fastest schedule. The same workload is also timed in the FP32
 form and in the double-float form (FP64-accurate), and the 256-system batch.
-value = S evaluations per second over the K timed steps; accepted RK steps per second
-are reported beside it. L2 (129 MB) is flushed between steps by writing a 256 MB
+value = S evaluations made per second over the K timed steps (counted by the device);
+accepted RK steps per second are reported beside it. L2 (129 MB) is flushed between steps by writing a 256 MB
 buffer outside the timed events (the system's working set, ~35 MB, would otherwise
 stay resident).
 
@@ -46,6 +47,7 @@ LAUNCHES_FUSED = 13         # forward columns, 6 x row kernel, 5 x fused inverse
 LAUNCHES_UNFUSED = 19       # 6 x (forward columns, rows, inverse columns) + combination / control
 FLAG_NO_FUSE = 32           # smol_opts.flags bit (SMOL_FLAG_NO_FUSE)
 L2_FLUSH_BYTES = 256 << 20
+CTL_BYTES = 240             # the device control block of one system (smol::Ctl)
 
 # Measured peaks (MEASURED_PEAKS.json of this machine, written by the pool's driver; read
 # at run time when present) and the FP64 ALU peak: 152 SMs x 2070 MHz x 2 FP64 FMA per
@@ -256,7 +258,9 @@ def config_dict(precision: str):
     w = WORKLOAD
     return {"workload": w["name"], "M": w["M"], "kernel": f"(i/j)^{w['a']}+(j/i)^{w['a']} (rank 2)",
             "lambda": w["lam"], "n0": "monodisperse, advanced to t=5 before timing", "scheme": "rkf45",
-            "tol": w["tol"], "precision": precision, "step": "one RKF45 attempt (6 RHS evaluations)",
+            "tol": w["tol"], "precision": precision,
+            "step": "one RKF45 attempt (6 RHS evaluations; 5 when it retries a rejected step, whose S(n^k) "
+                    "it keeps); value counts the evaluations made",
             "l2": "flushed between timed steps (256 MB write outside the events)"}
 
 
@@ -284,7 +288,9 @@ def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: 
     run = tsys.start(n, st0["t"], w["t1"], w["tol"], scheme="rkf45")
     for _ in range(W):
         tsys.advance()
-    torch.cuda.synchronize()
+    # counters before the timed attempts (a retry of a rejected attempt reuses S(n^k),
+    # so evaluations are counted, not assumed; the run continues after finish)
+    _, stw = tsys.finish()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     with torch.cuda.stream(stream):
         for i in range(K):
@@ -294,10 +300,16 @@ def time_form(smol, torch, precision: str, K: int, W: int, stream, flush, rank: 
             ev[i][1].record(stream)
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    prof_ms, prof_cnt = tsys.profile(reps=10)
     run, stats = tsys.finish()
+    timed = {k: stats[k] - stw[k] for k in ("rhs_evals", "accepted", "rejected", "attempts")}
+    prof_ms, prof_cnt = tsys.profile(reps=10)
+    _, stp = tsys.finish()
+    # evaluations the profiled attempts skipped (retries keep S(n^k)): their forward and
+    # row launches return at once and their inverse pass only rescales k_1
+    prof_cnt["skipped"] = EVALS_PER_STEP * (stp["attempts"] - stats["attempts"]) - \
+        (stp["rhs_evals"] - stats["rhs_evals"])
     del run
-    return ms, stats, prof_ms, prof_cnt, tsys, U, V, sched
+    return ms, dict(stats, timed=timed), prof_ms, prof_cnt, tsys, U, V, sched
 
 
 def roofline(precision: str, prof_ms: dict, prof_cnt: dict, T: int, sched: dict) -> dict:
@@ -311,6 +323,14 @@ def roofline(precision: str, prof_ms: dict, prof_cnt: dict, T: int, sched: dict)
     per_step = {k: prof_ms[k] * prof_cnt[k] for k in prof_ms}
     dom = max(("fwd_cols", "rows", "inv_cols", "inv_fwd"), key=lambda k: per_step.get(k, 0.0))
     peaks, pk_src = measured_peaks()
+    # work per launch averaged over the profiled launches: a skipped evaluation (the retry
+    # of a rejected attempt) makes one forward-column and one row launch do nothing and
+    # one inverse pass only rescale k_1
+    n, sk = max(prof_cnt[dom], 1), prof_cnt.get("skipped", 0)
+    drop = {"fwd_cols": 1.0, "rows": 1.0, "inv_cols": 1.0, "inv_fwd": fl["inv_cols"] / fl["inv_fwd"]}[dom]
+    fl = dict(fl, **{dom: fl[dom] * (1.0 - drop * sk / n)})
+    drop_b = {"fwd_cols": 1.0, "rows": 1.0, "inv_cols": 1.0, "inv_fwd": by["inv_cols"] / by["inv_fwd"]}[dom]
+    by = dict(by, **{dom: by[dom] * (1.0 - drop_b * sk / n)})
     if precision == "fp64":
         achieved = fl[dom] / (prof_ms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -324,6 +344,7 @@ def roofline(precision: str, prof_ms: dict, prof_cnt: dict, T: int, sched: dict)
                 "algorithmic_per_launch": by[dom]}
     tr = TRAFFIC.get((precision, dom))
     roof["traffic"] = tr["bytes"] if tr and tr.get("src") == src_digest() else None
+    roof["profiled_evals_skipped"] = sk
     roof["kernel_ms"] = {k: round(v * 1000.0, 3) for k, v in prof_ms.items()}
     roof["kernel_ms_unit"] = "us per launch (CUDA events, one kernel at a time)"
     return roof
@@ -369,12 +390,9 @@ def gpu_arm(args):
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    timed_attempts = K
-    acc_timed = stats["accepted"]  # includes warm-up attempts; scaled below
-    total_att = stats["attempts"]
-    acc_rate = acc_timed / max(total_att, 1)
-    value = world * EVALS_PER_STEP * K / (ms / 1000.0)
-    accepted_per_s = world * acc_rate * K / (ms / 1000.0)
+    tm = stats["timed"]  # counters of the K timed attempts
+    value = world * tm["rhs_evals"] / (ms / 1000.0)
+    accepted_per_s = world * tm["accepted"] / (ms / 1000.0)
 
     # e2e: public API with host buffers, per step H2D state -> one attempt -> D2H state + stats
     sopts = {k: v for k, v in sched.items() if k in smol.SCHEDULE_KEYS}
@@ -396,7 +414,8 @@ def gpu_arm(args):
         "config": dict(config_dict(precision), parallelism=f"replicas{world}",
                        schedule=sched or "rule (untuned)"),
         "accepted_steps_per_s": accepted_per_s,
-        "attempts": {"accepted": stats["accepted"], "rejected": stats["rejected"], "t_end": stats["t"]},
+        "attempts": {"accepted": tm["accepted"], "rejected": tm["rejected"], "rhs_evals": tm["rhs_evals"],
+                     "t_end": stats["t"]},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K * (LAUNCHES_UNFUSED if sched.get("flags", 0) & FLAG_NO_FUSE
                                                         else LAUNCHES_FUSED),
         "clocks": clocks,
@@ -404,7 +423,7 @@ def gpu_arm(args):
     if args.both and precision == "fp64":
         ms32, st32, pm32, pc32, tsys32, _, _, sch32 = time_form(smol, torch, "fp32conv", K, W, stream, flush, rank,
                                                                 tune=not args.no_tune)
-        v32 = world * EVALS_PER_STEP * K / (ms32 / 1000.0)
+        v32 = world * st32["timed"]["rhs_evals"] / (ms32 / 1000.0)
         line["fp32conv"] = {"value": v32, "ms_per_step": ms32 / K, "speedup_vs_fp64": v32 / value,
                             "kernel_us": {k: round(v * 1000.0, 3) for k, v in pm32.items()}, "schedule": sch32,
                             "roofline": roofline("fp32conv", pm32, pc32, tsys32.num_transforms, sch32),
@@ -412,7 +431,7 @@ def gpu_arm(args):
         # the FP64-accurate double-float form (FP64 parity tolerance 1e-10)
         msd, std_, pmd, pcd, tsysd, _, _, schd = time_form(smol, torch, "df64", K, W, stream, flush, rank,
                                                            tune=not args.no_tune)
-        vd = world * EVALS_PER_STEP * K / (msd / 1000.0)
+        vd = world * std_["timed"]["rhs_evals"] / (msd / 1000.0)
         line["df64"] = {"value": vd, "ms_per_step": msd / K, "speedup_vs_fp64": vd / value,
                         "kernel_us": {k: round(v * 1000.0, 3) for k, v in pmd.items()}, "schedule": schd,
                         "roofline": roofline("df64", pmd, pcd, tsysd.num_transforms, schd),
@@ -434,11 +453,11 @@ def gpu_arm(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             msb = float(t.item())
         stb = smol.gather_shards(stb, rank_of, dist) if world > 1 else stb
-        att = sum(x["attempts"] for x in stb) if stb else 0
+        evb = sum(x["rhs_evals"] for x in stb) if stb else 0
         acc = sum(x["accepted"] for x in stb) if stb else 0
         line["batch"] = {"systems": args.batch, "precision": "fp32conv", "steps": Kb, "ms_per_step": msb / Kb,
-                         "rhs_evals_per_s": EVALS_PER_STEP * args.batch * Kb / (msb / 1000.0),
-                         "accepted_steps_per_s": acc / max(att, 1) * args.batch * Kb / (msb / 1000.0),
+                         "rhs_evals_per_s": evb / (msb / 1000.0),
+                         "accepted_steps_per_s": acc / (msb / 1000.0),
                          "scaling": "strong" if world > 1 else "n/a",
                          "elements": int(sum(r["M"] for r in batch_recipe(args.batch))), "launch_flags": bflags,
                          "note": "one step = one RKF45 attempt of every system; systems from seed 2407, "
@@ -475,7 +494,7 @@ def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count
     b.start(n0s, 0.0, 1000.0, 1e-8, scheme="rkf45")
     for _ in range(W):
         b.advance()
-    torch.cuda.synchronize()
+    _, stw = b.finish()  # counters before the timed attempts (the run continues)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     with torch.cuda.stream(stream):
         for i in range(K):
@@ -486,6 +505,8 @@ def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(c) for a, c in ev)
     _, stats = b.finish()
+    # per system: the counters of the K timed attempts
+    stats = [{k: x[k] - y[k] for k in ("rhs_evals", "accepted", "rejected", "attempts")} for x, y in zip(stats, stw)]
     Ms = [r["M"] for r in rec]
     return ms, stats, Ms, flags
 
@@ -518,6 +539,7 @@ def e2e_leg(smol, torch, precision, K, U, V, stream, sched=None):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tc = 0.0
+    evals = 0
     with torch.cuda.stream(stream):
         for _ in range(K):
             d.copy_(h, non_blocking=True)
@@ -525,11 +547,12 @@ def e2e_leg(smol, torch, precision, K, U, V, stream, sched=None):
             h.copy_(d, non_blocking=True)
             stream.synchronize()
             tc = st["t"]
+            evals += st["rhs_evals"]
     el = time.perf_counter() - t0
-    # state both ways, plus the control block (152 bytes) uploaded at start and read back
+    # state both ways, plus the control block (CTL_BYTES) uploaded at start and read back
     # (status snapshot and final read) by smol_integrate
-    return {"value": EVALS_PER_STEP * K / el, "unit": "RHS evals/s", "h2d_bytes_per_step": 8 * M + 152,
-            "d2h_bytes_per_step": 8 * M + 2 * 152, "steps": K}
+    return {"value": evals / el, "unit": "RHS evals/s", "h2d_bytes_per_step": 8 * M + CTL_BYTES,
+            "d2h_bytes_per_step": 8 * M + 2 * CTL_BYTES, "steps": K}
 
 
 def main():

@@ -136,7 +136,7 @@ typedef struct smol_stats {
     double  tau_next;        /* proposed next step (resume with tau0 = tau_next) */
     double  err_last;        /* error estimate of the last attempt */
     double  mass;            /* sum_s s n_s of the final state (FP64) */
-    int64_t rhs_evals;       /* S(n) evaluations actually made */
+    int64_t rhs_evals;       /* S(n) evaluations actually made (a retry reuses S(n^k)) */
     int64_t rhs_evals_paper; /* stages x RK steps evaluated, the count of the paper's tables */
     int64_t accepted;
     int64_t rejected;
@@ -187,8 +187,11 @@ int smol_rhs_terms(smol_system* sys, const double* d_n, double* d_birth, double*
  * SMOL_RKF45) and tolerance tol (> 0), starting from d_n (device, M doubles), and
  * writes n(t_end) back to d_n. Step control runs on the device; the host launches
  * captured CUDA graphs of opts.chunk attempts and reads a status block between
- * launches. Returns the final status (SMOL_OK or SMOL_STEADY on success) and fills
- * *stats when non-NULL. */
+ * launches. A rejected attempt is repeated from the same n^k (Sec. 2), so the retry
+ * keeps the first stage S(n^k) of the rejected attempt (rescaled to the new step)
+ * instead of evaluating it again; stats->rhs_evals counts the evaluations made.
+ * Returns the final status (SMOL_OK or SMOL_STEADY on success) and fills *stats when
+ * non-NULL. */
 int smol_integrate(smol_system* sys, double* d_n, double t0, double t1, double tol,
                    int32_t scheme, smol_stats* stats);
 

@@ -357,14 +357,17 @@ def integrate(S, n0, t0, t1, tol, opts: Options | None = None, tau0_system: Syst
               accepted=0, rejected=0, status=OK)
     log = []
     attempts = 0
+    S_n = None
     while t < t1:
         if attempts >= o.max_attempts:
             st["status"] = EMAXATTEMPTS
             break
         clamped = tau >= t1 - t
         h = (t1 - t) if clamped else tau
-        S_n = S(n)
-        st["rhs_evals"] += 1
+        # a rejected step is repeated from the same n (Sec. 2), whose S(n) is kept
+        if S_n is None:
+            S_n = S(n)
+            st["rhs_evals"] += 1
         if o.steady_rtol > 0:
             nn = _norm(n)
             if nn > 0 and _norm(S_n) / nn < o.steady_rtol:
@@ -410,6 +413,7 @@ def integrate(S, n0, t0, t1, tol, opts: Options | None = None, tau0_system: Syst
             log.append((t, h, err, accept))
         if accept:
             n = cand
+            S_n = None
             t = t1 if clamped else t + h
             st["accepted"] += 1
             if not clamped:

@@ -509,6 +509,7 @@ void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cuda
     q.pr = pr;
     q.fuse = !(E->o.flags & SMOL_FLAG_NO_FUSE);
     auto Ev = [&](StageIn in, int k, double hfac, bool first) {
+        in.first = first ? 1 : 0;  // S(n^k): reused by the retry of a rejected attempt
         if (Tr<R>::shadowed)
             for (int j = 0; j < in.nv; ++j)
                 if (in.slot[j] == SLOT_CUR) in.slot[j] = SLOT_CURF;

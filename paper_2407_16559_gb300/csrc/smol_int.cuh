@@ -129,7 +129,7 @@ __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, 
                                            double X, bool bad, double MS, double Q) {
     Ctl* c = &cref;
     c->arrive = 0;
-    c->rhs_evals += 1;  // S(n^k) of the first stage
+    if (!c->reuse) c->rhs_evals += 1;  // S(n^k) of the first stage (reused on a retry)
     if (P.steady) {
         c->steady = Q;
         if (steady_stop(P, c->nrm2, Q)) {
@@ -166,9 +166,11 @@ __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, 
         c->mass = MS;
         set_xe(c, S, X);
         if (!c->clamped) c->tau = tau_new;
+        c->reuse = 0;
     } else {
         c->rejected += 1;
         c->tau = tau_new;
+        c->reuse = 1;  // the retry starts from the same n^k: work vector 0 holds h S(n^k)
     }
     if (c->t < c->t1 && c->tau < P.tau_min_rel * fmax(1.0, fabs(c->t))) {
         c->status = ST_EUNDERFLOW;
@@ -179,7 +181,10 @@ __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, 
         c->status = ST_EMAXATT;
         c->done = 1;
     }
-    if (!c->done) set_next_step(c);
+    if (!c->done) {
+        set_next_step(c);
+        if (c->reuse) c->hf = c->h / h;  // rescales the kept k_1 = h S(n^k) to the new step
+    }
 }
 
 // err of an attempt for the stats and the step log (beside the controller, on another

@@ -58,11 +58,14 @@ struct Ctl {
     double steady;              // ||S(n)||_2^2 of the last attempt's first stage (unscaled)
     double mass;                // sum_s s n_s of the current state
     double itol2;               // 1 / tol^2 (0 for constant steps without a tolerance)
+    double hf;                  // when reuse: h / (the step work vector 0 is scaled with)
     int32_t done, status, cur, clamped;
     int64_t attempts, accepted, rejected, rhs_evals, rhs_paper;
     double* state[2];           // double-buffered state; state[cur] is n^k
     uint32_t arrive;            // arrival counter of the last-block-done reductions
-    int32_t pad;
+    int32_t reuse;              // the last attempt was rejected: work vector 0 holds
+                                // (h / hf) S(n^k) of the current state, and the next
+                                // attempt rescales it instead of evaluating S(n^k) again
     int32_t xe[MAXT];           // FP32 form: input scale exponents of the transforms
 };
 
@@ -117,6 +120,7 @@ enum { SLOT_CUR = -1, SLOT_OTHER = -2, SLOT_EXT = -3, SLOT_HALF = -4, SLOT_CURF 
 // FP64 value is needed.
 struct StageIn {
     int nv, direct;  // direct: y is the single FP64 term itself (c == 1)
+    int first;       // the attempt's evaluation of S(n^k), reused on a retry (Ctl::reuse)
     int slot[MAXV];
     double c[MAXV];
     float cf[MAXV];  // c rounded to FP32 and the remainder c - cf rounded to FP32 (set on
@@ -139,6 +143,8 @@ struct EpiOut {
 // into shared memory.
 struct CtlView {
     int done, cur;
+    int reuse;  // Ctl::reuse
+    double hf;  // Ctl::hf: the rescaling of a reused k_1
     const double* s0;
     const double* s1;
     double h, ymax;
@@ -481,9 +487,17 @@ __device__ __forceinline__ void load_ctl(const SysDev& sh, CtlView& cv) {
         cv.s1 = c->state[1];
         cv.h = c->h;
         cv.ymax = c->ymax;
+        cv.reuse = c->reuse;
+        cv.hf = c->hf;
     }
     __syncthreads();
 }
+
+// A retry after a rejected attempt starts from the same state n^k (Sec. 2: the step
+// is repeated from n^k with a smaller tau), so its first evaluation S(n^k) is the one
+// the rejected attempt made: the forward and row kernels of that evaluation return at
+// once, and its inverse pass rescales the stored k_1 = h' S(n^k) to the new step h.
+__device__ __forceinline__ bool reused(const StageIn& in, const CtlView& cv) { return in.first && cv.reuse; }
 
 // Both steps, for kernels with no prologue of their own.
 __device__ __forceinline__ int load_sys(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
@@ -657,7 +671,7 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sys
     typename vec2<R>::T wpre[WPRE];
     fwd_prologue<R>(S, bx, m, wpre);
     load_ctl(S, cv);
-    if (cv.done) {
+    if (cv.done || reused(in, cv)) {
         cp_async_wait();  // no copy into this CTA's shared memory outlives it
         return;
     }
@@ -739,7 +753,7 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
         double* sh = reinterpret_cast<double*>(smraw);
         if ((int)threadIdx.x < S.T) sh[3 * MAXT + threadIdx.x] = (double)reinterpret_cast<const R*>(S.W)[(size_t)threadIdx.x * S.Mp];
         load_ctl(S, cv);
-        if (cv.done) return;
+        if (cv.done || reused(in, cv)) return;
         finalize_scalars<R>(S, cv, in, sh);
         return;
     }
@@ -762,7 +776,7 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
         cp_async_el(twi + idx, reinterpret_cast<const cx<R>*>(S.twr) + (size_t)r * N2 + k2);
     }
     load_ctl(S, cv);
-    if (cv.done) {
+    if (cv.done || reused(in, cv)) {
         cp_async_wait();  // no copy into this CTA's shared memory outlives it
         return;
     }
@@ -960,6 +974,23 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
     }
 }
 
+// The inverse pass of a reused first evaluation: k_1 <- (h / h') k_1 at the CTA's
+// elements (the same thread per element pair as inv_body and fwd_body).
+template <typename R>
+__device__ __forceinline__ void rescale_k1(const SysDev& S, const CtlView& cv, const EpiOut& eo, int bx) {
+    if (eo.out_slot < 0) return;
+    R* k = reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride;
+    const R f = (R)cv.hf;
+    const Div DG = mkdiv(S.G);
+    const int half = (S.N1 >> 1) * S.G;
+    for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
+        const int i = col_elem(S, DG, bx, idx);
+        if (i >= S.M) continue;
+        k[i] = f * k[i];
+        if (i + 1 < S.M) k[i + 1] = f * k[i + 1];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Kernel C: the inverse pass of one evaluation.
 // ---------------------------------------------------------------------------
@@ -975,8 +1006,9 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
     const ColSm<R> m = col_sm<R>(S, smraw);
     stage_tw(m.twP, S.lgN1, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
     load_ctl(S, cv);
-    if (cv.done) {
+    if (cv.done || reused(in, cv)) {
         cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        if (!cv.done) rescale_k1<R>(S, cv, eo, bx);
         return;
     }
     inv_body<R>(S, cv, in, eo, bx, m, sm);
@@ -1006,7 +1038,13 @@ __global__ void __launch_bounds__(256) k_inv_fwd(const SysDev* __restrict__ sysv
         cp_async_wait();  // no copy into this CTA's shared memory outlives it
         return;
     }
-    inv_body<R>(S, cv, in, eo, bx, m, sm);
+    if (reused(in, cv)) {
+        cp_async_wait();
+        stage_tw_fix(m.twP, S.lgN1, S.lgMp);  // as inv_body does
+        rescale_k1<R>(S, cv, eo, bx);
+    } else {
+        inv_body<R>(S, cv, in, eo, bx, m, sm);
+    }
     __syncthreads();  // the forward pass reuses the tile buffers
     fwd_body<R>(S, cv, nx, bx, m, wpre, false, red);
 }

@@ -281,3 +281,31 @@ def test_mass_statistic_and_conservation(smol, precision):
     m = float(np.dot(s, n.cpu().numpy()))
     assert abs(st["mass"] - m) <= 1e-13 * m
     assert abs(m - 1.0) <= (1e-7 if precision != "fp32conv" else 1e-4)
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+@pytest.mark.parametrize("scheme", ["rkf45", "rk4", "rk2"])
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_retry_keeps_first_stage(smol, precision, scheme, fuse):
+    """A rejected attempt is repeated from the same n^k (Sec. 2): the retry keeps the
+    rejected attempt's S(n^k), rescaled to the new step, where the oracle keeps its
+    S(n). A large initial step forces a run of rejections; the decisions, the number of
+    evaluations made and the final state match the oracle, in the fused and the
+    unfused launch sequence."""
+    M = 512
+    flags = 0 if fuse else smol.FLAG_NO_FUSE
+    n, st, m, ost, olog, sysm = run_both(smol, M, "brownian", 0.3, 0.01, 5.0, 1e-8, scheme, precision=precision,
+                                         tau0=2.0, flags=flags)
+    assert st["status"] == ost["status"] == 0
+    retries = sum(1 for prev in olog[:-1] if not prev[3])
+    assert retries >= 3
+    assert (st["accepted"], st["rejected"]) == (ost["accepted"], ost["rejected"])
+    assert st["rhs_evals"] == ost["rhs_evals"] and st["rhs_evals_paper"] == ost["rhs_evals_paper"]
+    per = 6 if scheme == "rkf45" else 3 * oracle.STAGES[scheme] - 1
+    assert st["rhs_evals"] == per * len(olog) - retries
+    assert np.linalg.norm(n - m) <= 1e-9 * np.linalg.norm(m)
+    _, h, _, acc, cnt = sysm.get_log()
+    oh = np.array([x[1] for x in olog])
+    assert cnt == len(olog) and np.array_equal(acc, [x[3] for x in olog])
+    lead = next(i for i, x in enumerate(olog) if x[3])  # the first run of rejections
+    assert lead >= 2 and np.allclose(h[:lead + 1], oh[:lead + 1], rtol=1e-6, atol=0)

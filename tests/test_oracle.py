@@ -274,7 +274,9 @@ def test_integrate_stats_conventions():
     assert st["status"] == oracle.OK and st["t"] == 2.0
     assert st["accepted"] + st["rejected"] == len(log)
     assert st["rhs_evals_paper"] == 6 * len(log)
-    assert st["rhs_evals"] == 6 * len(log)
+    # an attempt after a rejection starts from the same n and keeps its S(n)
+    retries = sum(1 for prev in log[:-1] if not prev[3])
+    assert st["rhs_evals"] == 6 * len(log) - retries
     # a fixed-step replay of the accepted steps reproduces the trajectory bit for bit
     taus = [h for (_, h, _, acc) in log if acc]
     m = monodisperse(M)
@@ -295,6 +297,24 @@ def test_rhs_eval_counts_match_calls(scheme, opts):
     assert st["rhs_evals"] == sysm.evals
     per = oracle.STAGES[scheme] * (1 if (scheme == "rkf45" or opts) else 3)
     assert st["rhs_evals_paper"] == per * len(log)
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk4", "rkf45"])
+def test_retry_keeps_first_stage(scheme):
+    """A rejected attempt is repeated from the same n^k (Sec. 2), so the retry's first
+    stage S(n^k) is not evaluated again: the actual count is the paper's count less one
+    per retry, and equals the number of calls of S. A large initial step forces
+    rejections."""
+    M = 32
+    U, V = kernel_factors("brownian", M, a=0.3)
+    sysm = oracle.System(M, 0.01, U=U, V=V)
+    _, st, log = oracle.integrate(sysm, monodisperse(M), 0.0, 1.0, 1e-8,
+                                  oracle.Options(scheme=scheme, tau0=2.0, log=True))
+    retries = sum(1 for prev in log[:-1] if not prev[3])
+    assert st["rejected"] >= 2 and retries == st["rejected"]
+    assert st["rhs_evals"] == sysm.evals
+    p = oracle.STAGES[scheme]
+    assert st["rhs_evals"] == len(log) * (p if scheme == "rkf45" else 3 * p - 1) - retries
 
 
 def test_integrate_status_codes():
