@@ -143,12 +143,42 @@ __device__ __forceinline__ void dft8(cx<R>* u, bool inv) {
     u[7] = b3;
 }
 
+// Length-8 DFT of u[0..3] with u[4..7] = 0 (the first pass of a zero-padded input):
+// the radix-2 split is then a copy, a_m = b_m = u_m.
+template <typename R>
+__device__ __forceinline__ void dft8_lower(cx<R>* u, bool inv) {
+    const R h = sqrt_half<R>();
+    cx<R> a0 = u[0], a1 = u[1], a2 = u[2], a3 = u[3];
+    cx<R> b0 = u[0], b1 = u[1], b2 = u[2], b3 = u[3];
+    const R s1 = (b1.x + b1.y) * h, d1 = (b1.x - b1.y) * h;
+    const R s3 = (b3.x + b3.y) * h, d3 = (b3.x - b3.y) * h;
+    b1 = inv ? mk<R>(d1, s1) : mk<R>(s1, -d1);
+    b2 = inv ? mul_pi(b2) : mul_mi(b2);
+    b3 = inv ? mk<R>(-s3, d3) : mk<R>(-d3, -s3);
+    dft4<R>(a0, a1, a2, a3, inv);
+    dft4<R>(b0, b1, b2, b3, inv);
+    u[0] = a0;
+    u[1] = b0;
+    u[2] = a1;
+    u[3] = b1;
+    u[4] = a2;
+    u[5] = b2;
+    u[6] = a3;
+    u[7] = b3;
+}
+
+// Which half of a tile transform is known or wanted (zero-padded convolution inputs
+// and the linear part of the inverse): HALF_IN, the upper half of the input is zero and
+// not read (first pass); HALF_OUT, only the lower half of the output is written (last
+// pass: outputs m < RAD / 2 of each butterfly).
+enum { HALF_NONE = 0, HALF_IN = 1, HALF_OUT = 2 };
+
 // One Stockham pass of radix RAD (8, 4 or 2) on sub-transform length p = 2^lgp of a
 // length-P transform over G interleaved sequences: for butterfly i in [0, P/RAD),
 // k = i mod p, inputs in[i + m P/RAD] (m < RAD) are multiplied by W_{RAD p}^{m k},
 // transformed by a length-RAD DFT and stored at out[(i-k) RAD + k + m p].
 // twP is a shared-memory table twP[e] = W_P^e, e < P (conjugated for the inverse).
-template <typename R, int RAD>
+template <typename R, int RAD, int HALF = HALF_NONE>
 __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>* __restrict__ b, int lgP, int lgp,
                                               int G, const cx<R>* __restrict__ twP, bool inv) {
     constexpr int LGR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
@@ -164,52 +194,62 @@ __device__ __forceinline__ void stockham_pass(const cx<R>* __restrict__ a, cx<R>
         const int k = i & (p - 1);
         cx<R> u[RAD];
 #pragma unroll
-        for (int m = 0; m < RAD; ++m) u[m] = a[(i + m * q) * G + g];
-        if (k) {
-#pragma unroll
-            for (int m = 1; m < RAD; ++m) {
-                cx<R> w = twP[(m * k) << sh];
-                if (inv) w = conj(w);
-                u[m] = u[m] * w;
-            }
-        }
-        if (RAD == 8) {
-            dft8<R>(u, inv);
-        } else if (RAD == 4) {
-            dft4<R>(u[0], u[1], u[2], u[3], inv);
+        for (int m = 0; m < RAD; ++m)
+            u[m] = (HALF == HALF_IN && m >= RAD / 2) ? mk<R>((R)0, (R)0) : a[(i + m * q) * G + g];
+        if (HALF == HALF_IN && RAD == 8) {
+            dft8_lower<R>(u, inv);  // a first pass (p = 1): k = 0, no twiddles
         } else {
-            const cx<R> t = u[0] - u[1];
-            u[0] = u[0] + u[1];
-            u[1] = t;
+            if (k) {
+#pragma unroll
+                for (int m = 1; m < RAD; ++m) {
+                    cx<R> w = twP[(m * k) << sh];
+                    if (inv) w = conj(w);
+                    u[m] = u[m] * w;
+                }
+            }
+            if (RAD == 8) {
+                dft8<R>(u, inv);
+            } else if (RAD == 4) {
+                dft4<R>(u[0], u[1], u[2], u[3], inv);
+            } else {
+                const cx<R> t = u[0] - u[1];
+                u[0] = u[0] + u[1];
+                u[1] = t;
+            }
         }
         const int j = ((i - k) << LGR) + k;
 #pragma unroll
-        for (int m = 0; m < RAD; ++m) b[(j + m * p) * G + g] = u[m];
+        for (int m = 0; m < (HALF == HALF_OUT ? RAD / 2 : RAD); ++m) b[(j + m * p) * G + g] = u[m];
     }
+}
+
+template <typename R, int HALF>
+__device__ __forceinline__ void pass_sel(const cx<R>* a, cx<R>* b, int lgP, int lgp, int G,
+                                         const cx<R>* __restrict__ twP, bool inv, int rad) {
+    if (rad == 8) stockham_pass<R, 8, HALF>(a, b, lgP, lgp, G, twP, inv);
+    else if (rad == 4) stockham_pass<R, 4, HALF>(a, b, lgP, lgp, G, twP, inv);
+    else stockham_pass<R, 2, HALF>(a, b, lgP, lgp, G, twP, inv);
 }
 
 // Stockham autosort FFT of length P = 2^lgP on G interleaved sequences held in shared
 // memory as buf[p * G + g] (g fastest), radix-8 passes first, then one radix-4 or
 // radix-2 pass for the remaining factor. Ping-pongs between a and b and returns the
 // buffer holding the result, in natural order. inv selects the sign +i (unnormalised
-// inverse). twP: shared table W_P^e, e < P. Every thread of the block must call it;
-// the caller synchronises before.
-template <typename R>
+// inverse). twP: shared table W_P^e, e < P. HALF_IN: the upper half of the input is zero
+// and is not read; HALF_OUT: only the lower half of the result is written. Every thread
+// of the block must call it; the caller synchronises before.
+template <typename R, int HALF = HALF_NONE>
 __device__ __forceinline__ cx<R>* tile_fft_body(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ twP,
                                                 bool inv) {
     int lgp = 0;
     while (lgp < lgP) {
         const int rem = lgP - lgp;
-        if (rem >= 3) {
-            stockham_pass<R, 8>(a, b, lgP, lgp, G, twP, inv);
-            lgp += 3;
-        } else if (rem == 2) {
-            stockham_pass<R, 4>(a, b, lgP, lgp, G, twP, inv);
-            lgp += 2;
-        } else {
-            stockham_pass<R, 2>(a, b, lgP, lgp, G, twP, inv);
-            lgp += 1;
-        }
+        const int rad = rem >= 3 ? 8 : (rem == 2 ? 4 : 2);
+        const int lgr = rem >= 3 ? 3 : rem;
+        if (HALF == HALF_IN && lgp == 0) pass_sel<R, HALF_IN>(a, b, lgP, lgp, G, twP, inv, rad);
+        else if (HALF == HALF_OUT && lgp + lgr == lgP) pass_sel<R, HALF_OUT>(a, b, lgP, lgp, G, twP, inv, rad);
+        else pass_sel<R, HALF_NONE>(a, b, lgP, lgp, G, twP, inv, rad);
+        lgp += lgr;
         __syncthreads();
         cx<R>* t = a;
         a = b;
@@ -217,10 +257,10 @@ __device__ __forceinline__ cx<R>* tile_fft_body(cx<R>* a, cx<R>* b, int lgP, int
     }
     return a;
 }
-template <typename R>
+template <typename R, int HALF = HALF_NONE>
 __device__ __forceinline__ cx<R>* tile_fft(cx<R>* a, cx<R>* b, int lgP, int G, const cx<R>* __restrict__ twP,
                                            bool inv) {
-    return tile_fft_body<R>(a, b, lgP, G, twP, inv);
+    return tile_fft_body<R, HALF>(a, b, lgP, G, twP, inv);
 }
 
 // Asynchronous global -> shared copies of one element (4, 8 or 16 bytes; both addresses

@@ -591,7 +591,10 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
         ys[2 * idx + 1] = y1;
         if (!in.direct) *reinterpret_cast<typename vec2<R>::T*>(yb + i) = {y0, y1};
     }
-    for (int q = half * T + threadIdx.x; q < N1 * GT; q += blockDim.x) a[q] = mk<R>((R)0, (R)0);
+    // rows n1 >= N1 / 2 of the columns are the zero padding: the FP64 transform does not
+    // read them (HALF_IN), the others take them as zeros
+    if (!Tr<R>::fp64)
+        for (int q = half * T + threadIdx.x; q < N1 * GT; q += blockDim.x) a[q] = mk<R>((R)0, (R)0);
     cp_async_wait();
     if (fix_tw) stage_tw_fix(m.twP, S.lgN1, S.lgMp);
     __syncthreads();
@@ -645,7 +648,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
         const int t = threadIdx.x >> 1;
         S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
     }
-    cx<R>* res = tile_fft<R>(a, b, S.lgN1, GT, m.twP, false);
+    cx<R>* res = tile_fft<R, Tr<R>::fp64 ? HALF_IN : HALF_NONE>(a, b, S.lgN1, GT, m.twP, false);
     cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
     const Div DGT = mkdiv(GT);
     for (int idx = threadIdx.x; idx < N1 * GT; idx += blockDim.x) {
@@ -700,7 +703,7 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
     // Z holds the row spectra as Z[k2 * G + col], col = 2 t + rho; ia / ib are the
     // offsets k2 * G + rho of the pair's two frequencies ka and Mp - ka; w = W_L^ka.
     constexpr bool FOLD = Tr<R>::fp64;
-    cx<R> Ca = mk<R>((R)0, (R)0), Cb = Ca;
+    cx<R> Ca, Cb;
     for (int p = 0; p < S.npairs; ++p) {
         const int u = S.pu[p], v = S.pv[p];
         cx<R> Xa[2], Xb[2];
@@ -723,12 +726,18 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
             pa = scl(pa, pc[p]);
             pb = scl(pb, pc[p]);
         }
-        Ca = Ca + pa;
-        Cb = Cb + pb;
+        Ca = p ? Ca + pa : pa;  // npairs >= 1
+        Cb = p ? Cb + pb : pb;
     }
-    const cx<R> wb = -conj(w);  // W_L^(Mp - ka)
-    Ya = w * (Ca - conj(Cb)) + mul_pi(Ca + conj(Cb));
-    Yb = wb * (Cb - conj(Ca)) + mul_pi(Cb + conj(Ca));
+    // Packed inverse spectrum at ka and Mp - ka:
+    //   Ya = w (Ca - conj Cb) + i (Ca + conj Cb),
+    //   Yb = wb (Cb - conj Ca) + i (Cb + conj Ca) with wb = W_L^(Mp - ka) = -conj w.
+    // With D = Ca - conj Cb, G = Ca + conj Cb and P = w D: Cb - conj Ca = -conj D and
+    // Cb + conj Ca = conj G, so Yb = conj P + i conj G; one complex product serves both.
+    const cx<R> D = Ca - conj(Cb), Gs = Ca + conj(Cb);
+    const cx<R> P = w * D;
+    Ya = mk<R>(P.x - Gs.y, P.y + Gs.x);
+    Yb = mk<R>(P.x + Gs.y, Gs.x - P.y);
     if (!FOLD) {
         Ya = scl(Ya, (R)0.5);
         Yb = scl(Yb, (R)0.5);
@@ -925,7 +934,8 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
     cp_async_wait();
     stage_tw_fix(m.twP, S.lgN1, S.lgMp);
     __syncthreads();
-    cx<R>* res = tile_fft<R>(a, b, S.lgN1, G, m.twP, true);
+    // only rows n1 < N1 / 2 (sizes up to M) are needed: the FP64 transform writes no others
+    cx<R>* res = tile_fft<R, Tr<R>::fp64 ? HALF_OUT : HALF_NONE>(a, b, S.lgN1, G, m.twP, true);
     const R scale = rs[0], bscale = rs[1], lam1 = rs[2], s1r = rs[3], l1r = rs[4];
     const double src = src_s;
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
