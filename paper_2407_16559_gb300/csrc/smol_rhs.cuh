@@ -37,6 +37,8 @@
 // Batching. Every kernel takes a device array of system descriptors and a map from
 // blockIdx.x to (system, block of that system); one system is a batch of one.
 #pragma once
+#include <type_traits>
+
 #include "smol_fft.cuh"
 
 namespace smol {
@@ -215,6 +217,11 @@ template <>
 struct Tr<double> {
     static constexpr bool scaled = false, shadowed = false, fp64 = true;
 };
+// Column transforms pruned to the zero padding (HALF_IN) and to the sizes up to M
+// (HALF_OUT): FP64 and FP32; not double-float, whose kernels are bound by instruction
+// fetch, where the extra pass variants cost more than the work they save.
+template <typename R>
+constexpr bool PRUNE = !std::is_same<R, dd>::value;
 
 // Loads of one R value and of the R pair at 2 * pair, 2 * pair + 1: read-only path
 // (ldg) or coherent L2 path (ldcg).
@@ -591,9 +598,10 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
         ys[2 * idx + 1] = y1;
         if (!in.direct) *reinterpret_cast<typename vec2<R>::T*>(yb + i) = {y0, y1};
     }
-    // rows n1 >= N1 / 2 of the columns are the zero padding: the FP64 transform does not
-    // read them (HALF_IN), the others take them as zeros
-    if (!Tr<R>::fp64)
+    // rows n1 >= N1 / 2 of the columns are the zero padding: the FP64 and FP32 transforms
+    // do not read them (HALF_IN); the double-float one takes them as zeros (its variant
+    // with the pruned first pass costs more in instruction fetch than it saves)
+    if (!PRUNE<R>)
         for (int q = half * T + threadIdx.x; q < N1 * GT; q += blockDim.x) a[q] = mk<R>((R)0, (R)0);
     cp_async_wait();
     if (fix_tw) stage_tw_fix(m.twP, S.lgN1, S.lgMp);
@@ -648,7 +656,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
         const int t = threadIdx.x >> 1;
         S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
     }
-    cx<R>* res = tile_fft<R, Tr<R>::fp64 ? HALF_IN : HALF_NONE>(a, b, S.lgN1, GT, m.twP, false);
+    cx<R>* res = tile_fft<R, PRUNE<R> ? HALF_IN : HALF_NONE>(a, b, S.lgN1, GT, m.twP, false);
     cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
     const Div DGT = mkdiv(GT);
     for (int idx = threadIdx.x; idx < N1 * GT; idx += blockDim.x) {
@@ -934,8 +942,8 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
     cp_async_wait();
     stage_tw_fix(m.twP, S.lgN1, S.lgMp);
     __syncthreads();
-    // only rows n1 < N1 / 2 (sizes up to M) are needed: the FP64 transform writes no others
-    cx<R>* res = tile_fft<R, Tr<R>::fp64 ? HALF_OUT : HALF_NONE>(a, b, S.lgN1, G, m.twP, true);
+    // only rows n1 < N1 / 2 (sizes up to M) are needed: the pruned transform writes no others
+    cx<R>* res = tile_fft<R, PRUNE<R> ? HALF_OUT : HALF_NONE>(a, b, S.lgN1, G, m.twP, true);
     const R scale = rs[0], bscale = rs[1], lam1 = rs[2], s1r = rs[3], l1r = rs[4];
     const double src = src_s;
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
