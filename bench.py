@@ -62,11 +62,13 @@ FIXED_SCHEDULE = {}
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
 # (precision, kernel class); valid only while the kernel sources are unchanged.
 TRAFFIC = {
-    # profiles/k_rows_M131072_fp64.md, profiles/k_inv_fwd_M131072_fp32conv.md (read + write)
-    ("fp64", "rows"): {"bytes": 8503552.0, "src": "c507d54711f37556"},
-    ("fp64", "inv_fwd"): {"bytes": 8479744.0, "src": "c507d54711f37556"},
-    ("fp32conv", "inv_fwd"): {"bytes": 4269568.0, "src": "c507d54711f37556"},
-    ("fp32conv", "rows"): {"bytes": 4297472.0, "src": "c507d54711f37556"},
+    # profiles/k_rows_M131072_*.md, profiles/k_inv_fwd_M131072_*.md (dram read + write)
+    ("fp64", "rows"): {"bytes": 8504320.0, "src": "516ef981546e9f6b"},
+    ("fp64", "inv_fwd"): {"bytes": 9546752.0, "src": "516ef981546e9f6b"},
+    ("fp32conv", "inv_fwd"): {"bytes": 4803072.0, "src": "516ef981546e9f6b"},
+    ("fp32conv", "rows"): {"bytes": 4296448.0, "src": "516ef981546e9f6b"},
+    ("df64", "inv_fwd"): {"bytes": 9574912.0, "src": "516ef981546e9f6b"},
+    ("df64", "rows"): {"bytes": 8525824.0, "src": "516ef981546e9f6b"},
 }
 
 
