@@ -246,7 +246,7 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": EVALS_PER_STEP * 1000.0 / v, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(config_dict("fp64"), n0="monodisperse, oracle attempts from t = 0"),
+        "config": dict(config_dict("fp64"), n0="monodisperse, oracle attempts from t = 0", l2="n/a (host cores)"),
         "cpu_baseline": {"value": v, "unit": "RHS evals/s", "cores": 1, "kind": "oracle",
                          "sample": f"{res['evals']} evaluations of S(n) (numpy-FFT route) inside oracle RKF45 "
                                    f"attempts at M=2^17 from the monodisperse start, one thread"},
