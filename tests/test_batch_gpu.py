@@ -49,7 +49,30 @@ def test_batch_equals_single_systems(smol, precision):
         m, st = s.integrate(torch.from_numpy(n0), 0.0, 0.5, 1e-8, scheme="rkf45")
         assert sts[q]["status"] == st["status"] == 0
         assert (sts[q]["accepted"], sts[q]["rejected"]) == (st["accepted"], st["rejected"]), (q, sts[q], st)
+        assert sts[q]["rhs_evals"] == st["rhs_evals"]
         assert torch.allclose(ns[q], m, rtol=0, atol=1e-12 * float(m.abs().max()))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_batch_retries_keep_first_stage(smol, precision):
+    """A large initial step makes every system reject its first attempts, each on its
+    own schedule (here one rejection for the first system, two for the others), so one
+    launch holds systems whose first-stage kernels return at once (a retry keeps
+    S(n^k); Sec. 2 repeats the step from n^k) beside systems that evaluate. Each system
+    takes the oracle's decisions and makes its number of evaluations."""
+    import torch
+    specs = [(300, 0.3, 0.01), (1000, 0.4, 0.05), (77, 0.5, 0.2)]
+    Us, Vs, lams, n0s = _systems(specs)
+    b = smol.Batch(Us, Vs, lams, precision=precision, tau0=0.3)
+    ns, sts = b.integrate([torch.from_numpy(n) for n in n0s], 0.0, 3.0, 1e-8, scheme="rkf45")
+    for q, (U, V, lam, n0) in enumerate(zip(Us, Vs, lams, n0s)):
+        osys = oracle.System(len(n0), lam, U=U, V=V, route="lowrank")
+        m, ost, olog = oracle.integrate(osys, n0, 0.0, 3.0, 1e-8,
+                                        oracle.Options(scheme="rkf45", tau0=0.3, log=True))
+        assert sum(1 for prev in olog[:-1] if not prev[3]) >= 1
+        assert (sts[q]["accepted"], sts[q]["rejected"]) == (ost["accepted"], ost["rejected"])
+        assert sts[q]["rhs_evals"] == ost["rhs_evals"] < ost["rhs_evals_paper"]
+        assert np.linalg.norm(ns[q].cpu().numpy() - m) <= 1e-9 * np.linalg.norm(m)
 
 
 def test_batch_fp64_vs_oracle(smol):
