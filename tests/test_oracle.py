@@ -247,6 +247,54 @@ def test_double_halve_and_formula_controllers():
     assert (not acc) and abs(tn - 0.125) < 1e-15         # 1/4 * (1/4)^(1/2)
 
 
+def _stability(scheme, z):
+    """R(z) of the scheme on y' = lambda y, z = tau lambda (Heun's RK2, classical RK4)."""
+    if scheme == "rk2":
+        return 1 + z + z * z / 2
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk4"])
+@pytest.mark.parametrize("ctrl", ["double_halve", "formula"])
+def test_step_doubling_loop_on_linear_equation(scheme, ctrl):
+    """The step-doubling integrator on y' = -y against a replay built from the schemes'
+    stability polynomials alone: a full step multiplies y by R(-tau), two half steps by
+    R(-tau/2)^2, the error is their difference, the half steps are propagated, and the
+    step follows the rule of Sec. 2 (halve / double, or Eq. (6) with s = 1/4 and the
+    factor clamped to [0.1, 4])."""
+    p = 2 if scheme == "rk2" else 4
+    tol, t1, tau0 = 1e-7, 3.0, 0.3
+    y, st, log = oracle.integrate(lambda n: -n, np.array([1.0]), 0.0, t1, tol,
+                                  oracle.Options(scheme=scheme, ctrl=ctrl, tau0=tau0, log=True))
+    assert st["status"] == oracle.OK
+    t, yy, tau, rows = 0.0, 1.0, tau0, []
+    while t < t1:
+        clamped = tau >= t1 - t
+        h = t1 - t if clamped else tau
+        full = _stability(scheme, -h) * yy
+        half = _stability(scheme, -h / 2) ** 2 * yy
+        err = abs(half - full)
+        acc = err <= tol
+        if ctrl == "double_halve":
+            new = 2 * h if acc else h / 2
+        else:
+            new = h * min(max(0.25 * (tol / err) ** (1.0 / p), 0.1), 4.0)
+        rows.append((t, h, err, acc))
+        if acc:
+            yy, t = half, (t1 if clamped else t + h)
+            if not clamped:
+                tau = new
+        else:
+            tau = new
+    assert [r[3] for r in log] == [r[3] for r in rows]
+    # err is a difference of two O(y) values (relative rounding ~1e-9 at err ~ tol);
+    # Eq. (6) carries it into every later step, multiplicatively
+    rt = 1e-12 if ctrl == "double_halve" else 1e-5
+    np.testing.assert_allclose([r[1] for r in log], [r[1] for r in rows], rtol=rt, atol=0)
+    np.testing.assert_allclose([r[2] for r in log], [r[2] for r in rows], rtol=1e-5, atol=1e-18)
+    assert abs(y[0] - yy) <= 1e-12 and st["rejected"] >= 1
+
+
 # ---------------------------------------------------------------------------
 # Whole trajectories
 # ---------------------------------------------------------------------------
