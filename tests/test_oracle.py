@@ -248,10 +248,39 @@ def test_double_halve_and_formula_controllers():
 
 
 def _stability(scheme, z):
-    """R(z) of the scheme on y' = lambda y, z = tau lambda (Heun's RK2, classical RK4)."""
-    if scheme == "rk2":
-        return 1 + z + z * z / 2
-    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    """R(z) of a scheme on y' = lambda y, z = tau lambda, from tests/golden/rk_stability.json."""
+    g = json.load(open(os.path.join(GOLDEN, "rk_stability.json")))["polys"]
+    return _poly(g[scheme], z)
+
+
+def test_rkf45_loop_on_linear_equation():
+    """The RKF45 integrator on y' = -y against a replay built from the embedded pair's
+    stability polynomials: the error is |R5(-tau) - R4(-tau)| |y|, the fourth-order value
+    is propagated, tau <- 0.9 tau (tol/err)^(1/5) clamped to [0.1, 4] on every attempt,
+    and the last step is shortened to t1."""
+    tol, t1, tau0 = 1e-9, 4.0, 1.5
+    y, st, log = oracle.integrate(lambda n: -n, np.array([1.0]), 0.0, t1, tol,
+                                  oracle.Options(scheme="rkf45", tau0=tau0, log=True))
+    assert st["status"] == oracle.OK
+    t, yy, tau, rows = 0.0, 1.0, tau0, []
+    while t < t1:
+        clamped = tau >= t1 - t
+        h = t1 - t if clamped else tau
+        n4 = _stability("rkf45_n4", -h) * yy
+        err = abs(_stability("rkf45_n5", -h) * yy - n4)
+        acc = err <= tol
+        new = h * min(max(0.9 * (tol / err) ** 0.2, 0.1), 4.0)
+        rows.append((t, h, err, acc))
+        if acc:
+            yy, t = n4, (t1 if clamped else t + h)
+            if not clamped:
+                tau = new
+        else:
+            tau = new
+    assert [r[3] for r in log] == [r[3] for r in rows] and st["rejected"] >= 1
+    np.testing.assert_allclose([r[1] for r in log], [r[1] for r in rows], rtol=1e-5, atol=0)
+    np.testing.assert_allclose([r[2] for r in log], [r[2] for r in rows], rtol=1e-5, atol=1e-18)
+    assert abs(y[0] - yy) <= 1e-12
 
 
 @pytest.mark.parametrize("scheme", ["rk2", "rk4"])
