@@ -229,6 +229,27 @@ def test_linear_invariant_mass_plus_flux(scheme):
 # ---------------------------------------------------------------------------
 # Step-size controllers
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("route", ["direct", "lowrank"])
+def test_euler_initial_step_closed_forms(route):
+    """Sec. 1's criterion tau0 = a / max_i sum_j K_ij n_j on a monodisperse state
+    (n_1 = 1): the rate is K_i1, so tau0 = a for K = 1 and a / (M^a' + M^-a') for the
+    Brownian kernel (i/j)^a' + (j/i)^a', whose K_i1 = i^a' + i^-a' grows with i."""
+    M = 200
+    n = monodisperse(M)
+    U, V = kernel_factors("const", M)
+    sysm = oracle.System(M, 0.0, U=U, V=V, route=route)
+    assert oracle.euler_tau0(sysm, n, 0.1) == pytest.approx(0.1, rel=1e-15)
+    for a in (0.3, 0.9):
+        U, V = kernel_factors("brownian", M, a=a)
+        sysm = oracle.System(M, 0.01, U=U, V=V, route=route)
+        assert oracle.euler_tau0(sysm, n, 0.1) == pytest.approx(0.1 / (M ** a + M ** -a), rel=1e-13)
+    # a spread state: the rate of K = 1 is the number density N = sum_j n_j at every i
+    n2 = sample_state(M, 0.01)
+    U, V = kernel_factors("const", M)
+    sysm = oracle.System(M, 0.0, U=U, V=V, route=route)
+    assert oracle.euler_tau0(sysm, n2, 0.2) == pytest.approx(0.2 / float(np.sum(n2)), rel=1e-13)
+
+
 def test_rkf45_controller_worked_examples():
     g = json.load(open(os.path.join(GOLDEN, "rkf45_controller.json")))
     tol, tau = 1e-8, 0.37
