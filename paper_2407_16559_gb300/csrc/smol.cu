@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/smol.h"
+#include "smol_attr.h"
 #include "smol_int.cuh"
 
 using namespace smol;
@@ -314,15 +315,15 @@ bool carve(K k) {
                                 (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
 }
 
+// The limits only rise (smol_attr.h): a smaller system created later must not lower the
+// limit a larger live system (or the no-allocation entry point) launches with.
 template <typename R>
 int set_smem_attrs(const Engine* E) {
+    using smol_host::raise_smem;
     const int sc = (int)E->smemC, sb = (int)E->smemB;
-    const auto dyn = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (cudaFuncSetAttribute(k_fwd_cols<R>, dyn, sc) != cudaSuccess ||
-        cudaFuncSetAttribute(k_inv_cols<R>, dyn, sc) != cudaSuccess ||
-        cudaFuncSetAttribute(k_inv_fwd<R>, dyn, sc) != cudaSuccess ||
-        cudaFuncSetAttribute(k_inv_finish<R>, dyn, sc) != cudaSuccess ||
-        cudaFuncSetAttribute(k_rows<R>, dyn, sb) != cudaSuccess)
+    if (raise_smem(k_fwd_cols<R>, sc) != cudaSuccess || raise_smem(k_inv_cols<R>, sc) != cudaSuccess ||
+        raise_smem(k_inv_fwd<R>, sc) != cudaSuccess || raise_smem(k_inv_finish<R>, sc) != cudaSuccess ||
+        raise_smem(k_rows<R>, sb) != cudaSuccess)
         return SMOL_ECUDA;
     if (!(carve(k_fwd_cols<R>) && carve(k_rows<R>) && carve(k_inv_cols<R>) && carve(k_inv_fwd<R>) &&
           carve(k_inv_finish<R>) && carve(k_finish<R>) && carve(k_lincomb<R>)))

@@ -14,8 +14,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "../../include/smol.h"
+#include "smol_attr.h"
 #include "smol_rhs.cuh"
 
 using namespace smol;
@@ -50,8 +53,12 @@ static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 static_assert(SCRATCH_BYTES == 15320576, "the scratch size documented in smol.h");
 
 constexpr int MAX_DEVICES = 64;
-unsigned char* g_scratch_ptr[MAX_DEVICES];  // device address of g_scratch per device
-bool g_ready[MAX_DEVICES];
+// Per device: the device address of g_scratch, published by the release store of
+// g_ready (set-up runs once per device under g_setup_mutex, so two host threads making
+// their first call at the same time do not race).
+unsigned char* g_scratch_ptr[MAX_DEVICES];
+std::atomic<bool> g_ready[MAX_DEVICES];
+std::mutex g_setup_mutex;
 
 // Weights: W_t = column t of U (t < R) and row t - R of V (t >= R), zero beyond M.
 __global__ void k_static_weights(const double* __restrict__ U, const double* __restrict__ V, int M, int Mp, int R,
@@ -100,21 +107,22 @@ int ilog2i(int64_t v) {
 
 // Once per device, with that device current: the device address of the scratch array
 // (host code cannot use the symbol itself) and the shared-memory limits of the kernels.
+// The shared-memory limits are raised, never lowered (smol_attr.h), so a system created
+// later with smaller needs cannot break this entry point, and it cannot break them.
 int setup_device(int dev) {
     if (dev < 0 || dev >= MAX_DEVICES) return SMOL_EUNSUPPORTED;
-    if (g_ready[dev]) return SMOL_OK;
+    if (g_ready[dev].load(std::memory_order_acquire)) return SMOL_OK;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (g_ready[dev].load(std::memory_order_relaxed)) return SMOL_OK;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return SMOL_ECUDA;
     const int smax = 2 * 256 * 2 * SMAX_T * 16 + 5 * 256 * 16;  // row pass at Mp = SMAX_M
-    if (cudaFuncSetAttribute(k_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax) != cudaSuccess)
-        return SMOL_ECUDA;
-    if (cudaFuncSetAttribute(k_fwd_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_inv_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) !=
-            cudaSuccess)
+    if (smol_host::raise_smem(k_rows<double>, smax) != cudaSuccess ||
+        smol_host::raise_smem(k_fwd_cols<double>, 96 * 1024) != cudaSuccess ||
+        smol_host::raise_smem(k_inv_cols<double>, 96 * 1024) != cudaSuccess)
         return SMOL_ECUDA;
     g_scratch_ptr[dev] = (unsigned char*)p;
-    g_ready[dev] = true;
+    g_ready[dev].store(true, std::memory_order_release);
     return SMOL_OK;
 }
 

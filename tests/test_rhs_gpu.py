@@ -255,3 +255,23 @@ def test_rhs_at_maximum_size(smol, precision):
     with pytest.raises(smol.SmolError) as e:
         smol.System(U1, V1, 0.002, precision=precision)
     assert e.value.code == smol.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
+def test_small_system_after_large_keeps_large_working(smol, precision):
+    """The kernels' shared-memory limit is one setting per kernel shared by every live
+    system: creating a small system after a large one must not lower it below what the
+    large one launches with. The large system still evaluates and integrates afterwards."""
+    import torch
+    M = 1 << 17
+    U, V = kernel_factors("brownian", M, a=0.9)
+    n = sample_state(M, 0.005)
+    big = smol.System(U, V, 0.005, precision=precision)
+    S0 = big.rhs(torch.from_numpy(n).cuda()).cpu().numpy()
+    Us, Vs = kernel_factors("brownian", 1024, a=0.9)
+    small = smol.System(Us, Vs, 0.005, precision=precision)
+    small.rhs(torch.from_numpy(sample_state(1024, 0.005)).cuda())
+    S1 = big.rhs(torch.from_numpy(n).cuda()).cpu().numpy()
+    assert np.array_equal(S0, S1)
+    _, st = big.integrate(torch.from_numpy(n).cuda(), 0.0, 1e-3, 1e-8, scheme="rkf45")
+    assert st["status"] == 0 and st["accepted"] >= 1, st
