@@ -267,6 +267,14 @@ int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double
 int smol_get_log(smol_system* sys, double* h_t, double* h_tau, double* h_err,
                  int32_t* h_accepted, int32_t cap, int64_t* count);
 
+/* First step of the next integration (Sec. 2 leaves the initial step to the user; the
+ * Euler criterion of Sec. 1 is the default): tau0 > 0 replaces opts.tau0 for later
+ * smol_integrate / smol_integrate_start calls of this system, tau0 = 0 restores it.
+ * A run resumed from a checkpoint with tau0 = the previous call's stats.tau_next
+ * continues the step sequence it would have taken. Not while an integration runs.
+ * Returns SMOL_OK or SMOL_EINVAL. */
+int smol_set_tau0(smol_system* sys, double tau0);
+
 /* Number of distinct forward transforms T used per evaluation (<= 2R). */
 int smol_num_transforms(const smol_system* sys);
 
@@ -296,6 +304,9 @@ int smol_batch_integrate_finish(smol_batch* batch, smol_stats* stats);
  * for each launch mode that smol_tune tries, keeps the fastest for later integrations
  * of this batch and returns its flags in *flags and its microseconds per attempt of the
  * whole batch in *us_per_attempt (either may be NULL). Not while an integration runs. */
+/* Per-system first steps of the next batch integration (as smol_set_tau0): h_tau0
+ * (host, count entries) each > 0, or 0 for the batch's opts.tau0. */
+int smol_batch_set_tau0(smol_batch* batch, const double* h_tau0);
 /* The point sources of system `system` of a batch (as smol_set_sources). */
 int smol_batch_set_sources(smol_batch* batch, int32_t system, int32_t count, const int64_t* sizes,
                            const double* values);

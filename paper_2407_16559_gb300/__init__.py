@@ -92,6 +92,8 @@ SIGNATURES = {
     "smol_partition": (ctypes.c_int, [_I32, _P, _P, _I32, _P, _P]),
     "smol_set_sources": (ctypes.c_int, [_P, _I32, _P, _P]),
     "smol_batch_set_sources": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
+    "smol_set_tau0": (ctypes.c_int, [_P, _D]),
+    "smol_batch_set_tau0": (ctypes.c_int, [_P, _P]),
 }
 
 # option flags (smol_opts.flags)
@@ -290,6 +292,14 @@ class Batch:
         _check(_lib.smol_batch_set_sources(self._h, int(system), k.size, k.ctypes.data, v.ctypes.data),
                "smol_batch_set_sources")
 
+    def set_tau0(self, tau0s):
+        """First steps of the next integration, per system (0: the batch's tau0 option);
+        resuming with each system's stats['tau_next'] continues its step sequence."""
+        v = np.ascontiguousarray(tau0s, dtype=np.float64)
+        if v.size != self.count:
+            raise ValueError("one tau0 per system")
+        _check(_lib.smol_batch_set_tau0(self._h, v.ctypes.data), "smol_batch_set_tau0")
+
     def tune(self, n0s, tol: float, scheme: str = "rkf45", attempts: int = 16):
         """smol_batch_tune: keeps the fastest launch mode for this batch; returns
         (flags, microseconds per attempt of the whole batch)."""
@@ -393,6 +403,11 @@ class System:
         k = np.ascontiguousarray(list(sources.keys()), dtype=np.int64)
         v = np.ascontiguousarray(list(sources.values()), dtype=np.float64)
         _check(_lib.smol_set_sources(self._h, k.size, k.ctypes.data, v.ctypes.data), "smol_set_sources")
+
+    def set_tau0(self, tau0: float):
+        """First step of the next integration (0: the tau0 option); resuming with the
+        previous call's stats['tau_next'] continues its step sequence."""
+        _check(_lib.smol_set_tau0(self._h, float(tau0)), "smol_set_tau0")
 
     def rhs(self, n, out=None):
         """S(n) of Eq. (4) (device tensor of M doubles)."""

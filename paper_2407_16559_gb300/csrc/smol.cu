@@ -295,6 +295,7 @@ struct Engine {
     int run_scheme = 0;
     int64_t run_attempts = 1;
     std::vector<double*> run_dn;
+    std::vector<double> tau0;  // per system: first step of the next integration (<= 0: opts.tau0)
 };
 
 struct smol_system : Engine {};
@@ -940,7 +941,8 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
         h.t1 = t1;
         h.tol = tol;
         h.itol2 = tol > 0.0 ? 1.0 / (tol * tol) : 0.0;
-        h.tau = E->o.tau0 > 0.0 ? E->o.tau0 : (fixed ? E->o.fixed_tau : 0.0);
+        const double tq = (q < (int)E->tau0.size() && E->tau0[q] > 0.0) ? E->tau0[q] : E->o.tau0;
+        h.tau = tq > 0.0 ? tq : (fixed ? E->o.fixed_tau : 0.0);
         h.state[0] = d_n[q];
         h.state[1] = (double*)(E->ws + E->base[q] + E->lay[q].stateB);
     }
@@ -1274,6 +1276,20 @@ int smol_set_stream(smol_system* S, void* stream) {
 }
 
 int smol_num_transforms(const smol_system* S) { return S ? S->T[0] : 0; }
+
+int smol_set_tau0(smol_system* S, double tau0) {
+    if (!S || !(tau0 >= 0.0) || !isfinite(tau0) || S->running) return SMOL_EINVAL;
+    S->tau0.assign(1, tau0);
+    return SMOL_OK;
+}
+
+int smol_batch_set_tau0(smol_batch* B, const double* tau0) {
+    if (!B || !tau0 || B->running) return SMOL_EINVAL;
+    for (int q = 0; q < B->count; ++q)
+        if (!(tau0[q] >= 0.0) || !isfinite(tau0[q])) return SMOL_EINVAL;
+    B->tau0.assign(tau0, tau0 + B->count);
+    return SMOL_OK;
+}
 
 int smol_rhs(smol_system* S, const double* d_n, double* d_out) {
     if (!d_out) return SMOL_EINVAL;

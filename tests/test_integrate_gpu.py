@@ -152,6 +152,43 @@ def test_resume_equals_single_run(smol):
     assert torch.allclose(rest, full, rtol=0, atol=1e-8 * float(full.norm()))
 
 
+def test_resume_with_set_tau0(smol):
+    """smol_set_tau0 resumes the same system object from a checkpoint: a run split at
+    t = 1 takes exactly the steps of a new system created with tau0 = tau_next
+    (bit-identical state) and stays within the tolerance of the unsplit run; a batch
+    resumes each system with its own tau_next."""
+    import torch
+    M = 256
+    U, V = kernel_factors("brownian", M, a=0.3)
+    s = smol.System(U, V, 0.01, tau0=0.01)
+    n0 = torch.from_numpy(monodisperse(M)).cuda()
+    full, st = s.integrate(n0, 0.0, 2.0, 1e-8)
+    half, st1 = s.integrate(n0, 0.0, 1.0, 1e-8)
+    s.set_tau0(st1["tau_next"])
+    rest, st2 = s.integrate(half, st1["t"], 2.0, 1e-8)
+    s2 = smol.System(U, V, 0.01, tau0=st1["tau_next"])
+    rest2, _ = s2.integrate(half, st1["t"], 2.0, 1e-8)
+    assert st2["status"] == 0
+    assert torch.equal(rest, rest2)
+    assert torch.allclose(rest, full, rtol=0, atol=1e-8 * float(full.norm()))
+    s.set_tau0(0.0)  # back to the tau0 option
+    again, st3 = s.integrate(n0, 0.0, 2.0, 1e-8)
+    assert torch.equal(again, full) and st3["accepted"] == st["accepted"]
+    Ms = [100, 300]
+    fs = [kernel_factors("brownian", m, a=0.5) for m in Ms]
+    b = smol.Batch([f[0] for f in fs], [f[1] for f in fs], [0.01, 0.02], tau0=0.01)
+    n0s = [torch.from_numpy(monodisperse(m)).cuda() for m in Ms]
+    bf, sf = b.integrate(n0s, 0.0, 2.0, 1e-8)
+    bh, sh = b.integrate(n0s, 0.0, 1.0, 1e-8)
+    b.set_tau0([x["tau_next"] for x in sh])
+    br, sr = b.integrate(bh, 1.0, 2.0, 1e-8)
+    for q in range(2):
+        sq = smol.System(fs[q][0], fs[q][1], [0.01, 0.02][q], tau0=sh[q]["tau_next"])
+        rq, _ = sq.integrate(bh[q], 1.0, 2.0, 1e-8)
+        assert torch.allclose(br[q], rq, rtol=0, atol=1e-12 * float(rq.abs().max())), q
+        assert torch.allclose(br[q], bf[q], rtol=0, atol=1e-8 * float(bf[q].norm())), q
+
+
 def test_fp32conv_integrate_accuracy(smol):
     """FP32 convolutions with FP64 control on the relaxation workload: the state stays
     within the reduced-precision tolerance 1e-4 (relative, normwise) of the FP64 oracle."""
