@@ -231,13 +231,24 @@ int smol_integrate_finish(smol_system* sys, smol_stats* stats);
 int smol_profile_attempts(smol_system* sys, int32_t reps, double* kernel_ms, int64_t* kernel_launches,
                           int32_t nkinds);
 
+/* Measurement aid: the fused multiply-add rate of this GPU in FP64 (precision =
+ * SMOL_FP64) or FP32 (SMOL_FP32CONV), the arithmetic ceiling that the right-hand side's
+ * transforms are reported against (the paper gives no hardware figures; it only states
+ * the O(M R log M) cost of the FFT route, Sec. 1). Runs 4 CTAs of 256 threads per SM,
+ * each thread 8 independent chains of `iters` dependent fused multiply-adds, once to
+ * warm up and once timed with CUDA events on `stream` (cudaStream_t or NULL); returns
+ * *tflops = 2 x 8 x iters x threads / time (FMA = 2 flop) and, when non-NULL, *ms the
+ * timed kernel's duration. Synchronises the stream. SMOL_EINVAL or SMOL_ECUDA on error. */
+int smol_fma_rate(int32_t precision, int64_t iters, void* stream, double* tflops, double* ms);
+
 /* Constant point sources of Eq. (3): dn_s/dt = S_s(n) + P_s at up to SMOL_MAX_SOURCES
  * sizes (Sec. 3.1 injects P_1 = 1 and P_100 = p). With lambda = 0 the system is Eq. (3);
  * with lambda > 0 the sources are added to Eq. (4). sizes are 1-based (1..M), values
  * finite; count = 0 removes them. They enter S(n) (smol_rhs and the integrators; for
  * s = 1 through the FP64 monomer equation) but not the separate terms of
- * smol_rhs_terms. Not while an integration runs (between smol_integrate_start and
- * smol_integrate_finish). Returns SMOL_OK or SMOL_EINVAL. */
+ * smol_rhs_terms. They apply from the next smol_integrate / smol_integrate_start; a run
+ * started before cannot then be continued with smol_integrate_advance (which returns
+ * SMOL_EINVAL until the next start). Returns SMOL_OK or SMOL_EINVAL. */
 #define SMOL_MAX_SOURCES 8
 int smol_set_sources(smol_system* sys, int32_t count, const int64_t* sizes, const double* values);
 
@@ -271,7 +282,8 @@ int smol_get_log(smol_system* sys, double* h_t, double* h_tau, double* h_err,
  * Euler criterion of Sec. 1 is the default): tau0 > 0 replaces opts.tau0 for later
  * smol_integrate / smol_integrate_start calls of this system, tau0 = 0 restores it.
  * A run resumed from a checkpoint with tau0 = the previous call's stats.tau_next
- * continues the step sequence it would have taken. Not while an integration runs.
+ * continues the step sequence it would have taken. Takes effect at the next
+ * smol_integrate / smol_integrate_start (a run already started keeps its step).
  * Returns SMOL_OK or SMOL_EINVAL. */
 int smol_set_tau0(smol_system* sys, double tau0);
 
@@ -303,7 +315,8 @@ int smol_batch_integrate_finish(smol_batch* batch, smol_stats* stats);
  * `attempts` attempts of every system from copies of the states d_n[q] (not modified)
  * for each launch mode that smol_tune tries, keeps the fastest for later integrations
  * of this batch and returns its flags in *flags and its microseconds per attempt of the
- * whole batch in *us_per_attempt (either may be NULL). Not while an integration runs. */
+ * whole batch in *us_per_attempt (either may be NULL). A run started before cannot be
+ * continued afterwards (start a new one). */
 /* Per-system first steps of the next batch integration (as smol_set_tau0): h_tau0
  * (host, count entries) each > 0, or 0 for the batch's opts.tau0. */
 int smol_batch_set_tau0(smol_batch* batch, const double* h_tau0);

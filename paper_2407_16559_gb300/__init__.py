@@ -93,6 +93,7 @@ SIGNATURES = {
     "smol_set_sources": (ctypes.c_int, [_P, _I32, _P, _P]),
     "smol_batch_set_sources": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
     "smol_set_tau0": (ctypes.c_int, [_P, _D]),
+    "smol_fma_rate": (ctypes.c_int, [_I32, _I64, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "smol_batch_set_tau0": (ctypes.c_int, [_P, _P]),
 }
 
@@ -148,6 +149,18 @@ def rhs_static(U, V, lam: float, n, out=None, stream=None):
     _check(_lib.smol_rhs_static(M, R, U.data_ptr(), V.data_ptr(), float(lam), n.data_ptr(), out.data_ptr(),
                                 st.cuda_stream), "smol_rhs_static")
     return out
+
+
+def fma_rate(precision: str = "fp64", iters: int = 20000, stream=None):
+    """smol_fma_rate: measured fused multiply-add rate (TFLOP/s, FMA = 2 flop) and the
+    timed kernel's milliseconds, in FP64 ('fp64') or FP32 ('fp32conv')."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.smol_fma_rate(PRECISIONS[precision], int(iters), ctypes.c_void_p(stream.cuda_stream),
+                              ctypes.byref(tf), ctypes.byref(ms)), "smol_fma_rate")
+    return tf.value, ms.value
 
 
 def tune(U, V, lam: float, n0, tol: float, scheme: str = "rkf45", precision: str = "fp64", attempts: int = 64,

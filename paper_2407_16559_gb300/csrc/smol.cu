@@ -1198,7 +1198,7 @@ constexpr int PDL_BITS = SMOL_FLAG_NO_PDL | SMOL_FLAG_NO_PDL_FWD_COLS | SMOL_FLA
 namespace {
 static_assert(SMOL_MAX_SOURCES == MAXSRC, "source capacity of the C interface and the kernels");
 int set_sources(Engine* E, int q, int32_t count, const int64_t* sizes, const double* values) {
-    if (!E || q < 0 || q >= E->count || count < 0 || count > MAXSRC || E->running) return SMOL_EINVAL;
+    if (!E || q < 0 || q >= E->count || count < 0 || count > MAXSRC) return SMOL_EINVAL;
     if (count > 0 && (!sizes || !values)) return SMOL_EINVAL;
     for (int k = 0; k < count; ++k)
         if (sizes[k] < 1 || sizes[k] > E->sh[q].M || !isfinite(values[k])) return SMOL_EINVAL;
@@ -1217,12 +1217,14 @@ int set_sources(Engine* E, int q, int32_t count, const int64_t* sizes, const dou
         E->h_one = E->hs[0];
         E->h_oner = E->hsr[0];
     }
-    // captured graphs hold the old descriptor (single systems pass it by value)
+    // captured graphs hold the old descriptor (single systems pass it by value); a run
+    // started before cannot be continued with smol_integrate_advance
     if (E->gexec) {
         cudaGraphExecDestroy(E->gexec);
         E->gexec = nullptr;
     }
     E->gkey = -1;
+    E->running = false;
     return SMOL_OK;
 }
 }  // namespace
@@ -1278,13 +1280,13 @@ int smol_set_stream(smol_system* S, void* stream) {
 int smol_num_transforms(const smol_system* S) { return S ? S->T[0] : 0; }
 
 int smol_set_tau0(smol_system* S, double tau0) {
-    if (!S || !(tau0 >= 0.0) || !isfinite(tau0) || S->running) return SMOL_EINVAL;
+    if (!S || !(tau0 >= 0.0) || !isfinite(tau0)) return SMOL_EINVAL;
     S->tau0.assign(1, tau0);
     return SMOL_OK;
 }
 
 int smol_batch_set_tau0(smol_batch* B, const double* tau0) {
-    if (!B || !tau0 || B->running) return SMOL_EINVAL;
+    if (!B || !tau0) return SMOL_EINVAL;
     for (int q = 0; q < B->count; ++q)
         if (!(tau0[q] >= 0.0) || !isfinite(tau0[q])) return SMOL_EINVAL;
     B->tau0.assign(tau0, tau0 + B->count);
@@ -1498,8 +1500,7 @@ int smol_batch_set_stream(smol_batch* B, void* stream) {
 
 int smol_batch_tune(smol_batch* B, double* const* d_n, double tol, int32_t scheme, int32_t attempts,
                     int32_t* flags, double* us_per_attempt) {
-    if (!B || !d_n || attempts < 1 || scheme < SMOL_RK2 || scheme > SMOL_RKF45 || !(tol > 0.0) || B->running)
-        return SMOL_EINVAL;
+    if (!B || !d_n || attempts < 1 || scheme < SMOL_RK2 || scheme > SMOL_RKF45 || !(tol > 0.0)) return SMOL_EINVAL;
     for (int q = 0; q < B->count; ++q)
         if (!d_n[q] || ((uintptr_t)d_n[q] & 15)) return SMOL_EINVAL;
     std::vector<double*> work(B->count, nullptr);
@@ -1530,6 +1531,7 @@ int smol_batch_tune(smol_batch* B, double* const* d_n, double tol, int32_t schem
         cudaGraphExecDestroy(B->gexec);
         B->gexec = nullptr;
     }
+    B->running = false;  // the timings ran on scratch copies: nothing to continue
     for (double* w : work)
         if (w) cudaFree(w);
     if (rc == SMOL_OK && best < 0.0) rc = SMOL_ECUDA;
