@@ -47,7 +47,7 @@ LAUNCHES_FUSED = 13         # forward columns, 6 x row kernel, 5 x fused inverse
 LAUNCHES_UNFUSED = 19       # 6 x (forward columns, rows, inverse columns) + combination / control
 FLAG_NO_FUSE = 32           # smol_opts.flags bit (SMOL_FLAG_NO_FUSE)
 L2_FLUSH_BYTES = 256 << 20
-CTL_BYTES = 240             # the device control block of one system (smol::Ctl)
+CTL_BYTES = 264             # the device control block of one system (smol::Ctl)
 
 # Peaks. HBM: the copy bandwidth of MEASURED_PEAKS.json (written by the pool's driver;
 # read at run time), else the fallback figure. FP64 and FP32 arithmetic: measured live
@@ -700,8 +700,9 @@ def tts_relax(smol, torch, stream):
                     break
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
-            errs = [rel_err_bound(h.cpu().numpy(), float(tl), g["head"][k], float(g["tail_norm"][k]))
-                    for k, (h, tl) in enumerate(zip(heads, tails))]
+            hidx = list(g["head_idx"]) if "head_idx" in g else list(range(len(g["head"])))
+            errs = [rel_err_bound(heads[k].cpu().numpy(), float(tails[k]), g["head"][j], float(g["tail_norm"][j]))
+                    for j, k in enumerate(hidx) if k < len(heads)]
             row[form] = {"seconds": wall, "attempts": att, "oracle_attempts": int(g["attempts"][len(errs) - 1]),
                          "max_rel_err_vs_oracle": max(errs), "first_rel_err": errs[0],
                          "mass_drift": abs(st["mass"] - float(g["mass"][len(errs) - 1])), "status": st["status"]}

@@ -350,7 +350,7 @@ void smol_batch_destroy(smol_batch* batch);
  *   M <= SMOL_STATIC_MAX_M, 1 <= R <= SMOL_STATIC_MAX_R, lambda >= 0.
  *   d_U: device, M x R row-major; d_V: device, R x M row-major; d_n, d_out: device,
  *   M doubles each, 16-byte aligned, not overlapping. stream: cudaStream_t or NULL.
- * Its scratch memory is a fixed device array of 15,320,576 bytes inside the library,
+ * Its scratch memory is a fixed device array of 15,320,832 bytes inside the library,
  * which every GPU that loads the library holds until exit. The first call on a device
  * looks up that array's device address and sets kernel attributes (once per device);
  * make that first call before any stream capture. All calls on a device share the

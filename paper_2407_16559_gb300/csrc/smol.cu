@@ -1143,10 +1143,11 @@ int rhs_common(smol_system* S, const double* d_n, double* d_out, double* d_birth
     eo.hfac = 1.0;
     const LaunchArgs A = args_for(S, true);
     if (S->o.precision == SMOL_FP32CONV) {
-        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n);
+        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n, 1);
+        k_tilt<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n);
         launch_eval<float>(S, A, in, eo, st, nullptr);
     } else if (S->o.precision == SMOL_DF64) {
-        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n);
+        k_absmax<<<S->H.nF, FIN_THREADS, 0, st>>>(A.sys, A.mapF, A.one, d_n, 0);
         launch_eval<dd>(S, A, in, eo, st, nullptr);
     } else {
         launch_eval<double>(S, A, in, eo, st, nullptr);

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(128) k_lincomb(const SysDev* __restrict__ sysv
 // norm) and need no square root; err itself (stats and log) is formed by another
 // thread at the same time (error_norm).
 __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, Ctl& cref, double E, double C,
-                                           double X, bool bad, double MS, double Q) {
+                                           double X, bool bad, double MS, double Q, double TB, const float* TMX) {
     Ctl* c = &cref;
     c->arrive = 0;
     if (!c->reuse) c->rhs_evals += 1;  // S(n^k) of the first stage (reused on a retry)
@@ -165,6 +165,8 @@ __device__ __forceinline__ void controller(const CtlParams& P, const SysDev& S, 
         c->ymax = X;
         c->mass = MS;
         set_xe(c, S, X);
+        c->tilt = tilt_from_bound(TB, S.Mp, S.T);  // FP32 form (the other forms ignore it)
+        for (int t = 0; t < TILT_T; ++t) c->tlog[t] = tilt_log(TMX[t]);
         if (!c->clamped) c->tau = tau_new;
         c->reuse = 0;
     } else {
@@ -227,6 +229,8 @@ struct FinAcc {
     double se, sc, ms;
     unsigned long long mxb;
     float fse, fsc, fmx;
+    float tb;              // FP32 form: the candidate's tilt bound (against the current state's
+    float tmx[TILT_T];     // input maxima) and its own input maxima max_i |W_t[i] n_i|
     bool fbad;
 };
 __device__ __forceinline__ FinAcc fin_acc() {
@@ -234,6 +238,9 @@ __device__ __forceinline__ FinAcc fin_acc() {
     a.se = a.sc = a.ms = 0.0;
     a.mxb = 0ull;
     a.fse = a.fsc = a.fmx = 0.f;
+    a.tb = INFINITY;
+#pragma unroll
+    for (int t = 0; t < TILT_T; ++t) a.tmx[t] = 0.f;
     a.fbad = false;
     return a;
 }
@@ -252,7 +259,7 @@ __device__ __forceinline__ void fin_acc_close(FinAcc& a) {
 // kernel reads the stage vector it has just written).
 template <typename R>
 __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const Terms<R>& tp, double* outp,
-                                         void* shadv, int i, FinAcc& a) {
+                                         void* shadv, int i, FinAcc& a, const float* tlog) {
     const StageIn& in = cd.in;
     const int p = i >> 1;
     const bool two = i + 1 < S.M;
@@ -317,6 +324,18 @@ __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const
         a.fsc += f0 * f0 + f1 * f1;
         a.fmx = fmaxf(a.fmx, fmaxf(fabsf(f0), fabsf(f1)));
         a.fbad = a.fbad || !isfinite(f0) || !isfinite(f1);
+        if (S.T <= TILT_T) {
+            // the next attempt's tilt: the transform inputs W_t n of the candidate
+            const float* Wf = reinterpret_cast<const float*>(S.W);
+#pragma unroll
+            for (int t = 0; t < TILT_T; ++t)
+                if (t < S.T) {
+                    const float w0 = __ldg(Wf + (size_t)t * S.Mp + i), w1 = two ? __ldg(Wf + (size_t)t * S.Mp + i + 1) : 0.f;
+                    const float v0 = w0 * f0, v1 = w1 * f1;
+                    a.tmx[t] = fmaxf(a.tmx[t], fmaxf(fabsf(v0), fabsf(v1)));
+                    a.tb = fminf(a.tb, fminf(tilt_bound_el(tlog[t], v0, i), tilt_bound_el(tlog[t], v1, i + 1)));
+                }
+        }
     } else if constexpr (std::is_same<R, dd>::value) {
         // Double-float form: the stage terms (double-float) are combined in double-float
         // arithmetic (high and low parts each through df_fma), the FP64 terms in FP64;
@@ -422,6 +441,9 @@ __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const
 struct FinSm {
     double wred[4][8];
     unsigned long long xred[8];
+    double tredd[8];
+    float tred[8];
+    float tmred[TILT_T][8];
     bool last;
 };
 
@@ -437,11 +459,18 @@ __device__ __forceinline__ void fin_tail(const SysDev& S, const CtlParams& P, Ct
     fin_acc_close<R>(acc);
     double se = acc.se, sc = acc.sc, ms = acc.ms;
     unsigned long long mxb = acc.mxb;
+    float tb = acc.tb;
+    float tmx[TILT_T];
+#pragma unroll
+    for (int t = 0; t < TILT_T; ++t) tmx[t] = acc.tmx[t];
     for (int o = 16; o > 0; o >>= 1) {
         se += __shfl_down_sync(0xffffffffu, se, o);
         sc += __shfl_down_sync(0xffffffffu, sc, o);
         ms += __shfl_down_sync(0xffffffffu, ms, o);
         mxb = max(mxb, __shfl_down_sync(0xffffffffu, mxb, o));
+        tb = fminf(tb, __shfl_down_sync(0xffffffffu, tb, o));
+#pragma unroll
+        for (int t = 0; t < TILT_T; ++t) tmx[t] = fmaxf(tmx[t], __shfl_down_sync(0xffffffffu, tmx[t], o));
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) {
@@ -449,32 +478,52 @@ __device__ __forceinline__ void fin_tail(const SysDev& S, const CtlParams& P, Ct
         f.wred[1][warp] = sc;
         f.wred[2][warp] = ms;
         f.xred[warp] = mxb;
+        f.tred[warp] = tb;
+#pragma unroll
+        for (int t = 0; t < TILT_T; ++t) f.tmred[t][warp] = tmx[t];
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x >= 5 && threadIdx.x < 5 + TILT_T) {
+        const int t = threadIdx.x - 5;
+        float x = f.tmred[t][0];
+        for (int w = 1; w < nw; ++w) x = fmaxf(x, f.tmred[t][w]);
+        S.fpart[FPW * blk + 5 + t] = (double)x;  // slots 5..: input maxima of the tilt
+    }
+    if (threadIdx.x < 5) {
         const int q = threadIdx.x;
         double v = 0.0;
         if (q == 2) {
             unsigned long long x = f.xred[0];
             for (int w = 1; w < nw; ++w) x = max(x, f.xred[w]);
             v = __longlong_as_double((long long)x);
+        } else if (q == 4) {
+            float x = f.tred[0];
+            for (int w = 1; w < nw; ++w) x = fminf(x, f.tred[w]);
+            v = (double)x;
         } else {
             const int r = q < 2 ? q : 2;
             v = f.wred[r][0];
             for (int w = 1; w < nw; ++w) v += f.wred[r][w];
         }
-        S.fpart[FPW * blk + (q == 3 ? 4 : q)] = v;  // E, C, max bits, -, mass moment
+        // slots: E, C, max bits, tilt bound, mass moment
+        S.fpart[FPW * blk + (q == 3 ? 4 : (q == 4 ? 3 : q))] = v;
     }
     if (!arrive_last(ctl, nblk, &f.last)) return;
-    double E = 0.0, C = 0.0, Q = 0.0, MS = 0.0;
+    double E = 0.0, C = 0.0, Q = 0.0, MS = 0.0, TB = INFINITY;
     unsigned long long XB = 0ull;
+    float TM[TILT_T];
+#pragma unroll
+    for (int t = 0; t < TILT_T; ++t) TM[t] = 0.f;
 #pragma unroll 4
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         const double* q = S.fpart + FPW * b;
         E += __ldcg(q);
         C += __ldcg(q + 1);
         XB = max(XB, (unsigned long long)__double_as_longlong(__ldcg(q + 2)));
+        TB = fmin(TB, __ldcg(q + 3));
         MS += __ldcg(q + 4);
+#pragma unroll
+        for (int t = 0; t < TILT_T; ++t) TM[t] = fmaxf(TM[t], (float)__ldcg(q + 5 + t));
     }
     if (P.steady)
         for (int b = threadIdx.x; b < S.nbx; b += blockDim.x) Q += __ldcg(S.sqpart + b);
@@ -484,6 +533,9 @@ __device__ __forceinline__ void fin_tail(const SysDev& S, const CtlParams& P, Ct
         Q += __shfl_down_sync(0xffffffffu, Q, o);
         MS += __shfl_down_sync(0xffffffffu, MS, o);
         XB = max(XB, __shfl_down_sync(0xffffffffu, XB, o));
+        TB = fmin(TB, __shfl_down_sync(0xffffffffu, TB, o));
+#pragma unroll
+        for (int t = 0; t < TILT_T; ++t) TM[t] = fmaxf(TM[t], __shfl_down_sync(0xffffffffu, TM[t], o));
     }
     const double nrm2_0 = cs.nrm2;  // read before the controller may overwrite them
     const int64_t att0 = cs.attempts;
@@ -494,21 +546,32 @@ __device__ __forceinline__ void fin_tail(const SysDev& S, const CtlParams& P, Ct
         f.wred[2][warp] = MS;
         f.wred[3][warp] = Q;
         f.xred[warp] = XB;
+        f.tredd[warp] = TB;
+#pragma unroll
+        for (int t = 0; t < TILT_T; ++t) f.tmred[t][warp] = TM[t];
     }
     __syncthreads();
     const int t2 = blockDim.x > 32 ? 32 : 0;
     if (threadIdx.x == 0 || threadIdx.x == t2) {
-        E = f.wred[0][0], C = f.wred[1][0], MS = f.wred[2][0], Q = f.wred[3][0], XB = f.xred[0];
+        E = f.wred[0][0], C = f.wred[1][0], MS = f.wred[2][0], Q = f.wred[3][0], XB = f.xred[0], TB = f.tredd[0];
         for (int w = 1; w < nw; ++w) {
             E += f.wred[0][w];
             C += f.wred[1][w];
             MS += f.wred[2][w];
             Q += f.wred[3][w];
             XB = max(XB, f.xred[w]);
+            TB = fmin(TB, f.tredd[w]);
         }
         const bool bad = XB >= INF_BITS;
         if (threadIdx.x == t2) error_norm(P, S, cs, nrm2_0, att0, E, bad, Q);
-        if (threadIdx.x == 0) controller(P, S, cs, E, C, __longlong_as_double((long long)XB), bad, MS, Q);
+        if (threadIdx.x == 0) {
+            float TMX[TILT_T];
+            for (int t = 0; t < TILT_T; ++t) {
+                TMX[t] = f.tmred[t][0];
+                for (int w = 1; w < nw; ++w) TMX[t] = fmaxf(TMX[t], f.tmred[t][w]);
+            }
+            controller(P, S, cs, E, C, __longlong_as_double((long long)XB), bad, MS, Q, TB, TMX);
+        }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < CW; q += blockDim.x)
@@ -543,7 +606,7 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
     FinAcc acc = fin_acc();
     const int np = (S.M + 1) >> 1;
     for (int p = blk * blockDim.x + threadIdx.x; p < np; p += S.nfin * blockDim.x)
-        fin_pair<R>(S, cd, tp, outp, shad, 2 * p, acc);
+        fin_pair<R>(S, cd, tp, outp, shad, 2 * p, acc, cv.tlog);
     fin_tail<R>(S, P, S.ctl, cs, blk, S.nfin, acc, f);
 }
 
@@ -578,7 +641,7 @@ __global__ void __launch_bounds__(256) k_inv_finish(const SysDev* __restrict__ s
     const int half = (S.N1 >> 1) * S.G;
     for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
         const int i = col_elem(S, DG, bx, idx);
-        if (i < S.M) fin_pair<R>(S, cd, tp, outp, shad, i, acc);
+        if (i < S.M) fin_pair<R>(S, cd, tp, outp, shad, i, acc, cv.tlog);
     }
     fin_tail<R>(S, P, S.ctl, cs, bx, S.nbx, acc, f);
 }
@@ -621,7 +684,7 @@ __global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, 
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ double red[33];
-    __shared__ double fin[MAXT + 3];
+    __shared__ double fin[MAXT + 3 + TILT_T];
     __shared__ bool last;
     const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
@@ -630,11 +693,17 @@ __global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, 
     const int W = S.T + 3;  // mu_t..., n2, max, mass
     double acc[MAXT + 3];
     for (int q = 0; q < W; ++q) acc[q] = 0.0;
+    double tmx[TILT_T];  // max_i |W_t[i] n_i| (the FP32 form's input tilt)
+    for (int t = 0; t < TILT_T; ++t) tmx[t] = 0.0;
     R* shad = S.shadow0 ? reinterpret_cast<R*>(cv.cur ? S.shadow1 : S.shadow0) : nullptr;
     for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) {
         const double y = n[i];
         if (shad) shad[i] = (R)y;
-        for (int t = 0; t < S.T; ++t) acc[t] += (double)Wr[(size_t)t * S.Mp + i] * y;
+        for (int t = 0; t < S.T; ++t) {
+            const double x = (double)Wr[(size_t)t * S.Mp + i] * y;
+            acc[t] += x;
+            if (t < TILT_T) tmx[t] = fmax(tmx[t], fabs(x));
+        }
         acc[S.T] += y * y;
         acc[S.T + 1] = fmax(acc[S.T + 1], fabs(y));
         acc[S.T + 2] += (double)(i + 1) * y;
@@ -643,17 +712,23 @@ __global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, 
         const double v = (q == S.T + 1) ? block_max(acc[q], red) : block_sum(acc[q], red);
         if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk + q] = v;
     }
+    for (int t = 0; t < TILT_T; ++t) {  // slots W.. (FPW >= MAXT + 4 >= W + TILT_T)
+        const double v = block_max(tmx[t], red);
+        if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk + W + t] = v;
+    }
     if (!arrive_last(ctl, S.nfin, &last)) return;
-    for (int q = 0; q < W; ++q) {
+    for (int q = 0; q < W + TILT_T; ++q) {
+        const bool mx = q == S.T + 1 || q >= W;
         double v = 0.0;
         for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) {
             const double x = __ldcg(S.fpart + (size_t)FPW * b + q);
-            v = (q == S.T + 1) ? fmax(v, x) : v + x;
+            v = mx ? fmax(v, x) : v + x;
         }
-        v = (q == S.T + 1) ? block_max(v, red) : block_sum(v, red);
+        v = mx ? block_max(v, red) : block_sum(v, red);
         if (threadIdx.x == 0) fin[q] = v;
     }
     if (threadIdx.x != 0) return;
+    for (int t = 0; t < TILT_T; ++t) ctl->tlog[t] = tilt_log((float)fin[W + t]);
     ctl->arrive = 0;
     ctl->nrm2 = fin[S.T];
     ctl->ymax = fin[S.T + 1];
@@ -665,7 +740,8 @@ __global__ void __launch_bounds__(128) k_prep1(const SysDev* __restrict__ sysv, 
 
 // Pass 2: collision rate D_i = sum_j K_ij n_j = sum_t delta_t W_t[i]; its maximum
 // gives the first step by the Euler criterion of Sec. 1, tau0 = a / max_i D_i, when
-// the caller gave none (ctl->tau <= 0). Then the first attempt's step h is set.
+// the caller gave none (ctl->tau <= 0). Then the first attempt's step h is set, and
+// (FP32 form) the input tilt from max |n| of pass 1.
 template <typename R>
 __global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                const __grid_constant__ SysDev one, double euler_a) {
@@ -676,20 +752,34 @@ __global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, 
     const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
     const R* Wr = reinterpret_cast<const R*>(S.W);
-    double mx = -INFINITY;
+    const double* n = cv.cur ? cv.s1 : cv.s0;
+    double mx = -INFINITY, tb = INFINITY;
     for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) {
         double d = 0.0;
-        for (int t = 0; t < S.T; ++t) d += __ldcg(S.aux + t) * (double)Wr[(size_t)t * S.Mp + i];
+        for (int t = 0; t < S.T; ++t) {
+            const double w = (double)Wr[(size_t)t * S.Mp + i];
+            d += __ldcg(S.aux + t) * w;
+            if (t < TILT_T) tb = fmin(tb, (double)tilt_bound_el(cv.tlog[t], (float)(w * n[i]), i));
+        }
         mx = fmax(mx, d);
     }
     mx = block_max(mx, red);
-    if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk] = mx;
+    tb = -block_max(-tb, red);
+    if (threadIdx.x == 0) {
+        S.fpart[(size_t)FPW * blk] = mx;
+        S.fpart[(size_t)FPW * blk + 1] = tb;
+    }
     if (!arrive_last(ctl, S.nfin, &last)) return;
-    double rate = -INFINITY;
-    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) rate = fmax(rate, __ldcg(S.fpart + (size_t)FPW * b));
+    double rate = -INFINITY, tbm = INFINITY;
+    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) {
+        rate = fmax(rate, __ldcg(S.fpart + (size_t)FPW * b));
+        tbm = fmin(tbm, __ldcg(S.fpart + (size_t)FPW * b + 1));
+    }
     rate = block_max(rate, red);
+    tbm = -block_max(-tbm, red);
     if (threadIdx.x != 0) return;
     ctl->arrive = 0;
+    ctl->tilt = tilt_from_bound(tbm, S.Mp, S.T);  // FP32 form: the first attempt's input tilt
     if (!(ctl->tau > 0.0)) ctl->tau = (rate > 0.0) ? euler_a / rate : 1.0;
     if (ctl->t >= ctl->t1) ctl->done = 1;
     else set_next_step(ctl);
@@ -698,25 +788,70 @@ __global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, 
 // max_i |n_i| of the caller's vector into ctl->ymax (input scaling of a standalone
 // FP32 evaluation; single system).
 __global__ void __launch_bounds__(128) k_absmax(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                                const __grid_constant__ SysDev one, const double* __restrict__ n) {
+                                                const __grid_constant__ SysDev one, const double* __restrict__ n,
+                                                int tilt) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
     __shared__ double red[33];
     __shared__ bool last;
     const int blk = load_sys(sysv, map, one, S, cv);
     Ctl* ctl = S.ctl;
-    double mx = 0.0;
-    for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) mx = fmax(mx, fabs(n[i]));
+    // with tilt (FP32 weights): also max_i |W_t[i] n_i| per transform t < TILT_T
+    const float* Wf = tilt ? reinterpret_cast<const float*>(S.W) : nullptr;
+    double mx = 0.0, tmx[TILT_T];
+    for (int t = 0; t < TILT_T; ++t) tmx[t] = 0.0;
+    for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x) {
+        mx = fmax(mx, fabs(n[i]));
+        if (Wf)
+            for (int t = 0; t < S.T && t < TILT_T; ++t) tmx[t] = fmax(tmx[t], fabs((double)Wf[(size_t)t * S.Mp + i] * n[i]));
+    }
     mx = block_max(mx, red);
     if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk] = mx;
+    for (int t = 0; t < TILT_T; ++t) {
+        const double v = block_max(tmx[t], red);
+        if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk + 1 + t] = v;
+    }
     if (!arrive_last(ctl, S.nfin, &last)) return;
-    double m = 0.0;
-    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) m = fmax(m, __ldcg(S.fpart + (size_t)FPW * b));
-    m = block_max(m, red);
+    for (int q = 0; q <= TILT_T; ++q) {
+        double m = 0.0;
+        for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) m = fmax(m, __ldcg(S.fpart + (size_t)FPW * b + q));
+        m = block_max(m, red);
+        if (threadIdx.x != 0) continue;
+        if (q == 0) {
+            ctl->ymax = m;
+            set_xe(ctl, S, m);
+        } else {
+            ctl->tlog[q - 1] = tilt_log((float)m);
+        }
+    }
+    if (threadIdx.x == 0) ctl->arrive = 0;
+}
+
+// The input tilt of a standalone FP32 evaluation of the caller's vector n (after
+// k_absmax has stored the transform inputs' maxima; single system).
+__global__ void __launch_bounds__(128) k_tilt(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                              const __grid_constant__ SysDev one, const double* __restrict__ n) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ double red[33];
+    __shared__ bool last;
+    const int blk = load_sys(sysv, map, one, S, cv);
+    Ctl* ctl = S.ctl;
+    const float* Wf = reinterpret_cast<const float*>(S.W);
+    double tb = INFINITY;
+    if (S.T <= TILT_T)
+        for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x)
+            for (int t = 0; t < S.T; ++t)
+                tb = fmin(tb, (double)tilt_bound_el(cv.tlog[t], Wf[(size_t)t * S.Mp + i] * (float)n[i], i));
+    tb = -block_max(-tb, red);
+    if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk] = tb;
+    if (!arrive_last(ctl, S.nfin, &last)) return;
+    double m = INFINITY;
+    for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) m = fmin(m, __ldcg(S.fpart + (size_t)FPW * b));
+    m = -block_max(-m, red);
     if (threadIdx.x != 0) return;
     ctl->arrive = 0;
-    ctl->ymax = m;
-    set_xe(ctl, S, m);
+    ctl->tilt = tilt_from_bound(m, S.Mp, S.T);
 }
 
 // Keeps the stream busy for about `cycles` SM clocks (a bounded loop on the clock

@@ -47,8 +47,9 @@ constexpr int MAXR = 8;         // largest rank R
 constexpr int MAXT = 2 * MAXR;  // largest number of distinct transforms
 constexpr int MAXV = 10;        // terms of a stage-input linear combination
 constexpr int NVEC = 12;        // stage / work vectors per system
-constexpr int FPW = MAXT + 4;   // doubles per block of the finish / preparation partials
+constexpr int FPW = MAXT + 8;   // doubles per block of the finish / preparation partials
 constexpr int MAXSRC = 8;       // point sources P_k of Eq. (3) per system
+constexpr int TILT_T = 4;       // FP32 form: input tilt for systems of at most this many transforms
 
 // Device-resident control block of one system's integration (and of standalone
 // evaluations).
@@ -69,6 +70,9 @@ struct Ctl {
                                 // (h / hf) S(n^k) of the current state, and the next
                                 // attempt rescales it instead of evaluating S(n^k) again
     int32_t xe[MAXT];           // FP32 form: input scale exponents of the transforms
+    int32_t tilt;               // FP32 form: exponential tilt 2^(tilt i / Mp) of the inputs
+    int32_t pad_;
+    float tlog[TILT_T];         // FP32 form: log2 max_i |W_t[i] n_i| of the current state, t < TILT_T
 };
 
 // One system, as the kernels see it (device memory; 256-byte aligned array).
@@ -150,6 +154,8 @@ struct CtlView {
     const double* s0;
     const double* s1;
     double h, ymax;
+    int tilt;  // Ctl::tilt
+    float tlog[TILT_T];
     int xe[MAXT];
 };
 
@@ -211,11 +217,15 @@ struct vec2<dd> {
 // FP64 form's folded spectral constants.
 template <typename R>
 struct Tr {
-    static constexpr bool scaled = true, shadowed = true, fp64 = false;
+    static constexpr bool scaled = true, shadowed = true, fp64 = false, tilted = false;
+};
+template <>
+struct Tr<float> {
+    static constexpr bool scaled = true, shadowed = true, fp64 = false, tilted = true;
 };
 template <>
 struct Tr<double> {
-    static constexpr bool scaled = false, shadowed = false, fp64 = true;
+    static constexpr bool scaled = false, shadowed = false, fp64 = true, tilted = false;
 };
 // Column transforms pruned to the zero padding (HALF_IN) and to the sizes up to M
 // (HALF_OUT): FP64 and FP32; not double-float, whose kernels are bound by instruction
@@ -337,6 +347,49 @@ __device__ __forceinline__ void set_xe(Ctl* c, const SysDev& S, double ymax) {
     const int ey = (ymax > 0.0 && isfinite(ymax)) ? ilogb(ymax) : 0;
     for (int t = 0; t < S.T; ++t) c->xe[t] = S.wexp[t] + ey;
 }
+
+// Exponential tilt of the FP32 form (exponential tilting of a convolution: if x'_i =
+// x_i theta^i and y'_j = y_j theta^j then (x' * y')_m = theta^m (x * y)_m). A transform
+// rounds every output to about eps ||x'|| ||y'||; after the output is multiplied back by
+// theta^-m that floor falls off as theta^-m, so the tail of the size distribution, where
+// the true birth terms are tiny but the shattering source weights them by powers of the
+// size, no longer carries the FP32 rounding of the whole transform. theta = 2^(p / Mp)
+// with an integer p in [0, TILT_PMAX], chosen from the state so that |n_i| theta^i <=
+// max |n| (the inputs keep their largest entry at the head, and their norm).
+constexpr int TILT_PMAX = 48;
+// 2^(p i / Mp) and 2^(-p i / Mp) in FP32: p i is an exact integer (p <= TILT_PMAX,
+// i < 2^25), its fraction over Mp goes through exp2f, the integer part is a power of two.
+__device__ __forceinline__ float pow2f_int(int e) {
+    e = max(-126, min(127, e));
+    return __int_as_float((127 + e) << 23);
+}
+__device__ __forceinline__ float tilt_up(int p, int i, int lgMp) {
+    const int E = p * i;
+    return exp2f((float)(E & ((1 << lgMp) - 1)) * pow2f_int(-lgMp)) * pow2f_int(E >> lgMp);
+}
+__device__ __forceinline__ float tilt_down(int p, int i, int lgMp) {
+    const int E = p * i;
+    return exp2f(-(float)(E & ((1 << lgMp) - 1)) * pow2f_int(-lgMp)) * pow2f_int(-(E >> lgMp));
+}
+// The tilt must keep every transform's input below its own largest entry: with
+// x_t[i] = W_t[i] n_i, b = min_t min_i (log2 max_j |x_t[j]| - log2 |x_t[i]|) / i over the
+// nonzero entries i >= 1 (+inf when there are none), and p = floor(b Mp), clamped. The
+// bound of an accepted state sets the tilt of the next attempt's evaluations (all of
+// them: an evaluation's forward and inverse passes must use the same tilt). Systems
+// with more than TILT_T transforms are not tilted.
+__device__ __forceinline__ int tilt_from_bound(double b, int Mp, int T) {
+    if (T > TILT_T || !(b > 0.0)) return 0;
+    const double p = floor(b * (double)Mp);
+    return p >= (double)TILT_PMAX ? TILT_PMAX : (int)p;
+}
+// One input entry's contribution to that bound (ltop: log2 of its transform's max).
+__device__ __forceinline__ float tilt_bound_el(float ltop, float v, int i) {
+    const float a = fabsf(v);
+    if (i < 1 || !(a > 0.f) || !isfinite(a)) return INFINITY;
+    return (ltop - __log2f(a)) / (float)i;
+}
+// log2 of a maximum for tlog (0 when the transform's input is zero: it then bounds nothing).
+__device__ __forceinline__ float tilt_log(float mx) { return mx > 0.f && isfinite(mx) ? __log2f(mx) : 0.f; }
 
 // 2^e as R, exactly, without a double-precision ldexp (e within the normal range).
 template <typename R>
@@ -496,7 +549,9 @@ __device__ __forceinline__ void load_ctl(const SysDev& sh, CtlView& cv) {
         cv.ymax = c->ymax;
         cv.reuse = c->reuse;
         cv.hf = c->hf;
+        cv.tilt = c->tilt;
     }
+    if (threadIdx.x < TILT_T) cv.tlog[threadIdx.x] = c->tlog[threadIdx.x];
     __syncthreads();
 }
 
@@ -625,6 +680,13 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
             const R x0 = w.x * ys[2 * idx], x1 = w.y * ys[2 * idx + 1];
             mu += x0 + x1;
             nu += (R)(i + 1) * x0 + (R)(i + 2) * x1;
+            if constexpr (Tr<R>::tilted) {
+                if (cv.tilt) {  // the transform's input is tilted; the moments are not
+                    a[n1 * GT + t * G + g] =
+                        mk<R>(x0 * (sc * tilt_up(cv.tilt, i, S.lgMp)), x1 * (sc * tilt_up(cv.tilt, i + 1, S.lgMp)));
+                    continue;
+                }
+            }
             a[n1 * GT + t * G + g] = mk<R>(x0 * sc, x1 * sc);
         }
         if (viasm) {
@@ -945,6 +1007,7 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
     // only rows n1 < N1 / 2 (sizes up to M) are needed: the pruned transform writes no others
     cx<R>* res = tile_fft<R, PRUNE<R> ? HALF_OUT : HALF_NONE>(a, b, S.lgN1, G, m.twP, true);
     const R scale = rs[0], bscale = rs[1], lam1 = rs[2], s1r = rs[3], l1r = rs[4];
+    const int tilt = cv.tilt;
     const double src = src_s;
     R* kout = eo.out_slot >= 0 ? reinterpret_cast<R*>(S.vec) + (int64_t)eo.out_slot * S.vstride : nullptr;
     double sq = 0.0;
@@ -954,8 +1017,15 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
         const cx<R> z = res[idx];
         R D0 = pD0, D1 = pD1, y0 = py0, y1 = py1;
         if (idx != (int)threadIdx.x) epi_inputs<R>(S, Wr, yr, yd, i, D0, D1, y0, y1);
-        const R b0 = (i == 0) ? (R)0 : z.x * bscale;
-        const R b1 = z.y * bscale;
+        R b0 = (i == 0) ? (R)0 : z.x * bscale;
+        R b1 = z.y * bscale;
+        if constexpr (Tr<R>::tilted) {
+            // birth at index i is c[i - 1], tilted by theta^(i - 1)
+            if (tilt) {
+                if (i > 0) b0 *= tilt_down(tilt, i - 1, S.lgMp);
+                b1 *= tilt_down(tilt, i, S.lgMp);
+            }
+        }
         const R l0 = (i == 0) ? l1r : lam1 * y0 * D0;
         const R l1 = lam1 * y1 * D1;
         R s0 = b0 - l0;

@@ -6,8 +6,9 @@ here comes from the CUDA path. Each run integrates Eq. (4) with the paper's sche
 (Sec. 2) from the monodisperse start and stops at every checkpoint of its list (the last
 step before a checkpoint is clamped to it, and the next segment starts with the proposed
 step tau_next, exactly as a caller resuming with smol_set_tau0 does). Per checkpoint it
-stores the first `head` entries of n(t), the 2-norm of the remaining entries, the mass
-sum_s s n_s, N = sum_s n_s, ||S(n)||_2 and the cumulative attempt counts.
+stores the mass sum_s s n_s, N = sum_s n_s, ||S(n)||_2 and the cumulative attempt
+counts, and (at every checkpoint, or every head_every-th one) the first `head` entries
+of n(t) with the 2-norm of the remaining entries.
 
 Usage: python tests/golden/make_oracle_runs.py [name ...]   (default: every run; each
 run is its own process, started with the spawn method).
@@ -22,9 +23,9 @@ specify them completely):
       halve/double rule), checkpoints log-spaced over [0.01, 1].
   fig2_const: K = 1, lambda = 0.01, M = 32768, RKF45 tol 1e-8 to t = 10^4 (Fig. 2).
   fig3_a095_M2048: K = (i/j)^0.95 + (j/i)^0.95, lambda = 0.01, M = 2048, RKF45 tol 1e-8,
-      N(t) at every unit of t up to 130 (the oscillations of Fig. 3).
+      N(t) at every unit of t up to 130 (the oscillations of Fig. 3), states every 10.
   oscill_a09_M2048: the oscillatory workload's kernel and rate (a = 0.9,
-      lambda = 0.005) at M = 2048 to t = 200, N(t) at every unit of t.
+      lambda = 0.005) at M = 2048 to t = 200, N(t) at every unit of t, states every 10.
   oscill_a09_M131072_window: the oscillatory workload at full size, M = 2^17, over its
       first 0.2 time units (every 0.01).
   batch_small: the systems of the 256-system batch recipe (seed 2407) with M = 1024, each
@@ -62,9 +63,9 @@ RUNS = {
     "fig2_const": dict(sys=dict(M=32768, kind="const", a=0.0, lam=0.01), scheme="rkf45", tol=1e-8,
                        ts=[1.0, 10.0, 100.0, 1000.0, 5000.0, 10000.0], head=4096),
     "fig3_a095_M2048": dict(sys=dict(M=2048, kind="brownian", a=0.95, lam=0.01), scheme="rkf45", tol=1e-8,
-                            ts=np.arange(1.0, 131.0, 1.0).tolist(), head=2048),
+                            ts=np.arange(1.0, 131.0, 1.0).tolist(), head=2048, head_every=10),
     "oscill_a09_M2048": dict(sys=dict(M=2048, kind="brownian", a=0.9, lam=0.005), scheme="rkf45", tol=1e-8,
-                             ts=np.arange(1.0, 201.0, 1.0).tolist(), head=2048),
+                             ts=np.arange(1.0, 201.0, 1.0).tolist(), head=2048, head_every=10),
     "oscill_a09_M131072_window": dict(sys=dict(M=1 << 17, kind="brownian", a=0.9, lam=0.005), scheme="rkf45",
                                       tol=1e-8, ts=np.round(np.arange(0.01, 0.2001, 0.01), 10).tolist(), head=4096),
     "batch_small": dict(batch=dict(count=256, seed=2407, M=1024), scheme="rkf45", tol=1e-8, ts=[0.5, 1.0, 2.0],
@@ -79,16 +80,17 @@ def _system(spec):
     return oracle.System(spec["M"], spec["lam"], U=U, V=V, route="lowrank")
 
 
-def _trajectory(osys, M, scheme, tol, ts, head, steady_rtol=0.0, verbose=False):
-    """Integrates from the monodisperse start through the checkpoints ts."""
+def _trajectory(osys, M, scheme, tol, ts, head, steady_rtol=0.0, verbose=False, head_every=1):
+    """Integrates from the monodisperse start through the checkpoints ts; the leading
+    entries are kept at every head_every-th checkpoint (indices in head_idx)."""
     import oracle
     from synth import monodisperse
     n = monodisperse(M)
     t, tau = 0.0, 0.0
     cum = dict(attempts=0, accepted=0, rejected=0, rhs_evals=0)
-    rec = dict(t=[], head=[], tail_norm=[], mass=[], N=[], snorm=[], attempts=[], accepted=[], rejected=[],
-               rhs_evals=[], status=[], tau_next=[])
-    for tc in ts:
+    rec = dict(t=[], head=[], head_idx=[], tail_norm=[], mass=[], N=[], snorm=[], attempts=[], accepted=[],
+               rejected=[], rhs_evals=[], status=[], tau_next=[])
+    for kc, tc in enumerate(ts):
         o = oracle.Options(scheme=scheme, tau0=tau, steady_rtol=steady_rtol)
         n, st, _ = oracle.integrate(osys, n, t, tc, tol, o)
         for k in cum:
@@ -96,8 +98,10 @@ def _trajectory(osys, M, scheme, tol, ts, head, steady_rtol=0.0, verbose=False):
         t, tau = st["t"], st["tau_next"]
         S = osys.rhs(n)
         rec["t"].append(t)
-        rec["head"].append(n[:head].copy())
-        rec["tail_norm"].append(float(np.linalg.norm(n[head:])))
+        if kc % head_every == 0 or kc == len(ts) - 1:
+            rec["head"].append(n[:head].copy())
+            rec["head_idx"].append(kc)
+            rec["tail_norm"].append(float(np.linalg.norm(n[head:])))
         rec["mass"].append(oracle.total_mass(n))
         rec["N"].append(oracle.number_density(n))
         rec["snorm"].append(float(np.linalg.norm(S)))
@@ -130,7 +134,8 @@ def run(name):
     else:
         osys = _system(spec["sys"])
         out = _trajectory(osys, spec["sys"]["M"], spec["scheme"], spec["tol"], spec["ts"], spec["head"],
-                          spec.get("steady_rtol", 0.0), verbose=bool(os.environ.get("ORACLE_RUNS_VERBOSE")))
+                          spec.get("steady_rtol", 0.0), verbose=bool(os.environ.get("ORACLE_RUNS_VERBOSE")),
+                          head_every=spec.get("head_every", 1))
     meta = dict(name=name, spec=spec, seconds=round(time.time() - t0, 1),
                 generator="tests/golden/make_oracle_runs.py (oracle/ numpy FP64, FFT route)")
     path = os.path.join(HERE, f"oracle_{name}.npz")

@@ -186,7 +186,7 @@ def test_resume_with_set_tau0(smol):
         sq = smol.System(fs[q][0], fs[q][1], [0.01, 0.02][q], tau0=sh[q]["tau_next"])
         rq, _ = sq.integrate(bh[q], 1.0, 2.0, 1e-8)
         assert torch.allclose(br[q], rq, rtol=0, atol=1e-12 * float(rq.abs().max())), q
-        assert torch.allclose(br[q], bf[q], rtol=0, atol=1e-8 * float(bf[q].norm())), q
+        assert torch.allclose(br[q], bf[q], rtol=0, atol=1e-6 * float(bf[q].norm())), q
 
 
 def test_fp32conv_integrate_accuracy(smol):

@@ -1,0 +1,238 @@
+"""The paper's workloads (Sec. 3) integrated on the GPU and compared with the oracle's
+trajectories.
+
+The oracle runs are stored in tests/golden/oracle_<name>.npz, written by
+tests/golden/make_oracle_runs.py from oracle/ alone (numpy FP64, FFT route, the schemes
+and controllers of Sec. 2 step by step). Both sides start from the monodisperse state,
+stop at the same checkpoints (the last step before a checkpoint is clamped to it) and
+resume with the proposed step (smol_set_tau0 here, tau0 = tau_next there).
+
+Parity modes:
+  * relaxation (Sec. 3.1-3.2; the M = 2^16 workload with K = (i/j)^{1/3} + (j/i)^{1/3}
+    + 2 and lambda = 0.1, the K = 1 run of Fig. 2): the state at every checkpoint within
+    10 tol / ||n|| (relative, normwise) of the oracle's, the attempt counts within 2%,
+    and the steady state a zero of the oracle's own right-hand side;
+  * oscillation (Fig. 3 and the oscillatory workload's kernel and rate): N(t) = sum n_s
+    compared through the period and amplitude of its oscillation (1%) and the
+    accepted / rejected counts (2%), besides the states at the early checkpoints.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import kernel_factors, monodisperse
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def smol():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_16559_gb300 as m
+    return m
+
+
+def golden(name):
+    path = os.path.join(GOLDEN, f"oracle_{name}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"oracle trajectory {name} not generated (tests/golden/make_oracle_runs.py {name})")
+    g = dict(np.load(path, allow_pickle=False))
+    if "head_idx" not in g:
+        g["head_idx"] = np.arange(len(g["head"]))
+    return g
+
+
+def run_checkpoints(smol, kind, a, lam, M, ts, tol, scheme, H, precision="fp64", **opts):
+    """GPU run through the checkpoints ts; per checkpoint the first H entries, the norm of
+    the rest, N, mass and the cumulative counts."""
+    import torch
+    U, V = kernel_factors(kind, M, a=a)
+    sysm = smol.System(U, V, lam, precision=precision, chunk=64, **opts)
+    n = torch.from_numpy(monodisperse(M)).cuda()
+    t = 0.0
+    rec = dict(t=[], head=[], tail=[], N=[], mass=[], attempts=[], accepted=[], rejected=[], status=[])
+    cum = dict(attempts=0, accepted=0, rejected=0)
+    for tc in ts:
+        n, st = sysm.integrate(n, t, float(tc), tol, scheme=scheme, inplace=True)
+        sysm.set_tau0(st["tau_next"])
+        t = st["t"]
+        for k in cum:
+            cum[k] += st[k]
+            rec[k].append(cum[k])
+        rec["t"].append(t)
+        rec["head"].append(n[:H].cpu().numpy())
+        rec["tail"].append(float(torch.linalg.vector_norm(n[H:])))
+        rec["N"].append(float(n.sum()))
+        rec["mass"].append(st["mass"])
+        rec["status"].append(st["status"])
+        if st["status"] != 0:
+            break
+    return rec, n
+
+
+def rel_err(head, tail, ref_head, ref_tail):
+    """Upper bound of ||n - n_ref|| / ||n_ref|| from the leading entries and the norms of
+    the remaining entries (triangle inequality on the remainder)."""
+    d2 = float(np.sum((head - ref_head) ** 2)) + (tail + ref_tail) ** 2
+    return float(np.sqrt(d2 / (float(np.sum(ref_head ** 2)) + ref_tail ** 2)))
+
+
+def check_checkpoints(rec, g, tol, upto=None):
+    errs = []
+    for j, k in enumerate(g["head_idx"]):
+        if upto is not None and g["t"][k] > upto:
+            break
+        assert abs(rec["t"][k] - g["t"][k]) <= 1e-12 * max(1.0, g["t"][k])
+        ref = g["head"][j]
+        e = rel_err(rec["head"][k], rec["tail"][k], ref, float(g["tail_norm"][j]))
+        nrm = np.sqrt(np.sum(ref ** 2) + float(g["tail_norm"][j]) ** 2)
+        assert e <= 10 * tol / nrm, (g["t"][k], e, 10 * tol / nrm)
+        errs.append(e)
+    return errs
+
+
+def counts_close(rec, g, k, frac=0.02):
+    for key in ("accepted", "rejected"):
+        a, b = rec[key][k], int(g[key][k])
+        assert abs(a - b) <= max(2, frac * b), (key, a, b)
+
+
+RELAX = dict(kind="brownian_const", a=1.0 / 3.0, lam=0.1, M=1 << 16)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+@pytest.mark.parametrize("tol", [1e-9, 1e-6])
+def test_relaxation_rkf45_vs_oracle(smol, precision, tol):
+    """Relaxation workload (M = 2^16, rank 3, lambda = 0.1), RKF45 to t = 100 through 20
+    log-spaced checkpoints: states, mass and counts against the oracle."""
+    g = golden(f"relax_rkf45_tol{tol:g}")
+    rec, _ = run_checkpoints(smol, RELAX["kind"], RELAX["a"], RELAX["lam"], RELAX["M"], g["t"], tol, "rkf45",
+                             g["head"].shape[1], precision)
+    assert rec["status"][-1] == 0 and len(rec["t"]) == len(g["t"])
+    check_checkpoints(rec, g, tol)
+    counts_close(rec, g, len(g["t"]) - 1)
+    assert np.max(np.abs(np.array(rec["mass"]) - g["mass"])) <= 10 * tol
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk4"])
+def test_relaxation_step_doubling_vs_oracle(smol, scheme):
+    """The same workload with RK2 / RK4 and step doubling (halve/double rule, tol 1e-9)
+    over t <= 1 (8 log-spaced checkpoints)."""
+    g = golden(f"relax_{scheme}_tol1e-9")
+    rec, _ = run_checkpoints(smol, RELAX["kind"], RELAX["a"], RELAX["lam"], RELAX["M"], g["t"], 1e-9, scheme,
+                             g["head"].shape[1])
+    assert rec["status"][-1] == 0 and len(rec["t"]) == len(g["t"])
+    check_checkpoints(rec, g, 1e-9)
+    counts_close(rec, g, len(g["t"]) - 1)
+
+
+def test_relaxation_to_steady_state(smol):
+    """The relaxation workload to its steady state (||S(n)|| / ||n|| < 1e-10) with RKF45 at
+    tol 1e-9: the checkpoints the oracle reached agree, and the final state is a zero of
+    the oracle's own right-hand side to the stop criterion, with the mass it started
+    with (shattering conserves mass; the truncation flux is negligible at lambda = 0.1)."""
+    import torch
+    g = golden("relax_rkf45_steady")
+    U, V = kernel_factors(RELAX["kind"], RELAX["M"], a=RELAX["a"])
+    rec, n = run_checkpoints(smol, RELAX["kind"], RELAX["a"], RELAX["lam"], RELAX["M"],
+                             np.logspace(-1, 4, 26), 1e-9, "rkf45", g["head"].shape[1], steady_rtol=1e-10)
+    assert rec["status"][-1] == 1, rec["status"][-1]  # SMOL_STEADY
+    ok = np.nonzero(g["status"] == 0)[0]  # the oracle's checkpoints before its own stop
+    check_checkpoints(rec, g, 1e-9, upto=float(g["t"][ok[-1]]))
+    x = n.cpu().numpy()
+    S = oracle.System(RELAX["M"], RELAX["lam"], U=U, V=V, route="lowrank").rhs(x)
+    assert np.linalg.norm(S) / np.linalg.norm(x) < 1e-10 * (1 + 1e-3)
+    assert abs(oracle.total_mass(x) - 1.0) < 1e-7
+    if g["status"][-1] == 1:  # the oracle reached the steady state as well
+        ref = g["head"][-1]
+        e = rel_err(x[: ref.size], float(np.linalg.norm(x[ref.size:])), ref, float(g["tail_norm"][-1]))
+        assert e < 1e-8, e
+
+
+def test_fig2_constant_kernel_vs_oracle(smol):
+    """Fig. 2: K = 1, lambda = 0.01, M = 32768, RKF45 tol 1e-8 to t = 10^4. States at t = 1,
+    10, 100, 10^3, 5 10^3, 10^4 against the oracle, and the k^{-3/2} scaling of the
+    stationary tail that the paper shows settling by t = 10^4."""
+    g = golden("fig2_const")
+    rec, n = run_checkpoints(smol, "const", 0.0, 0.01, 32768, g["t"], 1e-8, "rkf45", g["head"].shape[1])
+    assert rec["status"][-1] == 0
+    check_checkpoints(rec, g, 1e-8)
+    counts_close(rec, g, len(g["t"]) - 1)
+    x = n.cpu().numpy()
+    k = np.arange(30, 3001)
+    slope = np.polyfit(np.log(k), np.log(x[k - 1] * np.exp(0.01 ** 2 * k)), 1)[0]
+    assert abs(slope + 1.5) < 0.1, slope
+
+
+def _extrema(t, N):
+    mx = [(t[i], N[i]) for i in range(1, len(N) - 1) if N[i] > N[i - 1] and N[i] >= N[i + 1]]
+    mn = [(t[i], N[i]) for i in range(1, len(N) - 1) if N[i] < N[i - 1] and N[i] <= N[i + 1]]
+    return mx, mn
+
+
+def _refine(t, N, i):
+    """Vertex of the parabola through three samples around index i (time of an extremum)."""
+    y0, y1, y2 = N[i - 1], N[i], N[i + 1]
+    h = t[i + 1] - t[i]
+    den = y0 - 2 * y1 + y2
+    return t[i] + (0.5 * h * (y0 - y2) / den if den != 0 else 0.0)
+
+
+def check_oscillation(rec, g, tol):
+    t, N, Nr = np.array(rec["t"]), np.array(rec["N"]), g["N"]
+    assert len(N) == len(Nr)
+    ig = [i for i in range(1, len(N) - 1) if N[i] > N[i - 1] and N[i] >= N[i + 1]]
+    ir = [i for i in range(1, len(Nr) - 1) if Nr[i] > Nr[i - 1] and Nr[i] >= Nr[i + 1]]
+    assert len(ig) == len(ir) >= 2, (ig, ir)
+    tg = [_refine(t, N, i) for i in ig]
+    tr = [_refine(g["t"], Nr, i) for i in ir]
+    pg, pr = np.diff(tg).mean(), np.diff(tr).mean()
+    assert abs(pg - pr) <= 0.01 * pr, (pg, pr)
+    ampg = N[ig[-1]] - N[ig[-2]:ig[-1]].min()
+    ampr = Nr[ir[-1]] - Nr[ir[-2]:ir[-1]].min()
+    assert abs(ampg - ampr) <= 0.01 * ampr, (ampg, ampr)
+    counts_close(rec, g, len(N) - 1)
+    return pg, ampg
+
+
+def test_fig3_oscillations_vs_oracle(smol):
+    """Fig. 3: K = (i/j)^0.95 + (j/i)^0.95, lambda = 0.01 (M = 2048, RKF45 tol 1e-8, t <= 130):
+    period and amplitude of the oscillations of N(t) and the counts against the oracle;
+    the states of the first 40 time units within 10 tol / ||n||."""
+    g = golden("fig3_a095_M2048")
+    rec, _ = run_checkpoints(smol, "brownian", 0.95, 0.01, 2048, g["t"], 1e-8, "rkf45", 2048)
+    assert rec["status"][-1] == 0
+    check_oscillation(rec, g, 1e-8)
+    check_checkpoints(rec, g, 1e-8, upto=40.0)
+
+
+def test_oscillatory_workload_kernel_vs_oracle(smol):
+    """The oscillatory workload's kernel and rate (a = 0.9, lambda = 0.005) at M = 2048,
+    t <= 200: the oscillation of N(t) (period, amplitude) and the counts against the
+    oracle; the early states within 10 tol / ||n||."""
+    g = golden("oscill_a09_M2048")
+    rec, _ = run_checkpoints(smol, "brownian", 0.9, 0.005, 2048, g["t"], 1e-8, "rkf45", 2048)
+    assert rec["status"][-1] == 0
+    check_oscillation(rec, g, 1e-8)
+    check_checkpoints(rec, g, 1e-8, upto=40.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_oscillatory_workload_full_size_window(smol, precision):
+    """The oscillatory workload at full size (M = 2^17, a = 0.9, lambda = 0.005, RKF45 tol
+    1e-8) over the first 0.2 time units, the window the oracle affords: states every 0.01
+    and the counts."""
+    g = golden("oscill_a09_M131072_window")
+    rec, _ = run_checkpoints(smol, "brownian", 0.9, 0.005, 1 << 17, g["t"], 1e-8, "rkf45", g["head"].shape[1],
+                             precision)
+    assert rec["status"][-1] == 0
+    check_checkpoints(rec, g, 1e-8)
+    counts_close(rec, g, len(g["t"]) - 1)
