@@ -47,7 +47,7 @@ LAUNCHES_FUSED = 13         # forward columns, 6 x row kernel, 5 x fused inverse
 LAUNCHES_UNFUSED = 19       # 6 x (forward columns, rows, inverse columns) + combination / control
 FLAG_NO_FUSE = 32           # smol_opts.flags bit (SMOL_FLAG_NO_FUSE)
 L2_FLUSH_BYTES = 256 << 20
-CTL_BYTES = 264             # the device control block of one system (smol::Ctl)
+CTL_BYTES = 328             # the device control block of one system (smol::Ctl)
 
 # Peaks. HBM: the copy bandwidth of MEASURED_PEAKS.json (written by the pool's driver;
 # read at run time), else the fallback figure. FP64 and FP32 arithmetic: measured live

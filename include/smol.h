@@ -56,7 +56,7 @@ extern "C" {
 /* Status codes. */
 #define SMOL_OK                0   /* success; integrate reached t1 */
 #define SMOL_STEADY            1   /* integrate stopped: ||S(n)||_2 / ||n||_2 < steady_rtol */
-#define SMOL_EINVAL           -1   /* bad argument (M < 1, R outside 1..8, NULL, t1 < t0, tol <= 0, ...) */
+#define SMOL_EINVAL           -1   /* bad argument (M < 1, R outside 1..SMOL_MAX_R, NULL, t1 < t0, tol <= 0, ...) */
 #define SMOL_ECUDA            -2   /* a CUDA runtime call failed */
 #define SMOL_ENONFINITE       -3   /* NaN or Inf in the error estimate or the candidate state */
 #define SMOL_ESTEP_UNDERFLOW  -4   /* step fell below tau_min_rel * max(1, |t|) */
@@ -64,6 +64,9 @@ extern "C" {
 #define SMOL_ETIMEOUT         -6   /* a bounded device wait gave up */
 #define SMOL_ENOSPACE         -7   /* workspace smaller than smol_workspace_bytes() */
 #define SMOL_EUNSUPPORTED     -8   /* shape beyond what the kernels support (see smol_max_m) */
+
+/* Largest rank R of the kernel factors. */
+#define SMOL_MAX_R 16
 
 /* Schemes of Sec. 2. */
 #define SMOL_RK2    0
@@ -148,8 +151,15 @@ typedef struct smol_stats {
 /* Fills *opts with the defaults listed above. Never fails for a non-NULL pointer. */
 void smol_default_opts(smol_opts* opts);
 
-/* Largest M the kernels accept for rank R and precision, or 0 if R is unsupported. */
+/* Largest M the kernels accept for rank R and precision when no transforms are shared
+ * (T = 2R distinct forward transforms), or 0 if R is unsupported. */
 int64_t smol_max_m(int32_t R, int32_t precision);
+
+/* Largest M for T distinct forward transforms (1 <= T <= 2 SMOL_MAX_R). Columns of U and
+ * rows of V that are equal up to a factor share a transform (a symmetric kernel given as
+ * V = diag(s) U^T, as smol_lowrank_kernel returns it, has T = R), so smol_init_system
+ * accepts up to this M for the factors' actual T. Returns 0 for an unsupported T. */
+int64_t smol_max_m_transforms(int32_t T, int32_t precision);
 
 /* Bytes of device workspace a system of size M, rank R needs under opts (NULL =
  * defaults). The workspace must stay allocated, untouched by the caller and
@@ -350,7 +360,7 @@ void smol_batch_destroy(smol_batch* batch);
  *   M <= SMOL_STATIC_MAX_M, 1 <= R <= SMOL_STATIC_MAX_R, lambda >= 0.
  *   d_U: device, M x R row-major; d_V: device, R x M row-major; d_n, d_out: device,
  *   M doubles each, 16-byte aligned, not overlapping. stream: cudaStream_t or NULL.
- * Its scratch memory is a fixed device array of 15,320,832 bytes inside the library,
+ * Its scratch memory is a fixed device array of 15,321,344 bytes inside the library,
  * which every GPU that loads the library holds until exit. The first call on a device
  * looks up that array's device address and sets kernel attributes (once per device);
  * make that first call before any stream capture. All calls on a device share the
@@ -362,6 +372,33 @@ void smol_batch_destroy(smol_batch* batch);
 #define SMOL_STATIC_MAX_R 3
 int smol_rhs_static(int64_t M, int32_t R, const double* d_U, const double* d_V, double lambda,
                     const double* d_n, double* d_out, void* stream);
+
+/* Collision kernels of Sec. 3.1 for smol_lowrank_kernel (sizes i, j >= 1):
+ *   SMOL_KERNEL_CONST:          K_ij = 1
+ *   SMOL_KERNEL_BROWNIAN:       K_ij = (i/j)^a + (j/i)^a + c, params = {a, c}
+ *   SMOL_KERNEL_FREE_MOLECULAR: K_ij = (i^{1/3} + j^{1/3})^2 sqrt(1/i + 1/j)
+ * The first two have exact ranks 1 and <= 3; the free-molecular kernel has no exact low
+ * rank and is approximated. */
+#define SMOL_KERNEL_CONST          0
+#define SMOL_KERNEL_BROWNIAN       1
+#define SMOL_KERNEL_FREE_MOLECULAR 2
+
+/* Low-rank factors K ~= U V of a symmetric kernel on sizes 1..M (host code, no GPU), so
+ * that the O(M R log M) right-hand side of Sec. 1 applies to a kernel without an exact
+ * low rank; the paper takes such factors from a cross approximation (Sec. 1 and its
+ * reference on the fast evaluation). Symmetric adaptive cross approximation of
+ * D^-1 K D^-1, D = diag(sqrt |K_ii|), with diagonal pivots (Bunch-Kaufman 2 x 2 pivots
+ * where a diagonal pivot is too small), until the residual is below tol relative to the
+ * scaled matrix or max_rank terms are taken.
+ *   params: kernel parameters (SMOL_KERNEL_BROWNIAN: {a, c}; may be NULL otherwise).
+ *   h_U: host, >= M * max_rank doubles: receives U as M x R row-major (R = *rank);
+ *   h_V: host, >= max_rank * M doubles: receives V as R x M row-major, V = diag(s) U^T
+ *        with signs s = +-1 (so the factors share their R transforms: T = R).
+ *   *err_est (may be NULL): max |K^ - K| / |K| over the first and last 8 rows and every
+ *        ceil(M/64)-th row, all columns (exact kernel entries).
+ * Returns SMOL_OK or SMOL_EINVAL (bad kind, M < 1, tol <= 0, max_rank < 1, NULL). */
+int smol_lowrank_kernel(int32_t kind, const double* params, int64_t M, double tol, int32_t max_rank,
+                        double* h_U, double* h_V, int32_t* rank, double* err_est);
 
 /* Releases the system (not the workspace). Safe on NULL. */
 void smol_destroy(smol_system* sys);

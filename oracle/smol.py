@@ -48,7 +48,8 @@ EINVAL, ENONFINITE, ESTEP_UNDERFLOW, EMAXATTEMPTS = -1, -3, -4, -5
 # Kernels K_{i,j} (Sec. 1 example; Sec. 3.1 list; Sec. 3.2 non-local kernel)
 # ---------------------------------------------------------------------------
 def kernel_closed_form(kind: str, M: int, a: float = 0.0, c: float = 2.0) -> np.ndarray:
-    """K_{i,j} for i, j = 1..M evaluated from its closed form."""
+    """K_{i,j} for i, j = 1..M evaluated from its closed form (the kernels listed in
+    Sec. 3.1: constant, generalized Brownian (+ c), free-molecular)."""
     i = np.arange(1, M + 1, dtype=np.float64)[:, None]
     j = np.arange(1, M + 1, dtype=np.float64)[None, :]
     if kind == "const":
@@ -57,6 +58,9 @@ def kernel_closed_form(kind: str, M: int, a: float = 0.0, c: float = 2.0) -> np.
         return (i / j) ** a + (j / i) ** a
     if kind == "brownian_const":
         return (i / j) ** a + (j / i) ** a + c
+    if kind == "free_molecular":
+        # Sec. 3.1: (i^{1/3} + j^{1/3})^2 sqrt(1/i + 1/j); no exact low rank
+        return (np.cbrt(i) + np.cbrt(j)) ** 2 * np.sqrt(1.0 / i + 1.0 / j)
     raise ValueError(kind)
 
 

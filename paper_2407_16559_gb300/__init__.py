@@ -94,6 +94,9 @@ SIGNATURES = {
     "smol_batch_set_sources": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
     "smol_set_tau0": (ctypes.c_int, [_P, _D]),
     "smol_fma_rate": (ctypes.c_int, [_I32, _I64, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "smol_max_m_transforms": (_I64, [_I32, _I32]),
+    "smol_lowrank_kernel": (ctypes.c_int, [_I32, _P, _I64, _D, _I32, _P, _P, ctypes.POINTER(_I32),
+                                           ctypes.POINTER(_D)]),
     "smol_batch_set_tau0": (ctypes.c_int, [_P, _P]),
 }
 
@@ -149,6 +152,29 @@ def rhs_static(U, V, lam: float, n, out=None, stream=None):
     _check(_lib.smol_rhs_static(M, R, U.data_ptr(), V.data_ptr(), float(lam), n.data_ptr(), out.data_ptr(),
                                 st.cuda_stream), "smol_rhs_static")
     return out
+
+
+KERNELS = {"const": 0, "brownian": 1, "free_molecular": 2}
+MAX_R = 16
+
+
+def max_m_transforms(T: int, precision: str = "fp64") -> int:
+    """Largest M for T distinct forward transforms (smol_max_m_transforms)."""
+    return int(_lib.smol_max_m_transforms(int(T), PRECISIONS[precision]))
+
+
+def lowrank_kernel(kind: str, M: int, tol: float = 1e-10, max_rank: int = MAX_R, a: float = 0.0, c: float = 0.0):
+    """smol_lowrank_kernel: symmetric cross approximation K ~= U V of a kernel of Sec. 3.1
+    on sizes 1..M (host code). Returns (U (M, R), V (R, M), sampled max relative entry
+    error)."""
+    U = np.zeros(M * max_rank)
+    V = np.zeros(max_rank * M)
+    par = np.array([a, c], dtype=np.float64)
+    r, e = ctypes.c_int32(), ctypes.c_double()
+    _check(_lib.smol_lowrank_kernel(KERNELS[kind], par.ctypes.data, int(M), float(tol), int(max_rank), U.ctypes.data,
+                                    V.ctypes.data, ctypes.byref(r), ctypes.byref(e)), "smol_lowrank_kernel")
+    R = r.value
+    return U[: M * R].reshape(M, R).copy(), V[: R * M].reshape(R, M).copy(), e.value
 
 
 def fma_rate(precision: str = "fp64", iters: int = 20000, stream=None):

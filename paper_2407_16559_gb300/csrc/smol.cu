@@ -206,14 +206,23 @@ bool proportional(const double* x, const double* w, int M, double* c) {
     return true;
 }
 
-int64_t max_m_for(int32_t R, int32_t precision) {
-    if (R < 1 || R > MAXR) return 0;
+static_assert(MAXR == SMOL_MAX_R, "rank limit of the C interface and the kernels");
+
+// Largest M whose rule shape fits T distinct transforms in shared memory.
+int64_t max_m_transforms(int32_t T, int32_t precision) {
+    if (T < 1 || T > MAXT) return 0;
     int64_t best = 0;
     for (int lg = 2; lg <= 22; ++lg) {
         Shape s = make_shape((int64_t)1 << lg, precision);
-        if (smem_cols(s, 2 * R) <= SMEM_LIMIT && smem_rows(s, 2 * R) <= SMEM_LIMIT) best = (int64_t)1 << lg;
+        if (smem_cols(s, T) <= SMEM_LIMIT && smem_rows(s, T) <= SMEM_LIMIT) best = (int64_t)1 << lg;
     }
     return best;
+}
+
+// Largest M for rank R with no shared transforms (T = 2R).
+int64_t max_m_for(int32_t R, int32_t precision) {
+    if (R < 1 || R > MAXR) return 0;
+    return max_m_transforms(2 * R, precision);
 }
 
 // A batch counts as wide when its systems together hold more than 2^20 sizes.
@@ -225,7 +234,9 @@ bool is_wide(int count, const int64_t* M) {
 
 size_t batch_bytes(int count, const int64_t* M, int R, const smol_opts& o) {
     if (count < 1 || count > MAX_BATCH || R < 1 || R > MAXR) return 0;
-    const int64_t mm = max_m_for(R, o.precision);
+    // the factors' actual T (<= 2R) is known only at init, which refuses shapes that do
+    // not fit; here any M that fits with one transform
+    const int64_t mm = max_m_transforms(1, o.precision);
     std::vector<Shape> sh;
     size_t tot = 0;
     const bool wide = is_wide(count, M);
@@ -1241,6 +1252,8 @@ void smol_default_opts(smol_opts* opts) {
 
 int64_t smol_max_m(int32_t R, int32_t precision) { return max_m_for(R, precision); }
 
+int64_t smol_max_m_transforms(int32_t T, int32_t precision) { return max_m_transforms(T, precision); }
+
 size_t smol_workspace_bytes(int64_t M, int32_t R, const smol_opts* opts) {
     smol_opts o;
     if (opts) o = *opts;
@@ -1257,7 +1270,7 @@ int smol_init_system(smol_system** out, int64_t M, int32_t R, const double* h_U,
     else default_opts(&o);
     int rc = check_opts(o);
     if (rc != SMOL_OK) return rc;
-    if (M > max_m_for(R, o.precision)) return SMOL_EUNSUPPORTED;
+    if (M > max_m_transforms(1, o.precision)) return SMOL_EUNSUPPORTED;
     if (((uintptr_t)d_workspace & 255) != 0) return SMOL_EINVAL;
     if (workspace_bytes < batch_bytes(1, &M, R, o)) return SMOL_ENOSPACE;
     smol_system* S = new smol_system();
@@ -1381,7 +1394,7 @@ int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double
     smol_opts base = *opts;
     int rc = check_opts(base);
     if (rc != SMOL_OK) return rc;
-    if (M > max_m_for(R, base.precision)) return SMOL_EUNSUPPORTED;
+    if (M > max_m_transforms(1, base.precision)) return SMOL_EUNSUPPORTED;
     base.max_attempts = (int64_t)1 << 62;
     base.fixed_tau = 0.0;
     double* d_work = nullptr;
@@ -1454,7 +1467,7 @@ int smol_batch_init(smol_batch** out, int32_t count, const int64_t* M, int32_t R
     else default_opts(&o);
     int rc = check_opts(o);
     if (rc != SMOL_OK) return rc;
-    const int64_t mm = max_m_for(R, o.precision);
+    const int64_t mm = max_m_transforms(1, o.precision);  // the exact check (actual T) is in init
     for (int q = 0; q < count; ++q) {
         if (M[q] < 1) return SMOL_EINVAL;
         if (M[q] > mm) return SMOL_EUNSUPPORTED;

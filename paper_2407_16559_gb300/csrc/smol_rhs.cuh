@@ -43,7 +43,7 @@
 
 namespace smol {
 
-constexpr int MAXR = 8;         // largest rank R
+constexpr int MAXR = 16;        // largest rank R (SMOL_MAX_R)
 constexpr int MAXT = 2 * MAXR;  // largest number of distinct transforms
 constexpr int MAXV = 10;        // terms of a stage-input linear combination
 constexpr int NVEC = 12;        // stage / work vectors per system

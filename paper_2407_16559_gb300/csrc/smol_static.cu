@@ -50,7 +50,7 @@ constexpr size_t SCRATCH_BYTES = OFF_RSC + al((size_t)(MAXT + 2) * 8 + 2 * MAXT 
 
 // The scratch memory of smol_rhs_static.
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
-static_assert(SCRATCH_BYTES == 15320832, "the scratch size documented in smol.h");
+static_assert(SCRATCH_BYTES == 15321344, "the scratch size documented in smol.h");
 
 constexpr int MAX_DEVICES = 64;
 // Per device: the device address of g_scratch, published by the release store of

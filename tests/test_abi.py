@@ -41,11 +41,12 @@ def test_host_side_queries(smol):
     o = smol.default_opts()
     assert o.precision == 0 and o.euler_a == 0.1 and o.fac_max == 4.0 and o.chunk == 32
     assert smol.max_m(2) >= 2 ** 17 and smol.max_m(3, "fp32conv") >= 2 ** 17
-    assert smol.max_m(0) == 0 and smol.max_m(9) == 0
+    assert smol.max_m(0) == 0 and smol.max_m(smol.MAX_R + 1) == 0 and smol.max_m(smol.MAX_R) > 0
+    assert smol.max_m_transforms(2) >= smol.max_m(2) and smol.max_m_transforms(2 * smol.MAX_R + 1) == 0
     lib = smol._lib
     assert lib.smol_workspace_bytes(2 ** 17, 2, None) > 0
     assert lib.smol_workspace_bytes(0, 2, None) == 0
-    assert lib.smol_workspace_bytes(16, 9, None) == 0
+    assert lib.smol_workspace_bytes(16, smol.MAX_R + 1, None) == 0
     assert smol.strerror(-3).startswith("non-finite")
 
 

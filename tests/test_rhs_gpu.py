@@ -245,15 +245,23 @@ def test_rhs_df64_full_size_sampled_direct_entries(smol):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
 def test_rhs_at_maximum_size(smol, precision):
-    """The largest M the kernels take for R = 2 (smol_max_m; the row tiles' shared
-    memory sets it): parity with the oracle's FFT route there, and the next size is
-    refused with SMOL_EUNSUPPORTED."""
-    M = smol.max_m(2, precision)
+    """The largest M the kernels take for the Brownian kernel, whose rank-2 factors share
+    their transforms (T = 2; smol_max_m_transforms: the tiles' shared memory sets it):
+    parity with the oracle's FFT route there, and the next size is refused with
+    SMOL_EUNSUPPORTED. Without shared transforms (random factors, T = 2R = 4) the limit
+    is smol_max_m(2)."""
+    M = smol.max_m_transforms(2, precision)
     U, V = kernel_factors("brownian", M, a=0.7)
+    assert smol.System(U, V, 0.002, precision=precision).num_transforms == 2
     check_rhs(smol, sample_state(M, 0.002, seed=5), U, V, 0.002, precision=precision, route="lowrank")
     U1, V1 = kernel_factors("brownian", M + 1, a=0.7)
     with pytest.raises(smol.SmolError) as e:
         smol.System(U1, V1, 0.002, precision=precision)
+    assert e.value.code == smol.EUNSUPPORTED
+    M4 = smol.max_m(2, precision)
+    U4, V4 = random_factors(M4 + 1, 2, seed=3)
+    with pytest.raises(smol.SmolError) as e:
+        smol.System(U4, V4, 0.002, precision=precision)
     assert e.value.code == smol.EUNSUPPORTED
 
 
