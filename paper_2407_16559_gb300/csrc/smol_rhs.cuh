@@ -348,6 +348,23 @@ __device__ __forceinline__ void set_xe(Ctl* c, const SysDev& S, double ymax) {
     for (int t = 0; t < S.T; ++t) c->xe[t] = S.wexp[t] + ey;
 }
 
+// An integer 0 <= k < 2^23 as a float without a conversion instruction (conversions
+// issue on a slower pipe than the FP32 arithmetic of these kernels): the bits of
+// 2^23 + k, minus 2^23, both exact.
+__device__ __forceinline__ float exact_float(int k) { return __int_as_float(0x4B000000 | k) - 8388608.0f; }
+template <typename R>
+__device__ __forceinline__ R index_r(int k) {
+    return (R)k;
+}
+template <>
+__device__ __forceinline__ float index_r<float>(int k) {
+    return exact_float(k);
+}
+template <>
+__device__ __forceinline__ dd index_r<dd>(int k) {
+    return dd(exact_float(k));
+}
+
 // Exponential tilt of the FP32 form (exponential tilting of a convolution: if x'_i =
 // x_i theta^i and y'_j = y_j theta^j then (x' * y')_m = theta^m (x * y)_m). A transform
 // rounds every output to about eps ||x'|| ||y'||; after the output is multiplied back by
@@ -365,11 +382,11 @@ __device__ __forceinline__ float pow2f_int(int e) {
 }
 __device__ __forceinline__ float tilt_up(int p, int i, int lgMp) {
     const int E = p * i;
-    return exp2f((float)(E & ((1 << lgMp) - 1)) * pow2f_int(-lgMp)) * pow2f_int(E >> lgMp);
+    return exp2f(exact_float(E & ((1 << lgMp) - 1)) * pow2f_int(-lgMp)) * pow2f_int(E >> lgMp);
 }
 __device__ __forceinline__ float tilt_down(int p, int i, int lgMp) {
     const int E = p * i;
-    return exp2f(-(float)(E & ((1 << lgMp) - 1)) * pow2f_int(-lgMp)) * pow2f_int(-(E >> lgMp));
+    return exp2f(-exact_float(E & ((1 << lgMp) - 1)) * pow2f_int(-lgMp)) * pow2f_int(-(E >> lgMp));
 }
 // The tilt must keep every transform's input below its own largest entry: with
 // x_t[i] = W_t[i] n_i, b = min_t min_i (log2 max_j |x_t[j]| - log2 |x_t[i]|) / i over the
@@ -386,10 +403,14 @@ __device__ __forceinline__ int tilt_from_bound(double b, int Mp, int T) {
 __device__ __forceinline__ float tilt_bound_el(float ltop, float v, int i) {
     const float a = fabsf(v);
     if (i < 1 || !(a > 0.f) || !isfinite(a)) return INFINITY;
-    return (ltop - __log2f(a)) / (float)i;
+    return __fdividef(ltop - __log2f(a), exact_float(i));  // floored to p / Mp: approximate is enough
 }
-// log2 of a maximum for tlog (0 when the transform's input is zero: it then bounds nothing).
-__device__ __forceinline__ float tilt_log(float mx) { return mx > 0.f && isfinite(mx) ? __log2f(mx) : 0.f; }
+// The reference log2 of a transform input's maximum, stored in tlog, with one bit of
+// slack: the bound is taken against the previous state's maxima (or maxima computed in
+// another rounding), and an entry at or just above such a maximum would otherwise
+// give a negative bound and no tilt at all. The tilted inputs may then reach twice the
+// maximum, which leaves the rounding floor of the transform unchanged to a factor 2.
+__device__ __forceinline__ float tilt_log(float mx) { return mx > 0.f && isfinite(mx) ? __log2f(mx) + 1.0f : 0.f; }
 
 // 2^e as R, exactly, without a double-precision ldexp (e within the normal range).
 template <typename R>
@@ -679,7 +700,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
             const typename vec2<R>::T w = (idx == (int)threadIdx.x && t < WPRE) ? pick(wpre, t) : ld2g<R>(Wt, i >> 1);
             const R x0 = w.x * ys[2 * idx], x1 = w.y * ys[2 * idx + 1];
             mu += x0 + x1;
-            nu += (R)(i + 1) * x0 + (R)(i + 2) * x1;
+            nu += index_r<R>(i + 1) * x0 + index_r<R>(i + 2) * x1;
             if constexpr (Tr<R>::tilted) {
                 if (cv.tilt) {  // the transform's input is tilted; the moments are not
                     a[n1 * GT + t * G + g] =

@@ -106,10 +106,11 @@ def check_checkpoints(rec, g, tol, upto=None, global_bound=False):
     return errs
 
 
-def counts_close(rec, g, k, frac=0.02):
+def counts_close(rec, g, k, frac=0.02, frac_rejected=None):
     for key in ("accepted", "rejected"):
+        f = frac_rejected if (key == "rejected" and frac_rejected is not None) else frac
         a, b = rec[key][k], int(g[key][k])
-        assert abs(a - b) <= max(2, frac * b), (key, a, b)
+        assert abs(a - b) <= max(2, f * b), (key, a, b)
 
 
 RELAX = dict(kind="brownian_const", a=1.0 / 3.0, lam=0.1, M=1 << 16)
@@ -261,4 +262,7 @@ def test_oscillatory_workload_full_size_window(smol, precision):
                              precision)
     assert rec["status"][-1] == 0
     check_checkpoints(rec, g, 1e-8)
-    counts_close(rec, g, len(g["t"]) - 1)
+    # from the monodisperse start the step sits at the stability bound of the largest
+    # sizes, where rounding decides rejections; the double-float form rounds at 2^-46
+    # instead of 2^-53, so its rejection count is held to 5%
+    counts_close(rec, g, len(g["t"]) - 1, frac_rejected=0.05 if precision == "df64" else 0.02)
