@@ -110,6 +110,13 @@ extern "C" {
    in one kernel with the next evaluation's forward column pass, or with the attempt's
    final combination). */
 #define SMOL_FLAG_NO_FUSE         32
+/* Single-system RKF45 integrations: each chunk of attempts is one cooperative launch of
+   a persistent kernel whose CTAs run the phases of the attempts back to back, separated
+   by grid-wide barriers, instead of a graph of 13 launches per attempt. The results are
+   those of the graph path. Needs every CTA of the grid resident at once; otherwise (and
+   for other schemes, fixed steps or batches) the graph path runs. A barrier wait that
+   gives up (about 2 s) ends the integration with SMOL_ETIMEOUT. */
+#define SMOL_FLAG_PERSISTENT      64
 
 typedef struct smol_system smol_system;   /* opaque, created by smol_init_system */
 
@@ -269,7 +276,8 @@ int smol_set_sources(smol_system* sys, int32_t count, const int64_t* sizes, cons
  *   - log2 N1 of the four-step split Mp = N1 N2: the rule's value and one either side;
  *   - columns per CTA of the column kernels: the rule's value, twice and four times it;
  *   - launch mode: programmatic dependent launch for every kernel, for none, or for
- *     all but the forward column kernel; fused column passes (default) or not.
+ *     all but the forward column kernel; fused column passes (default) or not; for
+ *     RKF45 also the persistent attempt kernel (SMOL_FLAG_PERSISTENT).
  * Candidates whose shared memory does not fit are skipped. *opts is read as the base
  * options and receives the fastest schedule in fft_lgn1, fft_g and flags (its other
  * fields are unchanged); *us_per_attempt (may be NULL) that schedule's microseconds

@@ -16,7 +16,7 @@
 
 #include "../../include/smol.h"
 #include "smol_attr.h"
-#include "smol_int.cuh"
+#include "smol_persist.cuh"
 
 using namespace smol;
 
@@ -140,7 +140,7 @@ Layout make_layout(const Shape& s, int R, int log_cap) {
 
 // Header of a batch workspace: control blocks, descriptors and block maps.
 struct Header {
-    size_t ctl, rctl, sys, sysr, mapC, mapB, mapF, total;
+    size_t ctl, rctl, sys, sysr, mapC, mapB, mapF, bar, total;
     int nC, nB, nF;  // blocks of the column / row / finish launches
 };
 
@@ -166,6 +166,7 @@ Header make_header(const std::vector<Shape>& sh) {
     H.mapC = take((size_t)H.nC * sizeof(int2));
     H.mapB = take((size_t)H.nB * sizeof(int2));
     H.mapF = take((size_t)H.nF * sizeof(int2));
+    H.bar = take(2 * sizeof(unsigned));  // grid barrier of the persistent attempt kernel
     H.total = o;
     return H;
 }
@@ -307,6 +308,13 @@ struct Engine {
     int64_t run_attempts = 1;
     std::vector<double*> run_dn;
     std::vector<double> tau0;  // per system: first step of the next integration (<= 0: opts.tau0)
+    // persistent attempt kernel (single system, RKF45, SMOL_FLAG_PERSISTENT)
+    unsigned* d_bar = nullptr;
+    bool persist_run = false;
+    const void* pkern = nullptr;
+    int pgrid = 0, pblock = 0;
+    size_t psmem = 0;
+    PersistPlan plan{};
 };
 
 struct smol_system : Engine {};
@@ -338,8 +346,9 @@ int set_smem_attrs(const Engine* E) {
         raise_smem(k_rows<R>, sb) != cudaSuccess)
         return SMOL_ECUDA;
     if (!(carve(k_fwd_cols<R>) && carve(k_rows<R>) && carve(k_inv_cols<R>) && carve(k_inv_fwd<R>) &&
-          carve(k_inv_finish<R>) && carve(k_finish<R>) && carve(k_lincomb<R>)))
+          carve(k_inv_finish<R>) && carve(k_finish<R>) && carve(k_lincomb<R>) && carve(k_persist<R>)))
         return SMOL_ECUDA;
+    if (E->count == 1 && raise_smem(k_persist<R>, std::max(sc, sb)) != cudaSuccess) return SMOL_ECUDA;
     return SMOL_OK;
 }
 
@@ -512,6 +521,51 @@ EpiOut epi_k(int slot, double hfac, int sq) {
     return e;
 }
 
+// The RKF45 attempt of Sec. 2: stage inputs n + sum_j a_ij k_j (k_j = h S), the fourth-
+// order candidate and the difference of the two weight rows of the tableau (the error).
+void rkf45_stages(StageIn in[6], StageIn& cand, StageIn& del) {
+    const int N = SLOT_CUR;
+    in[0] = stage({{N, 1.0}});
+    in[1] = stage({{N, 1.0}, {0, 0.25}});
+    in[2] = stage({{N, 1.0}, {0, 3.0 / 32.0}, {1, 9.0 / 32.0}});
+    in[3] = stage({{N, 1.0}, {0, 1932.0 / 2197.0}, {1, -7200.0 / 2197.0}, {2, 7296.0 / 2197.0}});
+    in[4] = stage({{N, 1.0}, {0, 439.0 / 216.0}, {1, -8.0}, {2, 3680.0 / 513.0}, {3, -845.0 / 4104.0}});
+    in[5] = stage({{N, 1.0}, {0, -8.0 / 27.0}, {1, 2.0}, {2, -3544.0 / 2565.0}, {3, 1859.0 / 4104.0}, {4, -11.0 / 40.0}});
+    cand = stage({{N, 1.0}, {0, 25.0 / 216.0}, {2, 1408.0 / 2565.0}, {3, 2197.0 / 4104.0}, {4, -1.0 / 5.0}});
+    del = stage({{0, 16.0 / 135.0 - 25.0 / 216.0},
+                 {2, 6656.0 / 12825.0 - 1408.0 / 2565.0},
+                 {3, 28561.0 / 56430.0 - 2197.0 / 4104.0},
+                 {4, -9.0 / 50.0 + 1.0 / 5.0},
+                 {5, 2.0 / 55.0}});
+}
+
+// A stage input as the kernels of form R take it: the first evaluation of an attempt is
+// marked (a retry reuses it), and the FP32 / double-float forms read the state's shadow.
+template <typename R>
+StageIn stage_for(StageIn in, bool first) {
+    in.first = first ? 1 : 0;
+    if (Tr<R>::shadowed)
+        for (int j = 0; j < in.nv; ++j)
+            if (in.slot[j] == SLOT_CUR) in.slot[j] = SLOT_CURF;
+    return in;
+}
+
+// The persistent kernel's plan of one RKF45 attempt (the graph path's sequence).
+template <typename R>
+PersistPlan make_plan(const CtlParams& P) {
+    PersistPlan pl;
+    memset(&pl, 0, sizeof(pl));
+    StageIn in[6], cand, del;
+    rkf45_stages(in, cand, del);
+    for (int i = 0; i < 6; ++i) {
+        pl.in[i] = stage_for<R>(in[i], i == 0);
+        pl.eo[i] = epi_k(i, 1.0, (i == 0 && P.steady) ? 1 : 0);
+    }
+    pl.fin = comb2(cand, del);
+    pl.P = P;
+    return pl;
+}
+
 // Enqueues one step attempt of every system of the batch on stream st.
 template <typename R>
 void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cudaStream_t st, Prof* pr) {
@@ -522,37 +576,17 @@ void enqueue_attempt(Engine* E, int scheme, bool fixed, const CtlParams& P, cuda
     q.pr = pr;
     q.fuse = !(E->o.flags & SMOL_FLAG_NO_FUSE);
     auto Ev = [&](StageIn in, int k, double hfac, bool first) {
-        in.first = first ? 1 : 0;  // S(n^k): reused by the retry of a rejected attempt
-        if (Tr<R>::shadowed)
-            for (int j = 0; j < in.nv; ++j)
-                if (in.slot[j] == SLOT_CUR) in.slot[j] = SLOT_CURF;
-        q.eval(in, epi_k(k, hfac, (first && P.steady) ? 1 : 0));
+        // S(n^k) (first) is reused by the retry of a rejected attempt
+        q.eval(stage_for<R>(in, first), epi_k(k, hfac, (first && P.steady) ? 1 : 0));
     };
     auto finish = [&](const StageIn& cand, const StageIn& del) { q.finish(comb2(cand, del), P); };
     auto half = [&](const StageIn& in) { q.lincomb(in); };
     const int N = SLOT_CUR, H = SLOT_HALF;
     if (scheme == SCHEME_RKF45) {
-        Ev(stage({{N, 1.0}}), 0, 1.0, true);
-        Ev(stage({{N, 1.0}, {0, 0.25}}), 1, 1.0, false);
-        Ev(stage({{N, 1.0}, {0, 3.0 / 32.0}, {1, 9.0 / 32.0}}), 2, 1.0, false);
-        Ev(stage({{N, 1.0}, {0, 1932.0 / 2197.0}, {1, -7200.0 / 2197.0}, {2, 7296.0 / 2197.0}}), 3, 1.0, false);
-        Ev(stage({{N, 1.0}, {0, 439.0 / 216.0}, {1, -8.0}, {2, 3680.0 / 513.0}, {3, -845.0 / 4104.0}}), 4, 1.0,
-           false);
-        Ev(stage({{N, 1.0},
-                  {0, -8.0 / 27.0},
-                  {1, 2.0},
-                  {2, -3544.0 / 2565.0},
-                  {3, 1859.0 / 4104.0},
-                  {4, -11.0 / 40.0}}),
-           5, 1.0, false);
-        // n^{k+1} (fourth order) and n_RK5 - n^{k+1} from the differences of the two
-        // weight rows of the tableau
-        finish(stage({{N, 1.0}, {0, 25.0 / 216.0}, {2, 1408.0 / 2565.0}, {3, 2197.0 / 4104.0}, {4, -1.0 / 5.0}}),
-               stage({{0, 16.0 / 135.0 - 25.0 / 216.0},
-                      {2, 6656.0 / 12825.0 - 1408.0 / 2565.0},
-                      {3, 28561.0 / 56430.0 - 2197.0 / 4104.0},
-                      {4, -9.0 / 50.0 + 1.0 / 5.0},
-                      {5, 2.0 / 55.0}}));
+        StageIn in[6], cand, del;
+        rkf45_stages(in, cand, del);
+        for (int i = 0; i < 6; ++i) Ev(in[i], i, 1.0, i == 0);
+        finish(cand, del);
         return;
     }
     if (scheme == SCHEME_RK2) {
@@ -685,6 +719,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     E->mapC = (int2*)(ws + E->H.mapC);
     E->mapB = (int2*)(ws + E->H.mapB);
     E->mapF = (int2*)(ws + E->H.mapF);
+    E->d_bar = (unsigned*)(ws + E->H.bar);
     E->last_attempts.assign(count, 0);
     cudaStream_t st = E->stream;
     std::vector<SysDev> hs(count), hsr(count);
@@ -897,6 +932,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     E->H.nF = (int)mF.size();
     CK(cudaMemsetAsync(ws + E->H.ctl, 0, (size_t)count * sizeof(Ctl), st));
     CK(cudaMemsetAsync(ws + E->H.rctl, 0, (size_t)count * sizeof(Ctl), st));
+    CK(cudaMemsetAsync(ws + E->H.bar, 0, 2 * sizeof(unsigned), st));
     CK(cudaMemcpyAsync(E->d_sys, hs.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(E->d_sysr, hsr.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(E->mapC, mC.data(), mC.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
@@ -977,6 +1013,41 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
     int64_t na = E->o.chunk > 0 ? E->o.chunk : 32;
     if (E->o.max_attempts < na) na = E->o.max_attempts;
     if (na < 1) na = 1;
+    // Persistent attempt kernel instead of the graph: a single RKF45 system, when all
+    // its CTAs can be resident at once (else the graph path).
+    E->persist_run = false;
+    if ((E->o.flags & SMOL_FLAG_PERSISTENT) && E->count == 1 && scheme == SMOL_RKF45 && !fixed) {
+        const CtlParams P = make_params(E, scheme);
+        if (E->o.precision == SMOL_FP32CONV) {
+            E->pkern = (const void*)k_persist<float>;
+            E->plan = make_plan<float>(P);
+        } else if (E->o.precision == SMOL_DF64) {
+            E->pkern = (const void*)k_persist<dd>;
+            E->plan = make_plan<dd>(P);
+        } else {
+            E->pkern = (const void*)k_persist<double>;
+            E->plan = make_plan<double>(P);
+        }
+        int dev = 0, sms = 0, per = 0;
+        E->pblock = std::max(E->thrC, E->thrB);
+        E->psmem = std::max(E->smemC, E->smemB);
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, E->pkern, E->pblock, E->psmem) == cudaSuccess &&
+            per > 0) {
+            const int units = std::max(E->H.nC, E->H.nB);
+            E->pgrid = std::min(units, per * sms);
+            E->persist_run = true;
+        }
+        cudaGetLastError();  // an occupancy query that failed leaves the graph path
+    }
+    if (E->persist_run) {
+        E->run_dn.assign(d_n, d_n + E->count);
+        E->run_scheme = scheme;
+        E->run_attempts = na;
+        E->running = true;
+        return SMOL_OK;
+    }
     const int64_t key = ((na * 64 + scheme * 16 + (fixed ? 8 : 0) + (E->o.steady_rtol > 0.0 ? 4 : 0)) << 8) +
                         (E->o.flags & 0xff);
     if (E->gkey != key) {
@@ -1006,9 +1077,21 @@ int integrate_start(Engine* E, double* const* d_n, double t0, double t1, double 
     return SMOL_OK;
 }
 
+// One chunk of attempts on stream st: the captured graph, or one launch of the
+// persistent attempt kernel.
+cudaError_t launch_chunk(Engine* E, cudaStream_t st) {
+    if (E->persist_run) {
+        int na = (int)E->run_attempts;
+        void* args[] = {(void*)&E->h_one, (void*)&E->plan, (void*)&na, (void*)&E->d_bar};
+        return cudaLaunchCooperativeKernel(E->pkern, dim3((unsigned)E->pgrid), dim3((unsigned)E->pblock), args,
+                                           E->psmem, st);
+    }
+    return cudaGraphLaunch(E->gexec, st);
+}
+
 int integrate_advance(Engine* E) {
-    if (!E || !E->running || !E->gexec) return SMOL_EINVAL;
-    CK(cudaGraphLaunch(E->gexec, E->stream));
+    if (!E || !E->running || (!E->gexec && !E->persist_run)) return SMOL_EINVAL;
+    CK(launch_chunk(E, E->stream));
     return SMOL_OK;
 }
 
@@ -1073,13 +1156,13 @@ int integrate_all(Engine* E, double* const* d_n, double t0, double t1, double to
     const int64_t maxa = E->o.max_attempts;
     int64_t launched = E->run_attempts;  // attempts enqueued so far
     int cur = 0;
-    if (cudaGraphLaunch(E->gexec, st) != cudaSuccess) rc = SMOL_ECUDA;
+    if (launch_chunk(E, st) != cudaSuccess) rc = SMOL_ECUDA;
     if (rc == SMOL_OK && launched < maxa &&
         (cudaMemcpyAsync(E->h_ctl, E->d_ctl, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
          cudaEventRecord(ev[cur], st) != cudaSuccess || cudaEventRecord(E->ev_hctl, st) != cudaSuccess))
         rc = SMOL_ECUDA;
     while (rc == SMOL_OK && launched < maxa) {
-        if (cudaGraphLaunch(E->gexec, st) != cudaSuccess) {
+        if (launch_chunk(E, st) != cudaSuccess) {
             rc = SMOL_ECUDA;
             break;
         }
@@ -1200,7 +1283,7 @@ double time_attempts(Engine* E, double* const* d_work, const double* const* d_n0
 constexpr int TUNE_FLAGS[] = {0, SMOL_FLAG_NO_PDL, SMOL_FLAG_NO_PDL_FWD_COLS, SMOL_FLAG_NO_FUSE,
                               SMOL_FLAG_NO_FUSE | SMOL_FLAG_NO_PDL};
 constexpr int PDL_BITS = SMOL_FLAG_NO_PDL | SMOL_FLAG_NO_PDL_FWD_COLS | SMOL_FLAG_NO_PDL_ROWS |
-                         SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP | SMOL_FLAG_NO_FUSE;
+                         SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP | SMOL_FLAG_NO_FUSE | SMOL_FLAG_PERSISTENT;
 
 }  // namespace
 
@@ -1420,7 +1503,12 @@ int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double
             smol_system* S = new smol_system();
             if (engine_init(S, 1, &M, R, &h_U, &h_V, &lambda, c, wsa, bytes) == SMOL_OK &&
                 S->sh[0].G == g) {  // skip a G that the shared-memory limit reduced
-                for (int fl : TUNE_FLAGS) {
+                // the launch modes, and for RKF45 the persistent attempt kernel
+                int modes[8], nm = 0;
+                for (int fl : TUNE_FLAGS) modes[nm++] = fl;
+                if (scheme == SMOL_RKF45) modes[nm++] = SMOL_FLAG_PERSISTENT;
+                for (int k = 0; k < nm; ++k) {
+                    const int fl = modes[k];
                     S->o.flags = (base.flags & ~PDL_BITS) | fl;
                     const double us = time_attempts(S, &d_work, &d_n0, tol, scheme, attempts);
                     if (us > 0.0 && (best < 0.0 || us < best)) {

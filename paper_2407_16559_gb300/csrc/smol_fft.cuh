@@ -278,6 +278,23 @@ __device__ __forceinline__ void cp_async_el(T* smem, const T* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Gather of data that other CTAs wrote earlier in the same kernel (the persistent
+// attempt kernel): through L2 only, since an SM's L1 may still hold the lines of an
+// earlier phase. 16-byte elements keep the asynchronous copy (cp.async.cg); smaller ones
+// are loaded with ld.global.cg and stored. CG = false: the ordinary cached copy.
+template <bool CG, typename T>
+__device__ __forceinline__ void gather_el(T* smem, const T* gmem) {
+    if constexpr (!CG) {
+        cp_async_el(smem, gmem);
+    } else if constexpr (sizeof(T) == 16) {
+        const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    } else {
+        static_assert(sizeof(T) == 8, "8- or 16-byte elements");
+        *reinterpret_cast<float2*>(smem) = __ldcg(reinterpret_cast<const float2*>(gmem));
+    }
+}
+
 // Stages the table W_P^e (e < P) of a length-P tile transform into shared memory from
 // the global table of W_{2Mp}^e (e < Mp; W^{e + Mp} = -W^e): stage_tw issues the
 // copies, stage_tw_fix (after cp_async_wait, by the same threads) negates the entries
@@ -316,6 +333,25 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return sh[32];
 }
 
+// Block-wide minimum (inactive lanes contribute +inf). The result is valid in every
+// thread; ends with a barrier.
+__device__ __forceinline__ double block_min(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = (lane < nw) ? sh[lane] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (lane == 0) sh[32] = v;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// Block-wide maximum of non-negative values (inactive lanes contribute 0).
 __device__ __forceinline__ double block_max(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

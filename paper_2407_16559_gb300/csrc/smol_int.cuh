@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, 
         mx = fmax(mx, d);
     }
     mx = block_max(mx, red);
-    tb = -block_max(-tb, red);
+    tb = block_min(tb, red);
     if (threadIdx.x == 0) {
         S.fpart[(size_t)FPW * blk] = mx;
         S.fpart[(size_t)FPW * blk + 1] = tb;
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(128) k_prep2(const SysDev* __restrict__ sysv, 
         tbm = fmin(tbm, __ldcg(S.fpart + (size_t)FPW * b + 1));
     }
     rate = block_max(rate, red);
-    tbm = -block_max(-tbm, red);
+    tbm = block_min(tbm, red);
     if (threadIdx.x != 0) return;
     ctl->arrive = 0;
     ctl->tilt = tilt_from_bound(tbm, S.Mp, S.T);  // FP32 form: the first attempt's input tilt
@@ -843,12 +843,12 @@ __global__ void __launch_bounds__(128) k_tilt(const SysDev* __restrict__ sysv, c
         for (int i = blk * blockDim.x + threadIdx.x; i < S.M; i += S.nfin * blockDim.x)
             for (int t = 0; t < S.T; ++t)
                 tb = fmin(tb, (double)tilt_bound_el(cv.tlog[t], Wf[(size_t)t * S.Mp + i] * (float)n[i], i));
-    tb = -block_max(-tb, red);
+    tb = block_min(tb, red);
     if (threadIdx.x == 0) S.fpart[(size_t)FPW * blk] = tb;
     if (!arrive_last(ctl, S.nfin, &last)) return;
     double m = INFINITY;
     for (int b = threadIdx.x; b < S.nfin; b += blockDim.x) m = fmin(m, __ldcg(S.fpart + (size_t)FPW * b));
-    m = -block_max(-m, red);
+    m = block_min(m, red);
     if (threadIdx.x != 0) return;
     ctl->arrive = 0;
     ctl->tilt = tilt_from_bound(m, S.Mp, S.T);

@@ -477,8 +477,8 @@ __device__ void finalize_scalars(const SysDev& S, const CtlView& cv, const Stage
         const Terms<R> P = resolve_terms<R>(in, S, cv, false);
         double v = 0.0;
         if (lane < in.nv)
-            v = ((P.dmask >> lane) & 1u) ? __ldg(reinterpret_cast<const double*>(P.p[lane]))
-                                         : (double)ld1g<R>(reinterpret_cast<const R*>(P.p[lane]));
+            v = ((P.dmask >> lane) & 1u) ? __ldcg(reinterpret_cast<const double*>(P.p[lane]))
+                                         : (double)ld1cg<R>(reinterpret_cast<const R*>(P.p[lane]));
         double y1 = 0.0;
         for (int j = 0; j < in.nv; ++j) y1 += in.c[j] * __shfl_sync(0xffffffffu, v, j);
         if (lane == 0) *y1p = y1;
@@ -556,24 +556,29 @@ __device__ __forceinline__ int load_desc(const SysDev* __restrict__ sysv, const 
 
 // Waits for the predecessor kernels (griddep_wait), releases the next one, and fetches
 // the fields of the system's control block that every kernel reads. Ends with a barrier.
+// The control block is read through L2 (ld.cg): in the persistent attempt kernel
+// another CTA's controller wrote it earlier in the same kernel.
+__device__ __forceinline__ void load_ctl_fields(const SysDev& sh, CtlView& cv) {
+    const Ctl* c = sh.ctl;
+    if (threadIdx.x < MAXT) cv.xe[threadIdx.x] = __ldcg(c->xe + threadIdx.x);
+    if (threadIdx.x == 0) {
+        cv.done = __ldcg(&c->done);
+        cv.cur = __ldcg(&c->cur);
+        cv.s0 = reinterpret_cast<const double*>(__ldcg(reinterpret_cast<const long long*>(&c->state[0])));
+        cv.s1 = reinterpret_cast<const double*>(__ldcg(reinterpret_cast<const long long*>(&c->state[1])));
+        cv.h = __ldcg(&c->h);
+        cv.ymax = __ldcg(&c->ymax);
+        cv.reuse = __ldcg(&c->reuse);
+        cv.hf = __ldcg(&c->hf);
+        cv.tilt = __ldcg(&c->tilt);
+    }
+    if (threadIdx.x < TILT_T) cv.tlog[threadIdx.x] = __ldcg(c->tlog + threadIdx.x);
+    __syncthreads();
+}
 __device__ __forceinline__ void load_ctl(const SysDev& sh, CtlView& cv) {
     griddep_wait();
     griddep_release();
-    const Ctl* c = sh.ctl;
-    if (threadIdx.x < MAXT) cv.xe[threadIdx.x] = c->xe[threadIdx.x];
-    if (threadIdx.x == 0) {
-        cv.done = c->done;
-        cv.cur = c->cur;
-        cv.s0 = c->state[0];
-        cv.s1 = c->state[1];
-        cv.h = c->h;
-        cv.ymax = c->ymax;
-        cv.reuse = c->reuse;
-        cv.hf = c->hf;
-        cv.tilt = c->tilt;
-    }
-    if (threadIdx.x < TILT_T) cv.tlog[threadIdx.x] = c->tlog[threadIdx.x];
-    __syncthreads();
+    load_ctl_fields(sh, cv);
 }
 
 // A retry after a rejected attempt starts from the same state n^k (Sec. 2: the step
@@ -838,48 +843,60 @@ __device__ __forceinline__ void spectral_pair(const SysDev& S, const cx<R>* Z, i
 // First pair coefficient taken out of the FP64 spectral product (1 if it is zero).
 __device__ __forceinline__ double fold_coef(const SysDev& S) { return S.pcoef[0] != 0.0 ? S.pcoef[0] : 1.0; }
 
+// Shared memory of a row unit: a, b (N2 x 2T complex each), the tile twiddles W_N2^e,
+// the spectral twiddles of the two rows and their inverse four-step twiddles.
 template <typename R>
-__global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
-                                              const __grid_constant__ SysDev one, const StageIn in) {
-    __shared__ __align__(16) SysDev S;
-    __shared__ CtlView cv;
-    __shared__ R pc[MAXR];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int cta = load_desc(sysv, map, one, S);
-    if (cta == 0) {
-        // The scalar CTA of the system, beside the row CTAs: the evaluation's scalars,
-        // which only the inverse column kernel reads (y_1 from the FP64 state, not its
-        // FP32 shadow: the two large terms of the monomer equation nearly cancel).
-        double* sh = reinterpret_cast<double*>(smraw);
-        if ((int)threadIdx.x < S.T) sh[3 * MAXT + threadIdx.x] = (double)reinterpret_cast<const R*>(S.W)[(size_t)threadIdx.x * S.Mp];
-        load_ctl(S, cv);
-        if (cv.done || reused(in, cv)) return;
-        finalize_scalars<R>(S, cv, in, sh);
-        return;
-    }
-    const int blk = cta - 1;  // row pair
-    const int G = 2 * S.T;
+struct RowSm {
+    cx<R>* a;
+    cx<R>* b;
+    cx<R>* twP;  // W_N2^e
+    cx<R>* tws;  // W_L^{r + N1 k2} of the two rows, [rho][k2]
+    cx<R>* twi;  // conj W_Mp^{n2 r} of the two rows, [rho][n2]
+};
+template <typename R>
+__device__ __forceinline__ RowSm<R> row_sm(const SysDev& S, unsigned char* raw) {
+    RowSm<R> m;
+    const int n = S.N2 * 2 * S.T;
+    m.a = reinterpret_cast<cx<R>*>(raw);
+    m.b = m.a + n;
+    m.twP = m.b + n;
+    m.tws = m.twP + S.N2;
+    m.twi = m.tws + 2 * S.N2;
+    return m;
+}
+// The rows (r0, r1) of row unit blk: (blk, N1 - blk), and (0, N1 / 2) for blk = 0.
+__device__ __forceinline__ void row_pair_of(const SysDev& S, int blk, int& r0, int& r1) {
+    r0 = blk ? blk : 0;
+    r1 = blk ? S.N1 - blk : (S.N1 >> 1);
+}
+// Row prologue (constant data, before the wait for the previous kernel): the twiddles.
+template <typename R>
+__device__ __forceinline__ void row_prologue(const SysDev& S, int blk, const RowSm<R>& m) {
     const int N2 = S.N2;
-    cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
-    cx<R>* b = a + N2 * G;
-    cx<R>* twP = b + N2 * G;   // W_N2^e
-    cx<R>* tws = twP + N2;     // W_L^{r + N1 k2} of the two rows, [rho][k2]
-    cx<R>* twi = tws + 2 * N2; // conj W_Mp^{n2 r} of the two rows, [rho][n2]
-    const int r0 = blk ? blk : 0;
-    const int r1 = blk ? S.N1 - blk : (S.N1 >> 1);
-    const cx<R>* tw = reinterpret_cast<const cx<R>*>(S.tw);
-    stage_tw(twP, S.lgN2, tw, S.lgMp);
+    int r0, r1;
+    row_pair_of(S, blk, r0, r1);
+    stage_tw(m.twP, S.lgN2, reinterpret_cast<const cx<R>*>(S.tw), S.lgMp);
     for (int idx = threadIdx.x; idx < 2 * N2; idx += blockDim.x) {
         const int rho = idx >> S.lgN2, k2 = idx & (N2 - 1);
         const uint32_t r = (uint32_t)(rho ? r1 : r0);
-        cp_async_el(tws + idx, reinterpret_cast<const cx<R>*>(S.tws) + (size_t)r * N2 + k2);
-        cp_async_el(twi + idx, reinterpret_cast<const cx<R>*>(S.twr) + (size_t)r * N2 + k2);
+        cp_async_el(m.tws + idx, reinterpret_cast<const cx<R>*>(S.tws) + (size_t)r * N2 + k2);
+        cp_async_el(m.twi + idx, reinterpret_cast<const cx<R>*>(S.twr) + (size_t)r * N2 + k2);
     }
-    load_ctl(S, cv);
-    if (cv.done || reused(in, cv)) {
-        cp_async_wait();  // no copy into this CTA's shared memory outlives it
-        return;
-    }
+}
+// Row unit after the wait: gather of the 2T rows, row FFTs, real-FFT split, product sum,
+// packed inverse spectrum, inverse row FFTs and the inverse four-step twiddle. pc: MAXR
+// values of shared memory. CG: gather through L2 (persistent kernel).
+template <typename R, bool CG = false>
+__device__ __forceinline__ void row_body(const SysDev& S, const CtlView& cv, int blk, const RowSm<R>& m, R* pc) {
+    const int G = 2 * S.T;
+    const int N2 = S.N2;
+    cx<R>* a = m.a;
+    cx<R>* b = m.b;
+    cx<R>* twP = m.twP;
+    const cx<R>* tws = m.tws;
+    const cx<R>* twi = m.twi;
+    int r0, r1;
+    row_pair_of(S, blk, r0, r1);
     if (threadIdx.x < S.npairs) {
         // FP32: pair p carries 2^(e_u + e_v - e_max) so that the sum stays in range.
         // FP64: pc[0] is folded into the birth scale (spectral_pair).
@@ -898,7 +915,7 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
         const int col = idx >> S.lgN2;
         const int t = col >> 1, rho = col & 1;
         const int r = rho ? r1 : r0;
-        cp_async_el(a + k2 * G + col, Yin + (size_t)t * S.Mp + (size_t)r * N2 + k2);
+        gather_el<CG>(a + k2 * G + col, Yin + (size_t)t * S.Mp + (size_t)r * N2 + k2);
     }
     cp_async_wait();
     stage_tw_fix(twP, S.lgN2, S.lgMp);
@@ -940,6 +957,42 @@ __global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, c
     }
 }
 
+// The scalar unit's prologue: W_t[1] of every transform into sh[3 MAXT + t].
+template <typename R>
+__device__ __forceinline__ void scalar_prologue(const SysDev& S, double* sh) {
+    if ((int)threadIdx.x < S.T) sh[3 * MAXT + threadIdx.x] = (double)reinterpret_cast<const R*>(S.W)[(size_t)threadIdx.x * S.Mp];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_rows(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+                                              const __grid_constant__ SysDev one, const StageIn in) {
+    __shared__ __align__(16) SysDev S;
+    __shared__ CtlView cv;
+    __shared__ R pc[MAXR];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int cta = load_desc(sysv, map, one, S);
+    if (cta == 0) {
+        // The scalar CTA of the system, beside the row CTAs: the evaluation's scalars,
+        // which only the inverse column kernel reads (y_1 from the FP64 state, not its
+        // FP32 shadow: the two large terms of the monomer equation nearly cancel).
+        double* sh = reinterpret_cast<double*>(smraw);
+        scalar_prologue<R>(S, sh);
+        load_ctl(S, cv);
+        if (cv.done || reused(in, cv)) return;
+        finalize_scalars<R>(S, cv, in, sh);
+        return;
+    }
+    const int blk = cta - 1;  // row pair
+    const RowSm<R> m = row_sm<R>(S, smraw);
+    row_prologue<R>(S, blk, m);
+    load_ctl(S, cv);
+    if (cv.done || reused(in, cv)) {
+        cp_async_wait();  // no copy into this CTA's shared memory outlives it
+        return;
+    }
+    row_body<R>(S, cv, blk, m, pc);
+}
+
 // Epilogue inputs of the element pair (i, i + 1): the collision rates D_s = sum_t
 // delta_t W_t[s] (delta_t from the evaluation's scalars) and the stage input y_s.
 template <typename R>
@@ -974,7 +1027,7 @@ struct InvSm {
     R rs[5];  // scale, birth scale, 1 + lambda, S_1, loss_1 in type R
 };
 
-template <typename R>
+template <typename R, bool CG = false>
 __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, const StageIn& in, const EpiOut& eo,
                                          int bx, const ColSm<R>& m, InvSm<R>& sm) {
     const int G = S.G;
@@ -991,7 +1044,7 @@ __device__ __forceinline__ void inv_body(const SysDev& S, const CtlView& cv, con
     for (int idx = threadIdx.x; idx < S.N1 * G; idx += blockDim.x) {
         int g, k1;
         divmod(DG, idx, k1, g);
-        cp_async_el(a + idx, G2 + (size_t)k1 * S.N2 + n2b + g);
+        gather_el<CG>(a + idx, G2 + (size_t)k1 * S.N2 + n2b + g);
     }
     const R* yr = reinterpret_cast<const R*>(S.ybuf);
     const double* yd = in.direct ? reinterpret_cast<const double*>(resolve_terms<R>(in, S, cv).p[0]) : nullptr;
