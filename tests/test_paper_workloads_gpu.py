@@ -103,9 +103,9 @@ def test_config4_reduced_precision_trajectories(smol):
     """The relaxation workload (M = 2^16, Brownian 1/3 + constant 2, lambda = 0.1, RKF45,
     tol 1e-9) in the FP32 form and in the double-float form against the FP64 solver at
     log-spaced checkpoints: the double-float form follows the FP64 trajectory to the
-    tolerance's level with the same amount of work; the FP32 form stays within 1e-3 early
-    on (its error estimate carries FFT rounding of ~1e-7 relative, which the controller at
-    tol 1e-9 cannot tell from truncation error)."""
+    tolerance's level with the same amount of work; the FP32 form stays within 1e-4 with
+    at most 1.5 times the attempts (its transform inputs are exponentially tilted, so
+    the FP32 rounding no longer fills the near-empty tail)."""
     import torch
     M = 65536
     U, V = kernel_factors("brownian_const", M, a=1.0 / 3.0)
@@ -136,6 +136,9 @@ def test_config4_reduced_precision_trajectories(smol):
     assert abs(np.dot(k, dd[-1]) - np.dot(k, ref[-1])) <= 2e-8
     lo = M - 2048
     assert abs(np.dot(k[:lo], dd[-1][:lo]) - np.dot(k[:lo], ref[-1][:lo])) <= 5e-9
-    f32, _ = run("fp32conv", ts[:6])
-    for a, b in zip(f32, ref[:6]):
-        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
+    # the FP32 form (exponentially tilted transform inputs) over the whole span, against
+    # the FP64 solver, with at most 1.5 times its work
+    f32, att32 = run("fp32conv", ts)
+    for a, b in zip(f32, ref):
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b)
+    assert att32 <= 1.5 * att64
