@@ -237,7 +237,7 @@ def test_tune_picks_a_valid_schedule(smol):
     assert us > 0.0
     assert sched["fft_lgn1"] in (5, 6, 7) and sched["fft_g"] in (2, 4, 8, 16, 32)
     assert sched["flags"] in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS, smol.FLAG_NO_FUSE,
-                              smol.FLAG_NO_FUSE | smol.FLAG_NO_PDL)
+                              smol.FLAG_NO_FUSE | smol.FLAG_NO_PDL, smol.FLAG_PERSISTENT)
     a, _ = smol.System(U, V, 0.01, fixed_tau=0.01, **sched).integrate(n0, 0.0, 1.0, 1e-8)
     b, _ = smol.System(U, V, 0.01, fixed_tau=0.01).integrate(n0, 0.0, 1.0, 1e-8)
     a, b = a.cpu().numpy(), b.cpu().numpy()
