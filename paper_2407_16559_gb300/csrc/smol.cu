@@ -166,7 +166,7 @@ Header make_header(const std::vector<Shape>& sh) {
     H.mapC = take((size_t)H.nC * sizeof(int2));
     H.mapB = take((size_t)H.nB * sizeof(int2));
     H.mapF = take((size_t)H.nF * sizeof(int2));
-    H.bar = take(2 * sizeof(unsigned));  // grid barrier of the persistent attempt kernel
+    H.bar = take(2 * BAR_GEN * sizeof(unsigned));  // grid barrier of the persistent attempt kernel
     H.total = o;
     return H;
 }
@@ -932,7 +932,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     E->H.nF = (int)mF.size();
     CK(cudaMemsetAsync(ws + E->H.ctl, 0, (size_t)count * sizeof(Ctl), st));
     CK(cudaMemsetAsync(ws + E->H.rctl, 0, (size_t)count * sizeof(Ctl), st));
-    CK(cudaMemsetAsync(ws + E->H.bar, 0, 2 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(ws + E->H.bar, 0, 2 * BAR_GEN * sizeof(unsigned), st));
     CK(cudaMemcpyAsync(E->d_sys, hs.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(E->d_sysr, hsr.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(E->mapC, mC.data(), mC.size() * sizeof(int2), cudaMemcpyHostToDevice, st));

@@ -33,30 +33,45 @@ struct PersistPlan {
     CtlParams P;
 };
 
-// Grid-wide barrier of a cooperative launch on bar[0] (arrival count) and bar[1]
-// (generation). Returns false when the wait gave up (and then marks the status).
+// GPU-scope acquire load and release / acquire-release atomics (PTX memory model): the
+// CTA's writes, ordered before its thread 0 by the block barrier, are released with the
+// arrival and acquired by every CTA that sees the new generation (cumulativity), without
+// a full fence on either side.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch on bar[0] (arrival count) and bar[BAR_GEN]
+// (generation, on its own 128-byte line, so that the polling does not contend with the
+// arrivals). Returns false when the wait gave up (and then marks the status).
+constexpr int BAR_GEN = 32;
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, Ctl* ctl, int* flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = bar + 1;
-        const unsigned gen = *vgen;  // read before arriving: it cannot advance before then
-        __threadfence();
+        const unsigned gen = ld_acquire(bar + BAR_GEN);  // read before arriving: it cannot advance before then
         int ok = 1;
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        if (atom_add_acq_rel(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;  // ordered before the release below; every CTA has arrived
+            st_release(bar + BAR_GEN, gen + 1u);
         } else {
             const long long t0 = clock64();
-            while (*vgen == gen) {
+            while (ld_acquire(bar + BAR_GEN) == gen) {
                 if (clock64() - t0 > BAR_WAIT_CYCLES) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
         if (!ok) {
             atomicExch(&ctl->status, (int)ST_ETIMEOUT);
             atomicExch(&ctl->done, 1);
