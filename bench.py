@@ -546,7 +546,7 @@ def gpu_arm(args):
         if rank == 0:
             print(json.dumps({"batch_ms_per_step": msb / K, "systems": args.batch, "steps": K}))
         return 0
-    peaks = live_peaks(smol, stream)  # untimed set-up
+    peaks = {} if args.no_peaks else live_peaks(smol, stream)  # untimed set-up
     barrier()
     with ClockSampler(local) as clk:
         ms, stats, prof_ms, prof_cnt, tsys, U, V, sched = time_form(smol, torch, precision, K, W, stream, flush, rank,
@@ -864,6 +864,9 @@ def main():
     ap.add_argument("--both", action="store_true", default=True)
     ap.add_argument("--no-both", dest="both", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the live FMA-rate measurement (profiling runs; the FP64 roofline then uses the "
+                         "derived figure and says so)")
     ap.add_argument("--tts", action="store_true", default=True,
                     help="time-to-solution legs against the oracle's trajectories (default on)")
     ap.add_argument("--no-tts", dest="tts", action="store_false")
