@@ -45,7 +45,8 @@ EVALS_PER_STEP = 6          # RKF45 stages
 LAUNCHES_FUSED = 13         # forward columns, 6 x row kernel, 5 x fused inverse+forward columns,
                             # fused last inverse + combination / control
 LAUNCHES_UNFUSED = 19       # 6 x (forward columns, rows, inverse columns) + combination / control
-FLAG_NO_FUSE = 32           # smol_opts.flags bit (SMOL_FLAG_NO_FUSE)
+FLAG_NO_FUSE = 32           # smol_opts.flags bits (SMOL_FLAG_NO_FUSE, SMOL_FLAG_PERSISTENT: one
+FLAG_PERSISTENT = 64        # cooperative launch per chunk of attempts; the timed chunk is one attempt)
 L2_FLUSH_BYTES = 256 << 20
 CTL_BYTES = 328             # the device control block of one system (smol::Ctl)
 
@@ -587,7 +588,8 @@ def gpu_arm(args):
                      "t_end": stats["t"]},
         "roofline": roof, "attempt_hbm": attempt_hbm(precision, T, WORKLOAD["M"], ms / K),
         "peaks_live": peaks, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": K * (LAUNCHES_UNFUSED if sched.get("flags", 0) & FLAG_NO_FUSE else LAUNCHES_FUSED),
+        "gpu_launches": K * (1 if sched.get("flags", 0) & FLAG_PERSISTENT else
+                             (LAUNCHES_UNFUSED if sched.get("flags", 0) & FLAG_NO_FUSE else LAUNCHES_FUSED)),
         "clocks": clocks,
     }
     if args.both and precision == "fp64":
