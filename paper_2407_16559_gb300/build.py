@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsmol.so")
 SOURCES = ["smol.cu", "smol_static.cu", "smol_probe.cu", "smol_lowrank.cpp"]
-HEADERS = ["smol_fft.cuh", "smol_rhs.cuh", "smol_int.cuh", "smol_dd.cuh", "smol_attr.h"]
+HEADERS = ["smol_fft.cuh", "smol_rhs.cuh", "smol_int.cuh", "smol_dd.cuh", "smol_persist.cuh", "smol_attr.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
