@@ -104,6 +104,7 @@ SIGNATURES = {
 FLAG_NO_PDL, FLAG_NO_PDL_FWD_COLS, FLAG_NO_PDL_ROWS, FLAG_NO_PDL_INV_COLS, FLAG_NO_PDL_STEP = 1, 2, 4, 8, 16
 FLAG_NO_FUSE = 32
 FLAG_PERSISTENT = 64
+FLAG_WIDE_COLS = 128
 SCHEDULE_KEYS = ("fft_lgn1", "fft_g", "flags")
 
 

@@ -88,10 +88,10 @@ size_t smem_rows(const Shape& s, int T) {
 }
 
 // Threads of a CTA whose passes cover `points` points: one per radix-8 butterfly,
-// between 32 and 256.
-int threads_for(int points) {
+// between 32 and cap.
+int threads_for(int points, int cap = 256) {
     int t = points / 8;
-    if (t > 256) t = 256;
+    if (t > cap) t = cap;
     if (t < 32) t = 32;
     return (t + 31) & ~31;
 }
@@ -297,6 +297,7 @@ struct Engine {
     int2 *mapC = nullptr, *mapB = nullptr, *mapF = nullptr;
     size_t smemC = 0, smemB = 0;
     int thrC = 32, thrB = 32;
+    int thrCW = 32;  // column CTAs with SMOL_FLAG_WIDE_COLS (single system)
     Ctl* h_ctl = nullptr;  // pinned host copies of the control blocks
     cudaEvent_t ev_rb[2] = {nullptr, nullptr};  // completions of read-backs into h_ctl
     cudaEvent_t ev_hctl = nullptr;  // the last stream operation that reads or writes h_ctl
@@ -395,12 +396,17 @@ void launch(const Engine* E, int kind, void (*k)(KArgs...), int grid, int block,
     cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
+// Threads of the column CTAs of this engine's launches.
+int col_threads(const Engine* E) {
+    return ((E->o.flags & SMOL_FLAG_WIDE_COLS) && E->count == 1) ? E->thrCW : E->thrC;
+}
+
 template <typename R>
 void launch_eval(const Engine* E, const LaunchArgs& A, const StageIn& in, const EpiOut& eo, cudaStream_t st,
                  Prof* pr) {
     {
         ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
-        launch(E, SMOL_PROF_FWD_COLS, k_fwd_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, in);
+        launch(E, SMOL_PROF_FWD_COLS, k_fwd_cols<R>, E->H.nC, col_threads(E), E->smemC, st, A.sys, A.mapC, A.one, in);
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_ROWS);
@@ -408,7 +414,7 @@ void launch_eval(const Engine* E, const LaunchArgs& A, const StageIn& in, const 
     }
     {
         ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
-        launch(E, SMOL_PROF_INV_COLS, k_inv_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, in, eo);
+        launch(E, SMOL_PROF_INV_COLS, k_inv_cols<R>, E->H.nC, col_threads(E), E->smemC, st, A.sys, A.mapC, A.one, in, eo);
     }
 }
 
@@ -431,12 +437,12 @@ struct Seq {
     void eval(const StageIn& in, const EpiOut& eo) {
         if (pending && fuse) {
             ProfScope ps(pr, st, SMOL_PROF_INV_FWD);
-            launch(E, SMOL_PROF_INV_COLS, k_inv_fwd<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, pin, peo,
+            launch(E, SMOL_PROF_INV_COLS, k_inv_fwd<R>, E->H.nC, col_threads(E), E->smemC, st, A.sys, A.mapC, A.one, pin, peo,
                    in);
         } else {
             flush();
             ProfScope ps(pr, st, SMOL_PROF_FWD_COLS);
-            launch(E, SMOL_PROF_FWD_COLS, k_fwd_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, in);
+            launch(E, SMOL_PROF_FWD_COLS, k_fwd_cols<R>, E->H.nC, col_threads(E), E->smemC, st, A.sys, A.mapC, A.one, in);
         }
         {
             ProfScope ps(pr, st, SMOL_PROF_ROWS);
@@ -449,7 +455,7 @@ struct Seq {
     void finish(const Comb2& c, const CtlParams& P) {
         if (pending && fuse) {
             ProfScope ps(pr, st, SMOL_PROF_INV_STEP);
-            launch(E, SMOL_PROF_STEP, k_inv_finish<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, pin, peo,
+            launch(E, SMOL_PROF_STEP, k_inv_finish<R>, E->H.nC, col_threads(E), E->smemC, st, A.sys, A.mapC, A.one, pin, peo,
                    c, P);
             pending = false;
             return;
@@ -466,7 +472,7 @@ struct Seq {
     void flush() {
         if (!pending) return;
         ProfScope ps(pr, st, SMOL_PROF_INV_COLS);
-        launch(E, SMOL_PROF_INV_COLS, k_inv_cols<R>, E->H.nC, E->thrC, E->smemC, st, A.sys, A.mapC, A.one, pin, peo);
+        launch(E, SMOL_PROF_INV_COLS, k_inv_cols<R>, E->H.nC, col_threads(E), E->smemC, st, A.sys, A.mapC, A.one, pin, peo);
         pending = false;
     }
 };
@@ -777,6 +783,10 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         // one thread per radix-8 butterfly of the column tiles, and at least one per
         // stage-input pair (so that all stage-input loads of a CTA are in flight at once)
         E->thrC = std::max(E->thrC, std::max(threads_for(s.N1 * s.G * T), std::min(256, (s.N1 * s.G / 2 + 31) & ~31)));
+        // wide column CTAs: one thread per element pair (the per-pair phases of the
+        // column kernels are chains of dependent FP64 operations, which more warps hide)
+        E->thrCW = std::max(E->thrCW, std::max(threads_for(s.N1 * s.G * T, COL_THREADS_MAX),
+                                               std::min(COL_THREADS_MAX, (s.N1 * s.G / 2 + 31) & ~31)));
         E->thrB = std::max(E->thrB, threads_for(s.N2 * 2 * T));
         char* b = ws + E->base[q];
         SysDev& d = hs[q];
@@ -1283,7 +1293,8 @@ double time_attempts(Engine* E, double* const* d_work, const double* const* d_n0
 constexpr int TUNE_FLAGS[] = {0, SMOL_FLAG_NO_PDL, SMOL_FLAG_NO_PDL_FWD_COLS, SMOL_FLAG_NO_FUSE,
                               SMOL_FLAG_NO_FUSE | SMOL_FLAG_NO_PDL};
 constexpr int PDL_BITS = SMOL_FLAG_NO_PDL | SMOL_FLAG_NO_PDL_FWD_COLS | SMOL_FLAG_NO_PDL_ROWS |
-                         SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP | SMOL_FLAG_NO_FUSE | SMOL_FLAG_PERSISTENT;
+                         SMOL_FLAG_NO_PDL_INV_COLS | SMOL_FLAG_NO_PDL_STEP | SMOL_FLAG_NO_FUSE | SMOL_FLAG_PERSISTENT |
+                         SMOL_FLAG_WIDE_COLS;
 
 }  // namespace
 
@@ -1504,8 +1515,10 @@ int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double
             if (engine_init(S, 1, &M, R, &h_U, &h_V, &lambda, c, wsa, bytes) == SMOL_OK &&
                 S->sh[0].G == g) {  // skip a G that the shared-memory limit reduced
                 // the launch modes, and for RKF45 the persistent attempt kernel
-                int modes[8], nm = 0;
+                int modes[12], nm = 0;
                 for (int fl : TUNE_FLAGS) modes[nm++] = fl;
+                modes[nm++] = SMOL_FLAG_WIDE_COLS | SMOL_FLAG_NO_PDL;
+                modes[nm++] = SMOL_FLAG_WIDE_COLS | SMOL_FLAG_NO_PDL_FWD_COLS;
                 if (scheme == SMOL_RKF45) modes[nm++] = SMOL_FLAG_PERSISTENT;
                 for (int k = 0; k < nm; ++k) {
                     const int fl = modes[k];

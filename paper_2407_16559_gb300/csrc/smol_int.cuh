@@ -223,8 +223,8 @@ struct Comb2 {
 // Per-thread accumulators of the final combination: ||error||^2, ||candidate||^2 and
 // sum_s s candidate_s (FP64), max |candidate| as the bit pattern of a non-negative
 // double (integer max is monotone on those, and a NaN or infinity pattern is at least
-// INF_BITS, which marks a non-finite candidate); the FP32 form keeps its norms, max and
-// finite test in FP32 until fin_acc_close.
+// INF_BITS, which marks a non-finite candidate); the FP32 form keeps its per-thread
+// norms, max and finite test in FP32.
 struct FinAcc {
     double se, sc, ms;
     unsigned long long mxb;
@@ -243,14 +243,6 @@ __device__ __forceinline__ FinAcc fin_acc() {
     for (int t = 0; t < TILT_T; ++t) a.tmx[t] = 0.f;
     a.fbad = false;
     return a;
-}
-template <typename R>
-__device__ __forceinline__ void fin_acc_close(FinAcc& a) {
-    if (std::is_same<R, float>::value) {
-        a.se = (double)a.fse;
-        a.sc = (double)a.fsc;
-        a.mxb = a.fbad ? INF_BITS : absbits((double)a.fmx);
-    }
 }
 
 // Final combination at the element pair (i, i + 1) (i even): candidate = sum c_j v_j
@@ -437,42 +429,62 @@ __device__ __forceinline__ void fin_pair(const SysDev& S, const Comb2& cd, const
     }
 }
 
-// Shared memory of fin_tail.
+// Shared memory of fin_tail: per-warp partials (up to 32 warps) and the last CTA's
+// reduced values.
 struct FinSm {
-    double wred[4][8];
-    unsigned long long xred[8];
-    double tredd[8];
-    float tred[8];
-    float tmred[TILT_T][8];
+    double wred[3][32];
+    unsigned long long xred[32];
+    float tred[32];
+    float tmred[TILT_T][32];
+    double res[5];            // last CTA: E, C, sum s n_s, tilt bound, Q
+    unsigned long long resx;  // last CTA: max |candidate| bits
+    float restm[TILT_T];      // last CTA: the tilt's input maxima
     bool last;
 };
 
 // End of an attempt, after every thread of the CTA has accumulated its elements: the
 // CTA's partials are written to slot blk of nblk; the last CTA of the system reduces
-// them in a fixed order (thread j takes partials j, j + blockDim, ...; then one fused
-// tree over the block) and runs the controller (thread 0) and the error norm (thread
-// 32) on the shared copy cs of the control block, which it then writes back.
+// them and runs the controller (thread 0) and the error norm (thread 32) on the shared
+// copy cs of the control block, which it then writes back.
+//
+// The reductions are short: the FP64 pipe of this part takes about 64 cycles per
+// dependent operation, so the last CTA gives each quantity its own warp (E, C, the mass
+// moment, Q, and the max / min / tilt values), whose lanes stride over the partials and
+// then meet in a shuffle tree; every order is fixed. The FP32 form's per-thread norms
+// are FP32 sums; from there on they are summed in FP64 (an FP32 warp sum would make the
+// error norm depend on the launch shape at 1e-7, enough to move the step sequence).
 template <typename R>
 __device__ __forceinline__ void fin_tail(const SysDev& S, const CtlParams& P, Ctl* ctl, Ctl& cs, int blk, int nblk,
                                          FinAcc acc, FinSm& f) {
     constexpr int CW = (int)(sizeof(Ctl) / 4);
-    fin_acc_close<R>(acc);
-    double se = acc.se, sc = acc.sc, ms = acc.ms;
-    unsigned long long mxb = acc.mxb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double se, sc;
+    unsigned long long mxb;
+    if constexpr (std::is_same<R, float>::value) {
+        se = (double)acc.fse;
+        sc = (double)acc.fsc;
+        mxb = acc.fbad ? INF_BITS : absbits((double)acc.fmx);
+    } else {
+        se = acc.se;
+        sc = acc.sc;
+        mxb = acc.mxb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        se += __shfl_down_sync(0xffffffffu, se, o);
+        sc += __shfl_down_sync(0xffffffffu, sc, o);
+        mxb = max(mxb, __shfl_down_sync(0xffffffffu, mxb, o));
+    }
+    double ms = acc.ms;
     float tb = acc.tb;
     float tmx[TILT_T];
 #pragma unroll
     for (int t = 0; t < TILT_T; ++t) tmx[t] = acc.tmx[t];
     for (int o = 16; o > 0; o >>= 1) {
-        se += __shfl_down_sync(0xffffffffu, se, o);
-        sc += __shfl_down_sync(0xffffffffu, sc, o);
         ms += __shfl_down_sync(0xffffffffu, ms, o);
-        mxb = max(mxb, __shfl_down_sync(0xffffffffu, mxb, o));
         tb = fminf(tb, __shfl_down_sync(0xffffffffu, tb, o));
 #pragma unroll
         for (int t = 0; t < TILT_T; ++t) tmx[t] = fmaxf(tmx[t], __shfl_down_sync(0xffffffffu, tmx[t], o));
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if (lane == 0) {
         f.wred[0][warp] = se;
         f.wred[1][warp] = sc;
@@ -508,70 +520,59 @@ __device__ __forceinline__ void fin_tail(const SysDev& S, const CtlParams& P, Ct
         // slots: E, C, max bits, tilt bound, mass moment
         S.fpart[FPW * blk + (q == 3 ? 4 : (q == 4 ? 3 : q))] = v;
     }
-    if (!arrive_last(ctl, nblk, &f.last)) return;
-    double E = 0.0, C = 0.0, Q = 0.0, MS = 0.0, TB = INFINITY;
-    unsigned long long XB = 0ull;
-    float TM[TILT_T];
+    if (!arrive_last_ar(ctl, nblk, &f.last)) return;
+    for (int qi = warp; qi < 5; qi += nw) {
+        if (qi == 4 && !P.steady) continue;
+        if (qi != 3) {
+            // sums: E (slot 0), C (slot 1), mass moment (slot 4); Q over the forward CTAs
+            double v = 0.0;
+            if (qi == 4) {
+                for (int b = lane; b < S.nbx; b += 32) v += __ldcg(S.sqpart + b);
+            } else {
+                const int slot = qi == 2 ? 4 : qi;
+                for (int b = lane; b < nblk; b += 32) v += __ldcg(S.fpart + FPW * b + slot);
+            }
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) f.res[qi == 2 ? 2 : (qi == 4 ? 4 : qi)] = v;
+        } else {
+            // max |candidate| bits (slot 2), tilt bound (slot 3, min), input maxima (5..)
+            unsigned long long x = 0ull;
+            double b3 = INFINITY;
+            float tm[TILT_T];
 #pragma unroll
-    for (int t = 0; t < TILT_T; ++t) TM[t] = 0.f;
-#pragma unroll 4
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const double* q = S.fpart + FPW * b;
-        E += __ldcg(q);
-        C += __ldcg(q + 1);
-        XB = max(XB, (unsigned long long)__double_as_longlong(__ldcg(q + 2)));
-        TB = fmin(TB, __ldcg(q + 3));
-        MS += __ldcg(q + 4);
+            for (int t = 0; t < TILT_T; ++t) tm[t] = 0.f;
+            for (int b = lane; b < nblk; b += 32) {
+                const double* q = S.fpart + FPW * b;
+                x = max(x, (unsigned long long)__double_as_longlong(__ldcg(q + 2)));
+                b3 = fmin(b3, __ldcg(q + 3));
 #pragma unroll
-        for (int t = 0; t < TILT_T; ++t) TM[t] = fmaxf(TM[t], (float)__ldcg(q + 5 + t));
-    }
-    if (P.steady)
-        for (int b = threadIdx.x; b < S.nbx; b += blockDim.x) Q += __ldcg(S.sqpart + b);
-    for (int o = 16; o > 0; o >>= 1) {
-        E += __shfl_down_sync(0xffffffffu, E, o);
-        C += __shfl_down_sync(0xffffffffu, C, o);
-        Q += __shfl_down_sync(0xffffffffu, Q, o);
-        MS += __shfl_down_sync(0xffffffffu, MS, o);
-        XB = max(XB, __shfl_down_sync(0xffffffffu, XB, o));
-        TB = fmin(TB, __shfl_down_sync(0xffffffffu, TB, o));
+                for (int t = 0; t < TILT_T; ++t) tm[t] = fmaxf(tm[t], (float)__ldcg(q + 5 + t));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                x = max(x, __shfl_down_sync(0xffffffffu, x, o));
+                b3 = fmin(b3, __shfl_down_sync(0xffffffffu, b3, o));
 #pragma unroll
-        for (int t = 0; t < TILT_T; ++t) TM[t] = fmaxf(TM[t], __shfl_down_sync(0xffffffffu, TM[t], o));
+                for (int t = 0; t < TILT_T; ++t) tm[t] = fmaxf(tm[t], __shfl_down_sync(0xffffffffu, tm[t], o));
+            }
+            if (lane == 0) {
+                f.resx = x;
+                f.res[3] = b3;
+#pragma unroll
+                for (int t = 0; t < TILT_T; ++t) f.restm[t] = tm[t];
+            }
+        }
     }
     const double nrm2_0 = cs.nrm2;  // read before the controller may overwrite them
     const int64_t att0 = cs.attempts;
-    __syncthreads();  // wred / xred reuse
-    if (lane == 0) {
-        f.wred[0][warp] = E;
-        f.wred[1][warp] = C;
-        f.wred[2][warp] = MS;
-        f.wred[3][warp] = Q;
-        f.xred[warp] = XB;
-        f.tredd[warp] = TB;
-#pragma unroll
-        for (int t = 0; t < TILT_T; ++t) f.tmred[t][warp] = TM[t];
-    }
     __syncthreads();
     const int t2 = blockDim.x > 32 ? 32 : 0;
     if (threadIdx.x == 0 || threadIdx.x == t2) {
-        E = f.wred[0][0], C = f.wred[1][0], MS = f.wred[2][0], Q = f.wred[3][0], XB = f.xred[0], TB = f.tredd[0];
-        for (int w = 1; w < nw; ++w) {
-            E += f.wred[0][w];
-            C += f.wred[1][w];
-            MS += f.wred[2][w];
-            Q += f.wred[3][w];
-            XB = max(XB, f.xred[w]);
-            TB = fmin(TB, f.tredd[w]);
-        }
-        const bool bad = XB >= INF_BITS;
+        const double E = f.res[0], Q = P.steady ? f.res[4] : 0.0;
+        const bool bad = f.resx >= INF_BITS;
         if (threadIdx.x == t2) error_norm(P, S, cs, nrm2_0, att0, E, bad, Q);
-        if (threadIdx.x == 0) {
-            float TMX[TILT_T];
-            for (int t = 0; t < TILT_T; ++t) {
-                TMX[t] = f.tmred[t][0];
-                for (int w = 1; w < nw; ++w) TMX[t] = fmaxf(TMX[t], f.tmred[t][w]);
-            }
-            controller(P, S, cs, E, C, __longlong_as_double((long long)XB), bad, MS, Q, TB, TMX);
-        }
+        if (threadIdx.x == 0)
+            controller(P, S, cs, E, f.res[1], __longlong_as_double((long long)f.resx), bad, f.res[2], Q, f.res[3],
+                       f.restm);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < CW; q += blockDim.x)
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
 // CTA combines the element pairs whose stage vector it has just formed, then fin_tail
 // over the nbx column CTAs of the system.
 template <typename R>
-__global__ void __launch_bounds__(256) k_inv_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(COL_THREADS_MAX) k_inv_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                     const __grid_constant__ SysDev one, const StageIn in,
                                                     const EpiOut eo, const Comb2 cd, const CtlParams P) {
     __shared__ __align__(16) SysDev S;

@@ -33,19 +33,14 @@ struct PersistPlan {
     CtlParams P;
 };
 
-// GPU-scope acquire load and release / acquire-release atomics (PTX memory model): the
-// CTA's writes, ordered before its thread 0 by the block barrier, are released with the
-// arrival and acquired by every CTA that sees the new generation (cumulativity), without
-// a full fence on either side.
+// GPU-scope acquire load and release store (PTX memory model; the acquire-release
+// atomic add is in smol_rhs.cuh): the CTA's writes, ordered before its thread 0 by the
+// block barrier, are released with the arrival and acquired by every CTA that sees the
+// new generation (cumulativity), without a full fence on either side.
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
 }
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -83,7 +78,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, Ctl* ctl, int* flag)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_persist(const __grid_constant__ SysDev one,
+__global__ void __launch_bounds__(256, 1) k_persist(const __grid_constant__ SysDev one,
                                                  const __grid_constant__ PersistPlan pl, int nattempts,
                                                  unsigned* bar) {
     __shared__ __align__(16) SysDev S;

@@ -47,7 +47,10 @@ constexpr int MAXR = 16;        // largest rank R (SMOL_MAX_R)
 constexpr int MAXT = 2 * MAXR;  // largest number of distinct transforms
 constexpr int MAXV = 10;        // terms of a stage-input linear combination
 constexpr int NVEC = 12;        // stage / work vectors per system
-constexpr int FPW = MAXT + 8;   // doubles per block of the finish / preparation partials
+constexpr int FPW = MAXT + 8;
+// Threads of a column CTA: at most 256 by default, up to 512 for a single system with
+// SMOL_FLAG_WIDE_COLS (one thread per element pair of a column tile).
+constexpr int COL_THREADS_MAX = 512;   // doubles per block of the finish / preparation partials
 constexpr int MAXSRC = 8;       // point sources P_k of Eq. (3) per system
 constexpr int TILT_T = 4;       // FP32 form: input tilt for systems of at most this many transforms
 
@@ -442,6 +445,24 @@ __device__ __forceinline__ bool arrive_last(Ctl* ctl, int nblk, bool* flag) {
     return *flag;
 }
 
+// GPU-scope acquire-release atomic add (PTX memory model): releases the writes ordered
+// before it (those of the whole CTA, through the preceding block barrier) and acquires
+// those released by earlier arrivals, in one operation.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// arrive_last with the arrival as one acquire-release atomic and no fences: for callers
+// that read the other CTAs' partials through L2 only (ld.cg), which the acquire orders.
+__device__ __forceinline__ bool arrive_last_ar(Ctl* ctl, int nblk, bool* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = atom_add_acq_rel(&ctl->arrive, 1u) == (unsigned)nblk - 1;
+    __syncthreads();
+    return *flag;
+}
+
 // FP32 copies of delta_t behind the FP64 scalars: [0, MAXT) rounded, [MAXT, 2 MAXT) the
 // remainders (the double-float form's low parts).
 __device__ __forceinline__ float* rsc_f(const SysDev& S) { return reinterpret_cast<float*>(S.rsc + MAXT + 2); }
@@ -693,6 +714,9 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
     // far fewer FP64 instructions than a shuffle tree in every warp; the FP32 form sums
     // in FP32 shuffles and then in FP64 across warps.
     const bool viasm = Tr<R>::fp64 && N1 * G >= (int)blockDim.x;
+    // the FP32 path's per-warp partials: red for up to 8 warps, else the second tile
+    // buffer (a CTA of more than 256 threads has N1 G >= 1024 points there)
+    const bool wbuf = !viasm && nw > 8;
     double* rb = reinterpret_cast<double*>(b);
     for (int t = 0; t < T; ++t) {
         const R sc = pow2<R>(-xexp<R>(S, cv, t));
@@ -725,8 +749,10 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
             nu += shfl_down(nu, o);
         }
         if (lane == 0) {
-            red[2 * t][warp] = (double)mu;
-            red[2 * t + 1][warp] = (double)nu;
+            double* rp = wbuf ? rb + 64 * t : red[2 * t];
+            const int st = wbuf ? 32 : 8;
+            rp[warp] = (double)mu;
+            rp[st + warp] = (double)nu;
         }
     }
     __syncthreads();
@@ -738,11 +764,15 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
             if (lane == 0) S.mpart[2 * ((size_t)(q >> 1) * S.nbx + bx) + (q & 1)] = v;
         }
         __syncthreads();  // the transform overwrites the second tile buffer
-    } else if (threadIdx.x < 2 * T) {
-        double v = 0.0;
-        for (int w = 0; w < nw; ++w) v += red[threadIdx.x][w];
-        const int t = threadIdx.x >> 1;
-        S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
+    } else {
+        if (threadIdx.x < 2 * T) {
+            const double* rp = wbuf ? rb + 32 * threadIdx.x : red[threadIdx.x];
+            double v = 0.0;
+            for (int w = 0; w < nw; ++w) v += rp[w];
+            const int t = threadIdx.x >> 1;
+            S.mpart[2 * ((size_t)t * S.nbx + bx) + (threadIdx.x & 1)] = v;
+        }
+        if (wbuf) __syncthreads();  // the transform overwrites the second tile buffer
     }
     cx<R>* res = tile_fft<R, PRUNE<R> ? HALF_IN : HALF_NONE>(a, b, S.lgN1, GT, m.twP, false);
     cx<R>* Yall = reinterpret_cast<cx<R>*>(S.Y);
@@ -757,7 +787,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
 
 // Kernel A: the forward pass of one evaluation.
 template <typename R>
-__global__ void __launch_bounds__(256) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(COL_THREADS_MAX) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                   const __grid_constant__ SysDev one, const StageIn in) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
@@ -1157,7 +1187,7 @@ __device__ __forceinline__ void rescale_k1(const SysDev& S, const CtlView& cv, c
 // Kernel C: the inverse pass of one evaluation.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(COL_THREADS_MAX) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                   const __grid_constant__ SysDev one, const StageIn in,
                                                   const EpiOut eo) {
     __shared__ __align__(16) SysDev S;
@@ -1182,7 +1212,7 @@ __global__ void __launch_bounds__(256) k_inv_cols(const SysDev* __restrict__ sys
 // k of this stage at its elements goes on to form the next stage input there.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(256) k_inv_fwd(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(COL_THREADS_MAX) k_inv_fwd(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                  const __grid_constant__ SysDev one, const StageIn in,
                                                  const EpiOut eo, const StageIn nx) {
     __shared__ __align__(16) SysDev S;

@@ -226,6 +226,31 @@ def test_launch_modes_do_not_change_results(smol, precision, scheme):
     assert np.linalg.norm(a[0] - b[0]) <= tol * np.linalg.norm(b[0])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32conv", "df64"])
+def test_wide_column_ctas_match_default(smol, precision):
+    """SMOL_FLAG_WIDE_COLS (512-thread column CTAs on a schedule with 512 element pairs a
+    tile, ragged M) only changes the order of block sums: the right-hand side and the
+    trajectory agree with the default launch to rounding, with the same decisions."""
+    import torch
+    M = 100000
+    U, V = kernel_factors("brownian", M, a=0.9)
+    n0 = torch.from_numpy(sample_state(M, 0.01)).cuda()
+    sched = dict(fft_lgn1=8, fft_g=4)
+    out = {}
+    for flags in (0, smol.FLAG_WIDE_COLS, smol.FLAG_WIDE_COLS | smol.FLAG_NO_FUSE):
+        s = smol.System(U, V, 0.005, precision=precision, tau0=1e-5, flags=flags, **sched)
+        r = s.rhs(n0).cpu().numpy()
+        n, st = s.integrate(n0, 0.0, 2e-3, 1e-8, scheme="rkf45")
+        assert st["status"] == 0
+        out[flags] = (r, n.cpu().numpy(), st["accepted"], st["rejected"])
+    tol = {"fp64": 1e-12, "df64": 1e-12, "fp32conv": 1e-6}[precision]
+    base = out[0]
+    for flags, got in out.items():
+        assert got[2:] == base[2:], (flags, got[2:], base[2:])
+        assert np.linalg.norm(got[0] - base[0]) <= tol * np.linalg.norm(base[0]), flags
+        assert np.linalg.norm(got[1] - base[1]) <= tol * np.linalg.norm(base[1]), flags
+
+
 def test_tune_picks_a_valid_schedule(smol):
     """smol_tune returns one of its candidates, and the tuned system follows the
     default one's constant-step trajectory to rounding."""
@@ -237,7 +262,8 @@ def test_tune_picks_a_valid_schedule(smol):
     assert us > 0.0
     assert sched["fft_lgn1"] in (5, 6, 7) and sched["fft_g"] in (2, 4, 8, 16, 32)
     assert sched["flags"] in (0, smol.FLAG_NO_PDL, smol.FLAG_NO_PDL_FWD_COLS, smol.FLAG_NO_FUSE,
-                              smol.FLAG_NO_FUSE | smol.FLAG_NO_PDL, smol.FLAG_PERSISTENT)
+                              smol.FLAG_NO_FUSE | smol.FLAG_NO_PDL, smol.FLAG_PERSISTENT,
+                              smol.FLAG_WIDE_COLS | smol.FLAG_NO_PDL, smol.FLAG_WIDE_COLS | smol.FLAG_NO_PDL_FWD_COLS)
     a, _ = smol.System(U, V, 0.01, fixed_tau=0.01, **sched).integrate(n0, 0.0, 1.0, 1e-8)
     b, _ = smol.System(U, V, 0.01, fixed_tau=0.01).integrate(n0, 0.0, 1.0, 1e-8)
     a, b = a.cpu().numpy(), b.cpu().numpy()
