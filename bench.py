@@ -519,6 +519,13 @@ def live_peaks(smol, stream) -> dict:
         except Exception as e:  # reported, and the FP64 roofline falls back to the derived figure
             out[key] = None
             out[key.replace("tflops", "error")] = str(e)
+    # dependent-chain latencies (SM cycles per operation, one warp; FP64 FMA also with 8)
+    try:
+        lat = {op: round(smol.op_latency(op, 1, stream=stream), 1) for op in smol.OP_LATENCY_OPS}
+        lat["dfma_8warps"] = round(smol.op_latency("dfma", 8, stream=stream), 1)
+        out["latency_cycles"] = lat
+    except Exception as e:
+        out["latency_error"] = str(e)
     return out
 
 

@@ -264,6 +264,14 @@ int smol_profile_attempts(smol_system* sys, int32_t reps, double* kernel_ms, int
  * timed kernel's duration. Synchronises the stream. SMOL_EINVAL or SMOL_ECUDA on error. */
 int smol_fma_rate(int32_t precision, int64_t iters, void* stream, double* tflops, double* ms);
 
+/* Measurement aid: SM clock cycles per operation of a chain of dependent operations op
+ * (0: FP64 fused multiply-add, 1: FP64 add, 2: FP32 fused multiply-add, 3: FP32 -> FP64
+ * conversion plus an FP64 multiply), run by `warps` (1..32) warps of one CTA at once, as
+ * warp 0 times it with clock64. With one warp this is the operation's latency; with
+ * several, the FP64 pipe's throughput shows once they contend. Synchronises `stream`.
+ * SMOL_EINVAL or SMOL_ECUDA on error. */
+int smol_op_latency(int32_t op, int32_t warps, void* stream, double* cycles);
+
 /* Constant point sources of Eq. (3): dn_s/dt = S_s(n) + P_s at up to SMOL_MAX_SOURCES
  * sizes (Sec. 3.1 injects P_1 = 1 and P_100 = p). With lambda = 0 the system is Eq. (3);
  * with lambda > 0 the sources are added to Eq. (4). sizes are 1-based (1..M), values

@@ -94,6 +94,7 @@ SIGNATURES = {
     "smol_batch_set_sources": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
     "smol_set_tau0": (ctypes.c_int, [_P, _D]),
     "smol_fma_rate": (ctypes.c_int, [_I32, _I64, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "smol_op_latency": (ctypes.c_int, [_I32, _I32, _P, ctypes.POINTER(_D)]),
     "smol_max_m_transforms": (_I64, [_I32, _I32]),
     "smol_lowrank_kernel": (ctypes.c_int, [_I32, _P, _I64, _D, _I32, _P, _P, ctypes.POINTER(_I32),
                                            ctypes.POINTER(_D)]),
@@ -189,6 +190,21 @@ def fma_rate(precision: str = "fp64", iters: int = 20000, stream=None):
     _check(_lib.smol_fma_rate(PRECISIONS[precision], int(iters), ctypes.c_void_p(stream.cuda_stream),
                               ctypes.byref(tf), ctypes.byref(ms)), "smol_fma_rate")
     return tf.value, ms.value
+
+
+OP_LATENCY_OPS = {"dfma": 0, "dadd": 1, "ffma": 2, "f2f_dmul": 3}
+
+
+def op_latency(op: str, warps: int = 1, stream=None) -> float:
+    """smol_op_latency: SM cycles per operation of a dependent chain of `op` ('dfma',
+    'dadd', 'ffma', 'f2f_dmul') run by `warps` warps of one CTA."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    c = ctypes.c_double()
+    _check(_lib.smol_op_latency(OP_LATENCY_OPS[op], int(warps), ctypes.c_void_p(stream.cuda_stream),
+                                ctypes.byref(c)), "smol_op_latency")
+    return c.value
 
 
 def tune(U, V, lam: float, n0, tol: float, scheme: str = "rkf45", precision: str = "fp64", attempts: int = 64,

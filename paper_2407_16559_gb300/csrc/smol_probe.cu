@@ -2,7 +2,8 @@
 // kernels are measured against. The FP64 form's transforms are bound by the FP64 pipe,
 // whose rate on this part is a small fraction of its FP32 rate, so its roofline needs a
 // measured FP64 peak rather than a datasheet figure; the FP32 rate serves the FP32 and
-// double-float forms. Measurement aid only: nothing on the solver's path calls it.
+// double-float forms. smol_op_latency gives the dependent-chain latencies behind the
+// kernels' FP64 costs. Measurement aids only: nothing on the solver's path calls them.
 #include <cuda_runtime.h>
 
 #include "../../include/smol.h"
@@ -64,7 +65,56 @@ int run(long long iters, cudaStream_t st, double* tflops, double* ms_out) {
     return SMOL_OK;
 }
 
+// Dependent-chain latency: `warps` warps of one CTA each run one chain of `iters`
+// dependent operations OP (0: FP64 fused multiply-add, 1: FP64 add, 2: FP32 fused
+// multiply-add, 3: FP32 -> FP64 conversion followed by an FP64 multiply); warp 0 lane 0
+// times its chain with clock64 and writes cycles per operation to *out. Stored only if
+// the chain ends on a value it cannot reach, so the compiler keeps every step.
+template <int OP>
+__global__ void k_chain(double a, double b, int iters, double never, double* sink, double* out) {
+    double x = a + (double)threadIdx.x * 1e-9;
+    float xf = (float)a;
+    __syncwarp();
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; ++i) {
+        if (OP == 0) x = fma(x, b, 1e-3);
+        else if (OP == 1) x = x + b;
+        else if (OP == 2) xf = fmaf(xf, (float)b, 1e-3f);
+        else x = (double)(float)x * b;
+    }
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) *out = (double)(t1 - t0) / (double)iters;
+    if (x + (double)xf == never && sink != nullptr) sink[threadIdx.x] = x;
+}
+
+template <int OP>
+int chain(int warps, cudaStream_t st, double* cycles) {
+    double* d = nullptr;
+    if (cudaMalloc(&d, sizeof(double)) != cudaSuccess) return SMOL_ECUDA;
+    const double b = OP == 1 ? 1e-9 : (OP == 3 ? 1.0000001 : 0.999);
+    k_chain<OP><<<1, 32 * warps, 0, st>>>(0.5, b, 64, -1.0, nullptr, d);  // warm-up
+    k_chain<OP><<<1, 32 * warps, 0, st>>>(0.5, b, 4096, -1.0, nullptr, d);
+    int rc = SMOL_OK;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(cycles, d, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = SMOL_ECUDA;
+    cudaFree(d);
+    return rc;
+}
+
 }  // namespace
+
+extern "C" int smol_op_latency(int32_t op, int32_t warps, void* stream, double* cycles) {
+    if (!cycles || warps < 1 || warps > 32) return SMOL_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (op) {
+        case 0: return chain<0>(warps, st, cycles);
+        case 1: return chain<1>(warps, st, cycles);
+        case 2: return chain<2>(warps, st, cycles);
+        case 3: return chain<3>(warps, st, cycles);
+        default: return SMOL_EINVAL;
+    }
+}
 
 extern "C" int smol_fma_rate(int32_t precision, int64_t iters, void* stream, double* tflops, double* ms) {
     if (!tflops || iters < 1) return SMOL_EINVAL;
