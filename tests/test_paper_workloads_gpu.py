@@ -103,7 +103,7 @@ def test_config4_reduced_precision_trajectories(smol):
     """The relaxation workload (M = 2^16, Brownian 1/3 + constant 2, lambda = 0.1, RKF45,
     tol 1e-9) in the FP32 form and in the double-float form against the FP64 solver at
     log-spaced checkpoints: the double-float form follows the FP64 trajectory to the
-    tolerance's level with the same amount of work; the FP32 form stays within 1e-4 with
+    tolerance's level (10 tol) with the same amount of work; the FP32 form stays within 1e-4 with
     at most 1.5 times the attempts (its transform inputs are exponentially tilted, so
     the FP32 rounding no longer fills the near-empty tail)."""
     import torch
@@ -125,8 +125,12 @@ def test_config4_reduced_precision_trajectories(smol):
     ts = np.logspace(-1, 2, 10)
     ref, att64 = run("fp64", ts)
     dd, attdd = run("df64", ts)
+    # within 10 tol (absolute norm, as for the oracle checkpoints): where a step's error
+    # sits at the accept bound, the two forms' roundings can decide it differently, and
+    # from there the step sequences part by accepted steps whose local errors are each
+    # at most tol (a few tol apart at most; 1.3 tol seen at t = 21.5)
     for a, b in zip(dd, ref):
-        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
+        assert np.linalg.norm(a - b) <= 10 * 1e-9
     assert abs(attdd - att64) <= 0.15 * att64  # near-boundary decisions round differently
     # Near steady state the controller lengthens the step up to the explicit scheme's
     # stability bound, set by the largest loss rates (1 + lambda) D_s, those of the top
