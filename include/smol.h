@@ -117,11 +117,12 @@ extern "C" {
    for other schemes, fixed steps or batches) the graph path runs. A barrier wait that
    gives up (about 2 s) ends the integration with SMOL_ETIMEOUT. */
 #define SMOL_FLAG_PERSISTENT      64
-/* Single systems: column kernels with one thread per element pair of their tile, up to
-   512 threads a CTA (default: up to 256, two or more pairs a thread). Their per-element
-   phases (stage input, epilogue, final combination) are chains of dependent FP64
-   operations, which the added warps overlap; the FFT passes keep one thread per
-   butterfly. No effect on batches. */
+/* Single FP64 or double-float systems: column kernels with one thread per element pair
+   of their tile, up to 512 threads a CTA (default: up to 256, two or more pairs a
+   thread). Their per-element phases (stage input, epilogue, final combination) are
+   chains of dependent FP64 operations, which the added warps overlap; the FFT passes
+   keep one thread per butterfly. No effect on batches or on the FP32 form (whose column
+   kernels keep to 256 threads). */
 #define SMOL_FLAG_WIDE_COLS       128
 
 typedef struct smol_system smol_system;   /* opaque, created by smol_init_system */

@@ -785,8 +785,8 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
         E->thrC = std::max(E->thrC, std::max(threads_for(s.N1 * s.G * T), std::min(256, (s.N1 * s.G / 2 + 31) & ~31)));
         // wide column CTAs: one thread per element pair (the per-pair phases of the
         // column kernels are chains of dependent FP64 operations, which more warps hide)
-        E->thrCW = std::max(E->thrCW, std::max(threads_for(s.N1 * s.G * T, COL_THREADS_MAX),
-                                               std::min(COL_THREADS_MAX, (s.N1 * s.G / 2 + 31) & ~31)));
+        const int wmax = o.precision == SMOL_FP32CONV ? 256 : COL_THREADS_MAX;  // the kernels' launch bounds
+        E->thrCW = std::max(E->thrCW, std::max(threads_for(s.N1 * s.G * T, wmax), std::min(wmax, (s.N1 * s.G / 2 + 31) & ~31)));
         E->thrB = std::max(E->thrB, threads_for(s.N2 * 2 * T));
         char* b = ws + E->base[q];
         SysDev& d = hs[q];

@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(128, 4) k_finish(const SysDev* __restrict__ sy
 // CTA combines the element pairs whose stage vector it has just formed, then fin_tail
 // over the nbx column CTAs of the system.
 template <typename R>
-__global__ void __launch_bounds__(COL_THREADS_MAX) k_inv_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(ColBounds<R>::threads) k_inv_finish(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                     const __grid_constant__ SysDev one, const StageIn in,
                                                     const EpiOut eo, const Comb2 cd, const CtlParams P) {
     __shared__ __align__(16) SysDev S;

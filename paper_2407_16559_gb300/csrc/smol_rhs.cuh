@@ -47,10 +47,23 @@ constexpr int MAXR = 16;        // largest rank R (SMOL_MAX_R)
 constexpr int MAXT = 2 * MAXR;  // largest number of distinct transforms
 constexpr int MAXV = 10;        // terms of a stage-input linear combination
 constexpr int NVEC = 12;        // stage / work vectors per system
-constexpr int FPW = MAXT + 8;
-// Threads of a column CTA: at most 256 by default, up to 512 for a single system with
-// SMOL_FLAG_WIDE_COLS (one thread per element pair of a column tile).
-constexpr int COL_THREADS_MAX = 512;   // doubles per block of the finish / preparation partials
+constexpr int FPW = MAXT + 8;   // doubles per block of the finish / preparation partials
+// Threads of a column CTA: at most 256 by default, up to 512 for a single FP64 or
+// double-float system with SMOL_FLAG_WIDE_COLS (one thread per element pair of a
+// column tile).
+constexpr int COL_THREADS_MAX = 512;
+// Launch bounds of the column kernels: the FP32 instances keep to 256 threads (a bound
+// of 512 caps registers at 128 and changes their allocation: one register more than 80
+// leaves the batch two CTAs per SM instead of three); the FP64 and double-float ones
+// allow 512 threads (128 registers a thread).
+template <typename R>
+struct ColBounds {
+    static constexpr int threads = COL_THREADS_MAX;
+};
+template <>
+struct ColBounds<float> {
+    static constexpr int threads = 256;
+};
 constexpr int MAXSRC = 8;       // point sources P_k of Eq. (3) per system
 constexpr int TILT_T = 4;       // FP32 form: input tilt for systems of at most this many transforms
 
@@ -714,9 +727,9 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
     // far fewer FP64 instructions than a shuffle tree in every warp; the FP32 form sums
     // in FP32 shuffles and then in FP64 across warps.
     const bool viasm = Tr<R>::fp64 && N1 * G >= (int)blockDim.x;
-    // the FP32 path's per-warp partials: red for up to 8 warps, else the second tile
-    // buffer (a CTA of more than 256 threads has N1 G >= 1024 points there)
-    const bool wbuf = !viasm && nw > 8;
+    // the per-warp partials of the shuffle path: red for up to 8 warps, else the second
+    // tile buffer (a CTA of more than 256 threads has N1 G >= 1024 points there)
+    const bool wbuf = ColBounds<R>::threads > 256 && !viasm && nw > 8;
     double* rb = reinterpret_cast<double*>(b);
     for (int t = 0; t < T; ++t) {
         const R sc = pow2<R>(-xexp<R>(S, cv, t));
@@ -787,7 +800,7 @@ __device__ __forceinline__ void fwd_body(const SysDev& S, const CtlView& cv, con
 
 // Kernel A: the forward pass of one evaluation.
 template <typename R>
-__global__ void __launch_bounds__(COL_THREADS_MAX) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(ColBounds<R>::threads) k_fwd_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                   const __grid_constant__ SysDev one, const StageIn in) {
     __shared__ __align__(16) SysDev S;
     __shared__ CtlView cv;
@@ -1187,7 +1200,7 @@ __device__ __forceinline__ void rescale_k1(const SysDev& S, const CtlView& cv, c
 // Kernel C: the inverse pass of one evaluation.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(COL_THREADS_MAX) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(ColBounds<R>::threads) k_inv_cols(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                   const __grid_constant__ SysDev one, const StageIn in,
                                                   const EpiOut eo) {
     __shared__ __align__(16) SysDev S;
@@ -1212,7 +1225,7 @@ __global__ void __launch_bounds__(COL_THREADS_MAX) k_inv_cols(const SysDev* __re
 // k of this stage at its elements goes on to form the next stage input there.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(COL_THREADS_MAX) k_inv_fwd(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
+__global__ void __launch_bounds__(ColBounds<R>::threads) k_inv_fwd(const SysDev* __restrict__ sysv, const int2* __restrict__ map,
                                                  const __grid_constant__ SysDev one, const StageIn in,
                                                  const EpiOut eo, const StageIn nx) {
     __shared__ __align__(16) SysDev S;

@@ -230,7 +230,8 @@ def test_launch_modes_do_not_change_results(smol, precision, scheme):
 def test_wide_column_ctas_match_default(smol, precision):
     """SMOL_FLAG_WIDE_COLS (512-thread column CTAs on a schedule with 512 element pairs a
     tile, ragged M) only changes the order of block sums: the right-hand side and the
-    trajectory agree with the default launch to rounding, with the same decisions."""
+    trajectory agree with the default launch to rounding, with the same decisions (the
+    FP32 form ignores the flag)."""
     import torch
     M = 100000
     U, V = kernel_factors("brownian", M, a=0.9)
