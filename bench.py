@@ -78,11 +78,11 @@ TRAFFIC = {
     # (precision, kernel class, log2 N1 of the benched schedule): dram read + write per
     # launch from the ncu captures summarised in profiles/ (k_inv_fwd_M131072_*.md,
     # k_rows_M131072_*.md); used only while the kernel sources are the captured ones
-    ("fp64", "inv_fwd", 9): {"bytes": 6413056.0, "src": "d3c0f65546876c53"},
-    ("fp64", "rows", 9): {"bytes": 8491008.0, "src": "d3c0f65546876c53"},
-    ("fp32conv", "inv_fwd", 8): {"bytes": 3231744.0, "src": "d3c0f65546876c53"},
-    ("fp32conv", "rows", 8): {"bytes": 4297728.0, "src": "d3c0f65546876c53"},
-    ("df64", "inv_fwd", 8): {"bytes": 6428416.0, "src": "d3c0f65546876c53"},
+    ("fp64", "inv_fwd", 9): {"bytes": 6413312.0, "src": "ca09e2bab01141bd"},
+    ("fp64", "rows", 9): {"bytes": 8490752.0, "src": "ca09e2bab01141bd"},
+    ("fp32conv", "inv_fwd", 8): {"bytes": 3230464.0, "src": "ca09e2bab01141bd"},
+    ("fp32conv", "rows", 8): {"bytes": 4297728.0, "src": "ca09e2bab01141bd"},
+    ("df64", "inv_fwd", 8): {"bytes": 6428416.0, "src": "ca09e2bab01141bd"},
 }
 
 
