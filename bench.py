@@ -78,11 +78,11 @@ TRAFFIC = {
     # (precision, kernel class, log2 N1 of the benched schedule): dram read + write per
     # launch from the ncu captures summarised in profiles/ (k_inv_fwd_M131072_*.md,
     # k_rows_M131072_*.md); used only while the kernel sources are the captured ones
-    ("fp64", "inv_fwd", 9): {"bytes": 6413312.0, "src": "ca09e2bab01141bd"},
-    ("fp64", "rows", 9): {"bytes": 8490752.0, "src": "ca09e2bab01141bd"},
-    ("fp32conv", "inv_fwd", 8): {"bytes": 3230464.0, "src": "ca09e2bab01141bd"},
-    ("fp32conv", "rows", 8): {"bytes": 4297728.0, "src": "ca09e2bab01141bd"},
-    ("df64", "inv_fwd", 8): {"bytes": 6428416.0, "src": "ca09e2bab01141bd"},
+    ("fp64", "inv_fwd", 9): {"bytes": 6413312.0, "src": "8e644209d26c520a"},
+    ("fp64", "rows", 9): {"bytes": 8491264.0, "src": "8e644209d26c520a"},
+    ("fp32conv", "inv_fwd", 8): {"bytes": 3231744.0, "src": "8e644209d26c520a"},
+    ("fp32conv", "rows", 8): {"bytes": 4298240.0, "src": "8e644209d26c520a"},
+    ("df64", "inv_fwd", 8): {"bytes": 6430720.0, "src": "8e644209d26c520a"},
 }
 
 
@@ -554,7 +554,7 @@ def gpu_arm(args):
         torch.cuda.synchronize()
 
     if args.only_batch:
-        msb, stb, Ms, _ = time_batch(smol, torch, "fp32conv", K, W, stream, flush, args.batch,
+        msb, stb, Ms, _, _ = time_batch(smol, torch, "fp32conv", K, W, stream, flush, args.batch,
                                      tune=not args.no_tune)
         if rank == 0:
             print(json.dumps({"batch_ms_per_step": msb / K, "systems": args.batch, "steps": K}))
@@ -627,8 +627,8 @@ def gpu_arm(args):
         res = {}
         for form in forms:
             barrier()
-            msb, stb, Ms, bflags = time_batch(smol, torch, form, Kb, W, stream, flush, args.batch,
-                                              tune=not args.no_tune, shard=shard)
+            msb, stb, Ms, bflags, bsched = time_batch(smol, torch, form, Kb, W, stream, flush, args.batch,
+                                                      tune=not args.no_tune, shard=shard)
             if dist is not None:
                 t = torch.tensor([msb], dtype=torch.float64, device="cuda")
                 dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -638,6 +638,7 @@ def gpu_arm(args):
             acc = sum(x["accepted"] for x in stb) if stb else 0
             res[form] = {"ms_per_step": msb / Kb, "rhs_evals_per_s": evb / (msb / 1000.0),
                          "accepted_steps_per_s": acc / (msb / 1000.0), "launch_flags": bflags,
+                         "schedules": bsched or "rule",
                          "attempt_hbm": attempt_hbm(form, 2, elements, msb / Kb)}
         b = dict(res["fp32conv"], systems=args.batch, precision="fp32conv", steps=Kb,
                  scaling="strong" if world > 1 else "n/a", elements=int(sum(r["M"] for r in rec)),
@@ -802,7 +803,11 @@ def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count
         Vs.append(V)
         lams.append(r["lam"])
         n0s.append(torch.from_numpy(monodisperse(r["M"])).cuda())
-    b = smol.Batch(Us, Vs, lams, precision=precision, stream=stream, tau0=1e-3, chunk=1)
+    tables = {}
+    if tune:  # FFT schedules per size class, then the launch mode (untimed set-up)
+        tables, _ = smol.batch_tune_schedules(Us, Vs, lams, n0s, 1e-8, attempts=4, precision=precision,
+                                              stream=stream, tau0=1e-3, chunk=1)
+    b = smol.Batch(Us, Vs, lams, precision=precision, stream=stream, tau0=1e-3, chunk=1, **tables)
     flags = b.tune(n0s, 1e-8, attempts=8)[0] if tune else 0
     b.start(n0s, 0.0, 1000.0, 1e-8, scheme="rkf45")
     for _ in range(W):
@@ -821,7 +826,9 @@ def time_batch(smol, torch, precision: str, K: int, W: int, stream, flush, count
     # per system: the counters of the K timed attempts
     stats = [{k: x[k] - y[k] for k in ("rhs_evals", "accepted", "rejected", "attempts")} for x, y in zip(stats, stw)]
     Ms = [r["M"] for r in rec]
-    return ms, stats, Ms, flags
+    sched = {str(1 << k): [int(tables["batch_lgn1"][k]), int(tables["batch_g"][k])]
+             for k in range(len(tables.get("batch_lgn1", []))) if tables["batch_lgn1"][k] or tables["batch_g"][k]}
+    return ms, stats, Ms, flags, sched
 
 
 def rhs_accuracy(smol, torch, U, V, precision: str = "fp32conv"):

@@ -125,6 +125,10 @@ extern "C" {
    kernels keep to 256 threads). */
 #define SMOL_FLAG_WIDE_COLS       128
 
+/* Size classes of the per-size FFT schedules of a batch (smol_opts.batch_lgn1 / batch_g):
+   class k holds the systems with FFT size Mp = 2^k. */
+#define SMOL_SIZE_CLASSES 24
+
 typedef struct smol_system smol_system;   /* opaque, created by smol_init_system */
 
 typedef struct smol_opts {
@@ -143,9 +147,14 @@ typedef struct smol_opts {
     int32_t chunk;          /* step attempts per CUDA-graph launch; default 32 */
     int32_t flags;          /* SMOL_FLAG_* bits; 0 = defaults */
     void*   stream;         /* cudaStream_t; NULL = legacy default stream */
-    /* FFT schedule of a single system (a batch uses the rule): 0 = the rule. */
+    /* FFT schedule of a single system: 0 = the rule. */
     int32_t fft_lgn1;       /* log2 N1 of Mp = N1 N2 (column length), 1 <= fft_lgn1 < log2 Mp */
     int32_t fft_g;          /* columns per CTA of the column kernels, a power of two <= 64 */
+    /* FFT schedules of a batch's systems by size class: entry k serves the systems whose
+       FFT size is Mp = 2^k (the same meanings as fft_lgn1 and fft_g; 0 = the rule;
+       smol_batch_tune_schedules fills them). */
+    int8_t  batch_lgn1[SMOL_SIZE_CLASSES];
+    int8_t  batch_g[SMOL_SIZE_CLASSES];
 } smol_opts;
 
 typedef struct smol_stats {
@@ -371,6 +380,24 @@ int smol_partition(int32_t count, const int64_t* M, const double* weight, int32_
 
 int smol_batch_tune(smol_batch* batch, double* const* d_n, double tol, int32_t scheme,
                     int32_t attempts, int32_t* flags, double* us_per_attempt);
+
+/* FFT schedules per size class for a batch: smol_tune's search applied to the batched
+ * form (Sec. 3 integrates each system on its own; each keeps the FFT route of Sec. 1,
+ * only the split Mp = N1 N2 and the columns per CTA change). Coordinate descent over the size
+ * classes present, the class holding the most sizes first: for each, the candidates
+ * log2 N1 = rule - 1, rule, rule + 1 with 1, 2 and 4 times the rule's columns per CTA
+ * are timed on the whole batch (`attempts` attempts from the states d_n0 on scratch
+ * copies; nothing of the caller's changes), with the other classes at their best so
+ * far. The arguments are those of smol_batch_workspace_bytes / smol_batch_init plus the
+ * states; *opts gives the precision, launch flags and starting tables, and receives the
+ * chosen batch_lgn1 / batch_g (its other fields unchanged). The caller then sizes and
+ * initialises the batch with *opts. Allocates and frees its own scratch (workspaces and
+ * state copies). *us_per_attempt (may be NULL): the time of an attempt of the whole
+ * batch with the chosen tables. SMOL_EINVAL, SMOL_EUNSUPPORTED or SMOL_ECUDA. */
+int smol_batch_tune_schedules(int32_t count, const int64_t* M, int32_t R, const double* const* h_U,
+                              const double* const* h_V, const double* lambda, double* const* d_n0,
+                              double tol, int32_t scheme, int32_t attempts, smol_opts* opts,
+                              double* us_per_attempt);
 int smol_batch_get_log(smol_batch* batch, int32_t system, double* h_t, double* h_tau,
                        double* h_err, int32_t* h_accepted, int32_t cap, int64_t* count);
 void smol_batch_destroy(smol_batch* batch);

@@ -41,7 +41,11 @@ class Opts(ctypes.Structure):
         ("fac_min", ctypes.c_double), ("fac_max", ctypes.c_double), ("max_attempts", ctypes.c_int64),
         ("chunk", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("fft_lgn1", ctypes.c_int32), ("fft_g", ctypes.c_int32),
+        ("batch_lgn1", ctypes.c_int8 * 24), ("batch_g", ctypes.c_int8 * 24),
     ]
+
+
+SIZE_CLASSES = 24  # SMOL_SIZE_CLASSES: batch_lgn1 / batch_g entry k serves Mp = 2^k
 
 
 class Stats(ctypes.Structure):
@@ -99,6 +103,8 @@ SIGNATURES = {
     "smol_lowrank_kernel": (ctypes.c_int, [_I32, _P, _I64, _D, _I32, _P, _P, ctypes.POINTER(_I32),
                                            ctypes.POINTER(_D)]),
     "smol_batch_set_tau0": (ctypes.c_int, [_P, _P]),
+    "smol_batch_tune_schedules": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P, _P, _D, _I32, _I32, _P,
+                                                 ctypes.POINTER(_D)]),
 }
 
 # option flags (smol_opts.flags)
@@ -282,12 +288,41 @@ def _make_opts(precision: str, stream, device, opts: dict):
             v = NORMS[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k!r}")
+        if k in ("batch_lgn1", "batch_g"):
+            vals = [int(x) for x in v]
+            if len(vals) > SIZE_CLASSES:
+                raise ValueError(f"{k}: at most {SIZE_CLASSES} entries")
+            v = (ctypes.c_int8 * SIZE_CLASSES)(*(vals + [0] * (SIZE_CLASSES - len(vals))))
         setattr(o, k, v)
     dev = torch.device(device if device is not None else "cuda")
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     o.stream = ctypes.c_void_p(stream.cuda_stream)
     return o, dev, stream
+
+
+def batch_tune_schedules(Us, Vs, lams, n0s, tol: float, scheme: str = "rkf45", attempts: int = 8,
+                         precision: str = "fp64", stream=None, device=None, **opts):
+    """smol_batch_tune_schedules: FFT schedules per size class for the batch (Us, Vs,
+    lams) from the states n0s (device tensors or arrays); returns ({'batch_lgn1': [...],
+    'batch_g': [...]}, microseconds per attempt of the whole batch). Pass the dict as
+    options to Batch."""
+    torch = _torch()
+    U = [np.ascontiguousarray(u, dtype=np.float64) for u in Us]
+    V = [np.ascontiguousarray(v, dtype=np.float64) for v in Vs]
+    count, R = len(U), U[0].shape[1]
+    M = np.array([u.shape[0] for u in U], dtype=np.int64)
+    lam = np.ascontiguousarray(lams, dtype=np.float64)
+    o, dev, _ = _make_opts(precision, stream, device, opts)
+    ns = [torch.as_tensor(n).to(device=dev, dtype=torch.float64).contiguous() for n in n0s]
+    pU = (ctypes.c_void_p * count)(*[u.ctypes.data for u in U])
+    pV = (ctypes.c_void_p * count)(*[v.ctypes.data for v in V])
+    pn = (ctypes.c_void_p * count)(*[n.data_ptr() for n in ns])
+    us = ctypes.c_double()
+    _check(_lib.smol_batch_tune_schedules(count, M.ctypes.data, R, pU, pV, lam.ctypes.data, pn, float(tol),
+                                          SCHEMES[scheme], int(attempts), ctypes.byref(o), ctypes.byref(us)),
+           "smol_batch_tune_schedules")
+    return {"batch_lgn1": list(o.batch_lgn1), "batch_g": list(o.batch_g)}, us.value
 
 
 class Batch:

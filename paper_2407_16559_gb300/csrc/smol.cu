@@ -73,6 +73,16 @@ Shape make_shape(int64_t M, int precision, bool wide = false, int lgn1 = 0, int 
     return s;
 }
 
+// Shape of system q of an engine of `count` systems: a single system takes fft_lgn1 /
+// fft_g, a batch its size class's entry of batch_lgn1 / batch_g (0: the rule).
+Shape engine_shape(int count, int64_t M, const smol_opts& o, bool wide) {
+    if (count == 1) return make_shape(M, o.precision, false, o.fft_lgn1, o.fft_g);
+    const int k = ilog2(M < 4 ? 4 : M);
+    const int lg = k < SMOL_SIZE_CLASSES ? o.batch_lgn1[k] : 0;
+    const int g = k < SMOL_SIZE_CLASSES ? o.batch_g[k] : 0;
+    return make_shape(M, o.precision, wide, lg, g);
+}
+
 // Dynamic shared memory of the column kernels (the larger of the forward pass: T*G
 // interleaved sequences, tile and four-step twiddles, y; and the inverse pass) and of
 // the row kernel (2T rows, tile twiddles, spectral and inverse four-step twiddles).
@@ -243,8 +253,7 @@ size_t batch_bytes(int count, const int64_t* M, int R, const smol_opts& o) {
     const bool wide = is_wide(count, M);
     for (int q = 0; q < count; ++q) {
         if (M[q] < 1 || M[q] > mm) return 0;
-        sh.push_back(count == 1 ? make_shape(M[q], o.precision, false, o.fft_lgn1, o.fft_g)
-                                : make_shape(M[q], o.precision, wide));
+        sh.push_back(engine_shape(count, M[q], o, wide));
         tot += make_layout(sh.back(), R, std::max(o.log_capacity, 0)).total;
     }
     return make_header(sh).total + tot;
@@ -706,8 +715,7 @@ int engine_init(Engine* E, int count, const int64_t* Ms, int R, const double* co
     const int logc = std::max(o.log_capacity, 0);
     const bool wide = is_wide(count, Ms);
     for (int q = 0; q < count; ++q) {
-        E->sh.push_back(count == 1 ? make_shape(Ms[q], prec, false, o.fft_lgn1, o.fft_g)
-                                   : make_shape(Ms[q], prec, wide));
+        E->sh.push_back(engine_shape(count, Ms[q], o, wide));
         E->lay.push_back(make_layout(E->sh.back(), R, logc));
     }
     E->H = make_header(E->sh);
@@ -976,6 +984,10 @@ int check_opts(const smol_opts& o) {
     if (o.log_capacity < 0 || o.chunk < 0) return SMOL_EINVAL;
     if (o.fft_lgn1 < 0 || o.fft_lgn1 > 30 || o.fft_g < 0 || o.fft_g > 64 || (o.fft_g & (o.fft_g - 1)))
         return SMOL_EINVAL;
+    for (int k = 0; k < SMOL_SIZE_CLASSES; ++k) {
+        const int lg = o.batch_lgn1[k], g = o.batch_g[k];
+        if (lg < 0 || lg > 30 || g < 0 || g > 64 || (g & (g - 1))) return SMOL_EINVAL;
+    }
     return SMOL_OK;
 }
 
@@ -1652,6 +1664,97 @@ int smol_batch_tune(smol_batch* B, double* const* d_n, double tol, int32_t schem
     if (rc == SMOL_OK && best < 0.0) rc = SMOL_ECUDA;
     if (rc != SMOL_OK) return rc;
     if (flags) *flags = bf;
+    if (us_per_attempt) *us_per_attempt = best;
+    return SMOL_OK;
+}
+
+int smol_batch_tune_schedules(int32_t count, const int64_t* M, int32_t R, const double* const* h_U,
+                              const double* const* h_V, const double* lambda, double* const* d_n0, double tol,
+                              int32_t scheme, int32_t attempts, smol_opts* opts, double* us_per_attempt) {
+    if (!M || !h_U || !h_V || !lambda || !d_n0 || !opts || count < 1 || count > MAX_BATCH || R < 1 || R > MAXR ||
+        attempts < 1 || scheme < SMOL_RK2 || scheme > SMOL_RKF45 || !(tol > 0.0))
+        return SMOL_EINVAL;
+    smol_opts base = *opts;
+    int rc = check_opts(base);
+    if (rc != SMOL_OK) return rc;
+    const int64_t mm = max_m_transforms(1, base.precision);
+    for (int q = 0; q < count; ++q) {
+        if (M[q] < 1 || !d_n0[q] || ((uintptr_t)d_n0[q] & 15)) return SMOL_EINVAL;
+        if (M[q] > mm) return SMOL_EUNSUPPORTED;
+    }
+    base.max_attempts = (int64_t)1 << 62;
+    base.fixed_tau = 0.0;
+    std::vector<double*> work(count, nullptr);
+    for (int q = 0; q < count && rc == SMOL_OK; ++q)
+        if (cudaMalloc((void**)&work[q], (size_t)M[q] * 8) != cudaSuccess) rc = SMOL_ECUDA;
+    // one whole-batch timing of the options c (-1 where it does not fit or fails)
+    auto timeit = [&](const smol_opts& c) -> double {
+        const size_t bytes = batch_bytes(count, M, R, c);
+        if (bytes == 0) return -1.0;
+        void* ws = nullptr;
+        if (cudaMalloc(&ws, bytes + 256) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.0;
+        }
+        void* wsa = (void*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+        smol_batch* B = new smol_batch();
+        double us = -1.0;
+        if (engine_init(B, count, M, R, h_U, h_V, lambda, c, wsa, bytes) == SMOL_OK)
+            us = time_attempts(B, work.data(), d_n0, tol, scheme, attempts);
+        engine_free(B);
+        delete B;
+        cudaFree(ws);
+        return us;
+    };
+    // the size classes present, the one holding the most sizes first
+    const bool wide = is_wide(count, M);
+    std::vector<std::pair<int64_t, int>> cls;
+    for (int q = 0; q < count; ++q) {
+        const int k = ilog2(M[q] < 4 ? 4 : M[q]);
+        bool found = false;
+        for (auto& c : cls)
+            if (c.second == k) {
+                c.first += M[q];
+                found = true;
+            }
+        if (!found) cls.push_back({M[q], k});
+    }
+    std::sort(cls.begin(), cls.end(), [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+        return a.first != b.first ? a.first > b.first : a.second > b.second;
+    });
+    smol_opts cur = base;
+    double best = rc == SMOL_OK ? timeit(cur) : -1.0;
+    if (rc == SMOL_OK && best < 0.0) rc = SMOL_ECUDA;
+    for (size_t ci = 0; ci < cls.size() && rc == SMOL_OK; ++ci) {
+        const int k = cls[ci].second;
+        if (k >= SMOL_SIZE_CLASSES) continue;
+        const int64_t Mk = (int64_t)1 << k;
+        const Shape now = engine_shape(2, Mk, cur, wide);  // the class's schedule so far
+        const Shape rule = make_shape(Mk, base.precision, wide);
+        for (int dl : {-1, 0, 1}) {
+            const int lg = rule.lgN1 + dl;
+            if (lg < 1 || lg >= k) continue;
+            const int g0 = make_shape(Mk, base.precision, wide, lg, 0).G;
+            for (int gm : {1, 2, 4}) {
+                const int g = g0 * gm;
+                if (g > 64 || g > (1 << (k - lg))) continue;
+                if (lg == now.lgN1 && g == now.G) continue;
+                smol_opts c = cur;
+                c.batch_lgn1[k] = (int8_t)lg;
+                c.batch_g[k] = (int8_t)g;
+                const double us = timeit(c);
+                if (us > 0.0 && us < best) {
+                    best = us;
+                    cur = c;
+                }
+            }
+        }
+    }
+    for (double* w : work)
+        if (w) cudaFree(w);
+    if (rc != SMOL_OK) return rc;
+    memcpy(opts->batch_lgn1, cur.batch_lgn1, sizeof(cur.batch_lgn1));
+    memcpy(opts->batch_g, cur.batch_g, sizeof(cur.batch_g));
     if (us_per_attempt) *us_per_attempt = best;
     return SMOL_OK;
 }

@@ -165,3 +165,39 @@ def test_batch_tune_keeps_results(smol):
             assert torch.linalg.norm(x - y) <= 1e-12 * torch.linalg.norm(x)
         else:
             assert torch.equal(x, y)
+
+
+def test_batch_tune_schedules_keeps_results(smol):
+    """smol_batch_tune_schedules picks a schedule per size class among its candidates
+    (log2 N1 within one of the rule, 1, 2 or 4 times the rule's columns per CTA); classes
+    the batch does not hold keep the rule. A batch built with the tables follows the
+    rule's trajectories: another split Mp = N1 N2 changes only the rounding of the
+    transforms. Where a step's error sits at the accept bound that rounding can decide it
+    the other way, and the step sequences part from there: the counts stay within 2%,
+    and the states within the global bound of two runs whose decisions part, 2 A tol
+    (A accepted steps, tol per accepted step; at least 10 tol)."""
+    import torch
+    Us, Vs, lams, n0s = _systems(SPECS)
+    st0 = [torch.from_numpy(n) for n in n0s]
+    tables, us = smol.batch_tune_schedules(Us, Vs, lams, st0, 1e-8, attempts=4, tau0=1e-3)
+    assert us > 0.0
+    held = {int(np.ceil(np.log2(max(M, 4)))) for M, _, _ in SPECS}
+    for k in range(smol.SIZE_CLASSES):
+        lg, g = tables["batch_lgn1"][k], tables["batch_g"][k]
+        if k not in held:
+            assert lg == 0 and g == 0, (k, lg, g)
+            continue
+        assert lg == 0 or 1 <= lg < k, (k, lg)
+        assert g == 0 or (g & (g - 1)) == 0 and g <= 64, (k, g)
+    a = smol.Batch(Us, Vs, lams, tau0=1e-3)
+    ra, sa = a.integrate(st0, 0.0, 0.3, 1e-8)
+    b = smol.Batch(Us, Vs, lams, tau0=1e-3, **tables)
+    rb, sb = b.integrate(st0, 0.0, 0.3, 1e-8)
+    tol = 1e-8
+    for x, y, p, q in zip(ra, rb, sa, sb):
+        assert p["status"] == 0 and q["status"] == 0
+        assert abs(p["accepted"] - q["accepted"]) <= max(2, 0.02 * p["accepted"]), (p["accepted"], q["accepted"])
+        assert float(torch.linalg.norm(x - y)) <= max(10 * tol, 2 * p["accepted"] * tol)
+    with pytest.raises(smol.SmolError):
+        smol.Batch(Us, Vs, lams, batch_g=[3] * smol.SIZE_CLASSES)
+
