@@ -353,7 +353,8 @@ int smol_batch_integrate_start(smol_batch* batch, double* const* d_n, double t0,
                                double tol, int32_t scheme);
 int smol_batch_integrate_advance(smol_batch* batch);
 int smol_batch_integrate_finish(smol_batch* batch, smol_stats* stats);
-/* Launch-mode autotuner of a batch (its FFT schedules follow the rule): times
+/* Launch-mode autotuner of a batch (its FFT schedules are those it was initialised with:
+ * the rule, or the tables of smol_batch_tune_schedules): times
  * `attempts` attempts of every system from copies of the states d_n[q] (not modified)
  * for each launch mode that smol_tune tries, keeps the fastest for later integrations
  * of this batch and returns its flags in *flags and its microseconds per attempt of the
