@@ -297,8 +297,10 @@ int smol_set_sources(smol_system* sys, int32_t count, const int64_t* sizes, cons
  * that the paper leaves open: it only states the O(M R log M) cost of the FFT route,
  * Sec. 1). For one system of the given problem it times `attempts` step attempts of
  * `scheme` at tolerance tol, after one warm-up chunk, for each candidate schedule:
- *   - log2 N1 of the four-step split Mp = N1 N2: the rule's value and one either side;
- *   - columns per CTA of the column kernels: the rule's value, twice and four times it;
+ *   - log2 N1 of the four-step split Mp = N1 N2: the rule's value, one above it and
+ *     two below;
+ *   - columns per CTA of the column kernels: the rule's value and 2, 4 and 8 times it
+ *     (at most 64);
  *   - launch mode: programmatic dependent launch for every kernel, for none, or for
  *     all but the forward column kernel; fused column passes (default) or not; for
  *     RKF45 also the persistent attempt kernel (SMOL_FLAG_PERSISTENT).
@@ -386,7 +388,7 @@ int smol_batch_tune(smol_batch* batch, double* const* d_n, double tol, int32_t s
  * form (Sec. 3 integrates each system on its own; each keeps the FFT route of Sec. 1,
  * only the split Mp = N1 N2 and the columns per CTA change). Coordinate descent over the size
  * classes present, the class holding the most sizes first: for each, the candidates
- * log2 N1 = rule - 1, rule, rule + 1 with 1, 2 and 4 times the rule's columns per CTA
+ * log2 N1 = rule - 2 ... rule + 1 with 1, 2, 4 and 8 times the rule's columns per CTA
  * are timed on the whole batch (`attempts` attempts from the states d_n0 on scratch
  * copies; nothing of the caller's changes), with the other classes at their best so
  * far. The arguments are those of smol_batch_workspace_bytes / smol_batch_init plus the

@@ -1508,11 +1508,11 @@ int smol_tune(int64_t M, int32_t R, const double* h_U, const double* h_V, double
     const Shape def = make_shape(M, base.precision);
     double best = -1.0;
     smol_opts bo = base;
-    for (int dl : {0, -1, 1}) {
+    for (int dl : {0, -1, -2, 1}) {
         const int lg = def.lgN1 + dl;
         if (lg < 1 || lg >= def.lgMp) continue;
         const int g0 = make_shape(M, base.precision, false, lg, 0).G;
-        for (int gm : {1, 2, 4}) {
+        for (int gm : {1, 2, 4, 8}) {
             const int g = g0 * gm;
             if (g > 64 || g > (1 << (def.lgMp - lg))) continue;  // beyond the columns there are
             smol_opts c = base;
@@ -1731,11 +1731,11 @@ int smol_batch_tune_schedules(int32_t count, const int64_t* M, int32_t R, const 
         const int64_t Mk = (int64_t)1 << k;
         const Shape now = engine_shape(2, Mk, cur, wide);  // the class's schedule so far
         const Shape rule = make_shape(Mk, base.precision, wide);
-        for (int dl : {-1, 0, 1}) {
+        for (int dl : {-2, -1, 0, 1}) {
             const int lg = rule.lgN1 + dl;
             if (lg < 1 || lg >= k) continue;
             const int g0 = make_shape(Mk, base.precision, wide, lg, 0).G;
-            for (int gm : {1, 2, 4}) {
+            for (int gm : {1, 2, 4, 8}) {
                 const int g = g0 * gm;
                 if (g > 64 || g > (1 << (k - lg))) continue;
                 if (lg == now.lgN1 && g == now.G) continue;

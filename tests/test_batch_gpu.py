@@ -169,7 +169,8 @@ def test_batch_tune_keeps_results(smol):
 
 def test_batch_tune_schedules_keeps_results(smol):
     """smol_batch_tune_schedules picks a schedule per size class among its candidates
-    (log2 N1 within one of the rule, 1, 2 or 4 times the rule's columns per CTA); classes
+    (log2 N1 from two below the rule to one above, 1, 2, 4 or 8 times the rule's columns
+    per CTA); classes
     the batch does not hold keep the rule. A batch built with the tables follows the
     rule's trajectories: another split Mp = N1 N2 changes only the rounding of the
     transforms. Where a step's error sits at the accept bound that rounding can decide it

@@ -115,12 +115,17 @@ def test_relative_error_bound_is_an_upper_bound(bench):
 
 
 def test_source_digest_ignores_comments(bench, tmp_path, monkeypatch):
+    """The digest follows the kernel headers' code, not their comments, and not the host
+    sources."""
     d = tmp_path / "paper_2407_16559_gb300" / "csrc"
     d.mkdir(parents=True)
-    (d / "a.cu").write_text("int f() { return 1; }  // one\n/* block */\n")
+    (d / "a.cuh").write_text("int f() { return 1; }  // one\n/* block */\n")
+    (d / "host.cu").write_text("int g() { return 1; }\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h1 = bench.src_digest()
-    (d / "a.cu").write_text("int f() { return 1; }  // changed comment\n\n")
+    (d / "a.cuh").write_text("int f() { return 1; }  // changed comment\n\n")
     assert bench.src_digest() == h1
-    (d / "a.cu").write_text("int f() { return 2; }\n")
+    (d / "host.cu").write_text("int g() { return 2; }\n")
+    assert bench.src_digest() == h1
+    (d / "a.cuh").write_text("int f() { return 2; }\n")
     assert bench.src_digest() != h1
