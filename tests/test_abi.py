@@ -66,3 +66,32 @@ def test_invalid_arguments_rejected_before_any_cuda_call(smol):
     assert lib.smol_rhs(None, None, None) == -1
     assert lib.smol_integrate(None, None, 0.0, 1.0, 1e-8, 2, None) == -1
     lib.smol_destroy(None)
+
+
+def test_malformed_schedule_options_rejected_before_any_cuda_call(smol):
+    """The batch's per-size schedule tables (smol_opts.batch_lgn1 / batch_g) are checked
+    like the single system's schedule: columns per CTA a power of two up to 64, log2 N1
+    up to 30; a bad entry is SMOL_EINVAL before the library touches a device."""
+    import numpy as np
+    lib = smol._lib
+    U = np.ones((1024, 1))
+    V = np.ones((1, 1024))
+    M = np.array([1024], dtype=np.int64)
+    pU = (ctypes.c_void_p * 1)(U.ctypes.data)
+    pV = (ctypes.c_void_p * 1)(V.ctypes.data)
+    lam = np.array([0.01])
+    pn = (ctypes.c_void_p * 1)(256)  # never dereferenced: the options are refused first
+    h = ctypes.c_void_p()
+    for field, k, bad in (("batch_g", 10, 3), ("batch_g", 10, -4), ("batch_lgn1", 10, 31), ("batch_lgn1", 5, -1)):
+        o = smol.default_opts()
+        getattr(o, field)[k] = bad
+        assert lib.smol_batch_init(ctypes.byref(h), 1, M.ctypes.data, 1, pU, pV, lam.ctypes.data, ctypes.byref(o),
+                                   256, 1 << 30) == -1, (field, k, bad)
+        us = ctypes.c_double()
+        assert lib.smol_batch_tune_schedules(1, M.ctypes.data, 1, pU, pV, lam.ctypes.data, pn, 1e-8, 2, 4,
+                                             ctypes.byref(o), ctypes.byref(us)) == -1, (field, k, bad)
+    o = smol.default_opts()
+    o.fft_g = 6
+    assert lib.smol_batch_init(ctypes.byref(h), 1, M.ctypes.data, 1, pU, pV, lam.ctypes.data, ctypes.byref(o),
+                               256, 1 << 30) == -1
+    assert smol.SIZE_CLASSES == len(o.batch_lgn1) == len(o.batch_g)
